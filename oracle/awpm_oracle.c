@@ -1,0 +1,374 @@
+/*
+ * CPU ORACLE -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded restatement of the weight-increasing
+ * alternating 4-cycle algorithm (WIAC) of Azad, Buluc, Li, Wang and Langguth,
+ * "A distributed-memory algorithm for computing a heavy-weight perfect matching
+ * on bipartite graphs" (arXiv 1801.09809), Section 5.3, Algorithms 2-6, in
+ * double precision.  Only the test suite, the package's smoke check and the
+ * CPU baseline of the benchmark may load it; the product path never does.
+ * It shares no code, header or table with the CUDA library.
+ *
+ * Conventions.  The matrix is n x n in CSC: colptr[n+1], rowidx[nnz] (rows
+ * strictly increasing inside a column), w[nnz].  Row and column vertices are
+ * both numbered 0..n-1.  mc[j] is the row matched to column j (m_j in the
+ * paper), mr[i] the column matched to row i (m_i), wm[j] = w(mc[j], j), the
+ * weight of the matched edge owned by column j.  A matched edge is named by
+ * its column.
+ *
+ * Readings of the paper (where it is silent or ambiguous):
+ *   - cycles are rooted at columns j and use only rows i > m_j (Section 5.3
+ *     text and Algorithm 3), not all i != m_j of Algorithm 1;
+ *   - the gain is evaluated left to right in IEEE double,
+ *       g = ((w(i,j) + w(m_j,m_i)) - w(i,m_i)) - w(m_j,j)      (Section 3),
+ *     and a cycle qualifies only if g > 0 (Algorithm 4), no epsilon;
+ *   - Step C (Algorithm 5) keeps, per root column j, the maximum gain; equal
+ *     gains go to the lowest row i;
+ *   - Step D (Algorithm 6) drops every Step-C winner whose second matched
+ *     edge {i, m_i} (column k = m_i) is itself the root edge of some Step-C
+ *     winner -- whether or not that winner later survives -- and keeps, per
+ *     remaining key column k, the maximum gain; equal gains go to the lowest
+ *     root column j;
+ *   - Algorithm 2 loops while a cycle was found: `iterations` counts passes of
+ *     Steps A-D including the last one that found nothing; max_iters = 0
+ *     means "until nothing is found" (with a cap of ORACLE_PASS_CAP passes).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_PASS_CAP 65536
+
+/* error codes (same meaning as the library's, defined independently) */
+#define OR_OK 0
+#define OR_INVALID_ARG 1
+#define OR_NOT_PERFECT 2
+#define OR_UNSORTED_OR_DUP 3
+#define OR_NONFINITE 4
+#define OR_OOM 5
+
+typedef struct {
+    int32_t iterations;      /* passes of Steps A-D executed */
+    int32_t converged;       /* 1 if the last pass found no weight-increasing cycle */
+    int64_t cycles_applied;  /* cycles flipped in total */
+    int64_t edge_checks;     /* (nnz - n) per pass */
+    int64_t candidates;      /* A-requests: entries (i, j) with i > m_j */
+    int64_t closing_found;   /* A-requests whose closing edge {m_j, m_i} exists */
+    int64_t positive;        /* B-requests: closing edge exists and g > 0 */
+    double weight_in;        /* sum over j of w(m_j, j), ascending j */
+    double weight_out;
+} oracle_stats;
+
+/* One A-request of Algorithm 3, carrying the cycle's four vertices. */
+typedef struct {
+    int32_t i, j, mj, mi;
+    double wij;
+} a_request;
+
+/* One B-request of Algorithm 4 (the closing weight rides along for the flip). */
+typedef struct {
+    int32_t i, j, mj, mi;
+    double g;
+    double wij, wq;
+} b_request;
+
+/* Position of entry (row, col) in the CSC arrays, or -1.  Linear scan. */
+static int64_t find_entry(const int32_t *colptr, const int32_t *rowidx, int32_t row, int32_t col)
+{
+    for (int64_t p = colptr[col]; p < colptr[col + 1]; ++p)
+        if (rowidx[p] == row)
+            return p;
+    return -1;
+}
+
+/*
+ * Input checks, in priority order: malformed arguments or column pointers or
+ * out-of-range rows (INVALID_ARG), rows not strictly increasing in a column
+ * (UNSORTED_OR_DUP), non-finite weights (NONFINITE), matching not a perfect
+ * matching over stored entries (NOT_PERFECT).
+ */
+int oracle_validate(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+                    const int32_t *mate)
+{
+    if (n < 0 || (n > 0 && (!colptr || !mate)))
+        return OR_INVALID_ARG;
+    if (n == 0)
+        return OR_OK;
+    if (colptr[0] != 0)
+        return OR_INVALID_ARG;
+    for (int32_t j = 0; j < n; ++j)
+        if (colptr[j + 1] < colptr[j])
+            return OR_INVALID_ARG;
+    int64_t nnz = colptr[n];
+    if (nnz > 0 && (!rowidx || !w))
+        return OR_INVALID_ARG;
+    for (int64_t p = 0; p < nnz; ++p)
+        if (rowidx[p] < 0 || rowidx[p] >= n)
+            return OR_INVALID_ARG;
+    for (int32_t j = 0; j < n; ++j)
+        for (int64_t p = colptr[j] + 1; p < colptr[j + 1]; ++p)
+            if (rowidx[p] <= rowidx[p - 1])
+                return OR_UNSORTED_OR_DUP;
+    for (int64_t p = 0; p < nnz; ++p)
+        if (!isfinite(w[p]))
+            return OR_NONFINITE;
+    char *seen = (char *)calloc((size_t)n, 1);
+    if (!seen)
+        return OR_OOM;
+    int rc = OR_OK;
+    for (int32_t j = 0; j < n && rc == OR_OK; ++j) {
+        int32_t r = mate[j];
+        if (r < 0 || r >= n || seen[r] || find_entry(colptr, rowidx, r, j) < 0)
+            rc = OR_NOT_PERFECT;
+        else
+            seen[r] = 1;
+    }
+    free(seen);
+    return rc;
+}
+
+/* Sum of the matched weights, ascending column order. */
+static double matching_weight(int32_t n, const double *wm)
+{
+    double s = 0.0;
+    for (int32_t j = 0; j < n; ++j)
+        s += wm[j];
+    return s;
+}
+
+/*
+ * One iteration of Algorithm 2: Steps A, B, C and D, then the flip.
+ * mc, mr, wm are updated in place.  Optional outputs (NULL to skip):
+ *   stepc_gain[j], stepc_row[j]: the Step-C winner rooted at column j
+ *       (gain, row i), or (0, -1) if column j sent no C-request;
+ *   stepd_root[k]: root column j of the cycle that won key column k in Step D
+ *       and was flipped, or -1;
+ *   counts[4]: candidates, closing_found, positive, flipped for this pass.
+ * Returns the number of cycles flipped, or -1 on allocation failure.
+ */
+int64_t oracle_pass(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+                    int32_t *mc, int32_t *mr, double *wm,
+                    double *stepc_gain, int32_t *stepc_row, int32_t *stepd_root, int64_t *counts)
+{
+    int64_t nnz = n > 0 ? colptr[n] : 0;
+    a_request *areq = (a_request *)malloc(sizeof(a_request) * (size_t)(nnz > 0 ? nnz : 1));
+    b_request *breq = (b_request *)malloc(sizeof(b_request) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t *cwin = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *dwin = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!areq || !breq || !cwin || !dwin) {
+        free(areq); free(breq); free(cwin); free(dwin);
+        return -1;
+    }
+    int64_t na = 0, nb = 0, nfound = 0;
+
+    /* Step A (Algorithm 3): every stored (i, j) with i > m_j asks the owner of
+     * {m_j, m_i} to close the cycle i - j - m_j - m_i. */
+    for (int32_t j = 0; j < n; ++j) {
+        int32_t mj = mc[j];
+        for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+            int32_t i = rowidx[p];
+            if (i > mj) {
+                a_request a;
+                a.i = i;
+                a.j = j;
+                a.mj = mj;
+                a.mi = mr[i];
+                a.wij = w[p];
+                areq[na++] = a;
+            }
+        }
+    }
+
+    /* Step B (Algorithm 4): if {m_j, m_i} exists, compute the gain
+     *   g(i,j,m_j,m_i) = w(i,j) + w(m_i,m_j) - w(i,m_i) - w(m_j,j)
+     * and forward positive ones.  w(i, m_i) is the matched weight of column m_i,
+     * w(m_j, j) the matched weight of column j. */
+    for (int64_t x = 0; x < na; ++x) {
+        a_request a = areq[x];
+        int64_t q = find_entry(colptr, rowidx, a.mj, a.mi);
+        if (q < 0)
+            continue;
+        ++nfound;
+        double wq = w[q];
+        double g = a.wij + wq - wm[a.mi] - wm[a.j];
+        if (g > 0.0) {
+            b_request b;
+            b.i = a.i;
+            b.j = a.j;
+            b.mj = a.mj;
+            b.mi = a.mi;
+            b.g = g;
+            b.wij = a.wij;
+            b.wq = wq;
+            breq[nb++] = b;
+        }
+    }
+
+    /* Step C (Algorithm 5): per matched edge {m_j, j}, i.e. per root column j,
+     * keep the B-request of maximum gain (equal gains: lowest row i). */
+    for (int32_t j = 0; j < n; ++j)
+        cwin[j] = -1;
+    for (int64_t x = 0; x < nb; ++x) {
+        int32_t j = breq[x].j;
+        int64_t cur = cwin[j];
+        if (cur < 0 || breq[x].g > breq[cur].g ||
+            (breq[x].g == breq[cur].g && breq[x].i < breq[cur].i))
+            cwin[j] = x;
+    }
+
+    /* Step D (Algorithm 6): per matched edge {i, m_i}, i.e. per key column
+     * k = m_i, keep the C-request of maximum gain (equal gains: lowest root j);
+     * a C-request whose key column k itself sent a C-request is dropped. */
+    for (int32_t k = 0; k < n; ++k)
+        dwin[k] = -1;
+    for (int32_t j = 0; j < n; ++j) {
+        if (cwin[j] < 0)
+            continue;
+        b_request *c = &breq[cwin[j]];
+        int32_t k = c->mi;
+        if (cwin[k] >= 0)
+            continue;
+        int64_t cur = dwin[k];
+        if (cur < 0 || c->g > breq[cur].g || (c->g == breq[cur].g && c->j < breq[cur].j))
+            dwin[k] = cwin[j];
+    }
+
+    if (stepc_gain || stepc_row) {
+        for (int32_t j = 0; j < n; ++j) {
+            if (stepc_gain)
+                stepc_gain[j] = cwin[j] >= 0 ? breq[cwin[j]].g : 0.0;
+            if (stepc_row)
+                stepc_row[j] = cwin[j] >= 0 ? breq[cwin[j]].i : -1;
+        }
+    }
+
+    /* Flip M := M xor {cycle}: column j takes row i, column k = m_i takes row m_j. */
+    int64_t flipped = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        if (stepd_root)
+            stepd_root[k] = dwin[k] >= 0 ? breq[dwin[k]].j : -1;
+        if (dwin[k] < 0)
+            continue;
+        b_request c = breq[dwin[k]];
+        mc[c.j] = c.i;
+        mr[c.i] = c.j;
+        mc[c.mi] = c.mj;
+        mr[c.mj] = c.mi;
+        wm[c.j] = c.wij;
+        wm[c.mi] = c.wq;
+        ++flipped;
+    }
+
+    if (counts) {
+        counts[0] = na;
+        counts[1] = nfound;
+        counts[2] = nb;
+        counts[3] = flipped;
+    }
+    free(areq);
+    free(breq);
+    free(cwin);
+    free(dwin);
+    return flipped;
+}
+
+/*
+ * Whole phase (Algorithm 2): initialise mates and matched weights from
+ * mate_in, run passes until one finds nothing (or max_iters passes ran),
+ * write the final matching to mate_out (may alias mate_in).
+ * trace_weight / trace_flips (capacity trace_cap, may be NULL) receive the
+ * matching weight and the number of cycles flipped after each pass.
+ */
+int oracle_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+                   const int32_t *mate_in, int32_t *mate_out, int32_t max_iters,
+                   oracle_stats *st, double *trace_weight, int64_t *trace_flips, int32_t trace_cap)
+{
+    oracle_stats s;
+    memset(&s, 0, sizeof(s));
+    int rc = oracle_validate(n, colptr, rowidx, w, mate_in);
+    if (rc != OR_OK)
+        return rc;
+    if (max_iters < 0)
+        return OR_INVALID_ARG;
+    int32_t nn = n > 0 ? n : 1;
+    int32_t *mc = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);
+    int32_t *mr = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);
+    double *wm = (double *)malloc(sizeof(double) * (size_t)nn);
+    if (!mc || !mr || !wm) {
+        free(mc); free(mr); free(wm);
+        return OR_OOM;
+    }
+    /* Initialisation (Algorithm 2, before the loop): every owner learns the
+     * mates and the matched weights. */
+    for (int32_t j = 0; j < n; ++j) {
+        mc[j] = mate_in[j];
+        mr[mate_in[j]] = j;
+        wm[j] = w[find_entry(colptr, rowidx, mate_in[j], j)];
+    }
+    s.weight_in = matching_weight(n, wm);
+    int64_t nnz = n > 0 ? colptr[n] : 0;
+    int32_t cap = max_iters > 0 ? max_iters : ORACLE_PASS_CAP;
+    for (int32_t it = 1; it <= cap; ++it) {
+        int64_t counts[4];
+        int64_t f = oracle_pass(n, colptr, rowidx, w, mc, mr, wm, NULL, NULL, NULL, counts);
+        if (f < 0) {
+            rc = OR_OOM;
+            break;
+        }
+        s.iterations = it;
+        s.edge_checks += nnz - n;
+        s.candidates += counts[0];
+        s.closing_found += counts[1];
+        s.positive += counts[2];
+        s.cycles_applied += f;
+        if (trace_weight && it <= trace_cap)
+            trace_weight[it - 1] = matching_weight(n, wm);
+        if (trace_flips && it <= trace_cap)
+            trace_flips[it - 1] = f;
+        if (f == 0) {
+            s.converged = 1;
+            break;
+        }
+    }
+    s.weight_out = matching_weight(n, wm);
+    if (rc == OR_OK)
+        for (int32_t j = 0; j < n; ++j)
+            mate_out[j] = mc[j];
+    if (st)
+        *st = s;
+    free(mc);
+    free(mr);
+    free(wm);
+    return rc;
+}
+
+/*
+ * Step-C records of one pass from a given matching, without flipping
+ * (Algorithms 3-5): stepc_gain[j], stepc_row[j] as in oracle_pass.
+ */
+int oracle_step_c(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+                  const int32_t *mate, double *stepc_gain, int32_t *stepc_row, int64_t *counts)
+{
+    int rc = oracle_validate(n, colptr, rowidx, w, mate);
+    if (rc != OR_OK)
+        return rc;
+    int32_t nn = n > 0 ? n : 1;
+    int32_t *mc = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);
+    int32_t *mr = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);
+    double *wm = (double *)malloc(sizeof(double) * (size_t)nn);
+    if (!mc || !mr || !wm) {
+        free(mc); free(mr); free(wm);
+        return OR_OOM;
+    }
+    for (int32_t j = 0; j < n; ++j) {
+        mc[j] = mate[j];
+        mr[mate[j]] = j;
+        wm[j] = w[find_entry(colptr, rowidx, mate[j], j)];
+    }
+    int64_t f = oracle_pass(n, colptr, rowidx, w, mc, mr, wm, stepc_gain, stepc_row, NULL, counts);
+    free(mc);
+    free(mr);
+    free(wm);
+    return f < 0 ? OR_OOM : OR_OK;
+}

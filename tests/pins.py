@@ -1,0 +1,279 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Each pin takes an oracle instance and raises AssertionError when the oracle
+disagrees.  They are collected in PINS so that the same suite can be run
+against deliberately broken copies of the oracle (tests/test_oracle_mutants.py):
+every plausible mistake must trip at least one pin.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import brute
+from paper_1801_09809_gb300 import gen
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ----------------------------------------------------------------------------
+# fixtures
+# ----------------------------------------------------------------------------
+
+def load_hand_cases(path=os.path.join(GOLDEN, "hand_cases.txt")):
+    cases, cur = [], None
+    for raw in open(path):
+        line = raw.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, _, rest = line.partition(" ")
+        if key == "case":
+            cur = {"name": rest, "entries": []}
+            cases.append(cur)
+        elif key == "cite":
+            cur["cite"] = rest
+        elif key == "n":
+            cur["n"] = int(rest)
+        elif key == "mate":
+            cur["mate"] = [int(x) for x in rest.split()]
+        elif key == "e":
+            r, c, w = rest.split()
+            cur["entries"].append((int(r), int(c), float(w)))
+        elif key == "expect_mate":
+            cur["expect_mate"] = [int(x) for x in rest.split()]
+        elif key in ("expect_iterations", "expect_cycles"):
+            cur[key] = int(rest)
+        elif key == "expect_weight":
+            cur[key] = float(rest)
+        else:
+            raise ValueError(line)
+    return cases
+
+
+def graph_of_case(c):
+    n = c["n"]
+    W = np.zeros((n, n))
+    S = np.zeros((n, n), dtype=bool)
+    for r, col, w in c["entries"]:
+        W[r, col] = w
+        S[r, col] = True
+    return gen.from_dense(W, S, c["mate"])
+
+
+def full2(w00, w01, w10, w11, mate=(0, 1)):
+    W = np.array([[w00, w01], [w10, w11]], dtype=np.float64)
+    return gen.from_dense(W, np.ones((2, 2), dtype=bool), list(mate))
+
+
+# ----------------------------------------------------------------------------
+# pins
+# ----------------------------------------------------------------------------
+
+def pin_hand_cases(orc):
+    """Hand-derived outcomes (tests/golden/hand_cases.txt)."""
+    for c in load_hand_cases():
+        g = graph_of_case(c)
+        out, st, _ = orc.improve(g)
+        assert out.tolist() == c["expect_mate"], (c["name"], out)
+        assert st["iterations"] == c["expect_iterations"], (c["name"], st)
+        assert st["cycles_applied"] == c["expect_cycles"], (c["name"], st)
+        assert st["converged"] == 1, c["name"]
+        assert st["weight_out"] == c["expect_weight"], (c["name"], st)
+
+
+def pin_2x2_closed_form(orc):
+    """n = 2, full pattern.  The only alternating 4-cycle swaps the two matched
+    edges; by the gain definition (Section 3) it flips exactly when
+    w01 + w10 > w00 + w11 (identity start), strictly (Algorithm 4)."""
+    vals = [-3.0, -1.5, -1.0, -0.25, 0.0, 0.5, 2.0]
+    rng = np.random.default_rng(7)
+    for _ in range(300):
+        w00, w01, w10, w11 = rng.choice(vals, 4)
+        for mate in ((0, 1), (1, 0)):
+            g = full2(w00, w01, w10, w11, mate)
+            out, st, _ = orc.improve(g)
+            if mate == (0, 1):
+                flip = (w01 + w10) > (w00 + w11)
+                expect = [1, 0] if flip else [0, 1]
+            else:
+                flip = (w00 + w11) > (w01 + w10)
+                expect = [0, 1] if flip else [1, 0]
+            assert out.tolist() == expect, (w00, w01, w10, w11, mate, out)
+            assert st["cycles_applied"] == int(flip)
+            assert st["iterations"] == (2 if flip else 1)
+            wexp = (w10 + w01) if expect == [1, 0] else (w00 + w11)
+            assert st["weight_out"] == wexp
+
+
+def pin_block_diagonal(orc):
+    """k independent full 2x2 blocks: one pass flips every block with positive
+    gain (they are vertex-disjoint and rooted at different columns), the
+    second pass finds nothing, and the result is the maximum-weight perfect
+    matching of each block (assignment problem on 2 x 2)."""
+    rng = np.random.default_rng(11)
+    k = 40
+    n = 2 * k
+    W = np.zeros((n, n))
+    S = np.zeros((n, n), dtype=bool)
+    mate = np.arange(n)
+    nflip = 0
+    expect = np.arange(n)
+    for b in range(k):
+        blk = rng.integers(-8, 9, size=(2, 2)).astype(np.float64) / 4.0
+        W[2 * b:2 * b + 2, 2 * b:2 * b + 2] = blk
+        S[2 * b:2 * b + 2, 2 * b:2 * b + 2] = True
+        if blk[0, 1] + blk[1, 0] > blk[0, 0] + blk[1, 1]:
+            nflip += 1
+            expect[2 * b], expect[2 * b + 1] = 2 * b + 1, 2 * b
+    g = gen.from_dense(W, S, mate)
+    out, st, trace = orc.improve(g, trace_cap=8)
+    assert out.tolist() == expect.tolist()
+    assert st["cycles_applied"] == nflip
+    assert st["iterations"] == (2 if nflip else 1)
+    assert trace[1][0] == nflip
+
+
+def pin_six_cycle(orc):
+    """Section 4: an alternating 6-cycle has no 4-cycle, so the phase cannot
+    improve it although a far heavier perfect matching exists."""
+    c = [x for x in load_hand_cases() if x["name"] == "six_cycle_counterexample"][0]
+    g = graph_of_case(c)
+    out, st, _ = orc.improve(g)
+    best, arg = brute.mwpm_bruteforce(g)
+    assert out.tolist() == [0, 1, 2] and st["cycles_applied"] == 0
+    assert best == 30.0 and arg.tolist() == [1, 2, 0]
+
+
+def _small_graphs(count=60, integer=False):
+    for s in range(count):
+        n = 2 + s % 6
+        dens = (0.3, 0.5, 0.8)[s % 3]
+        yield gen.random_small(n, dens, 1000 + s, integer_weights=integer)
+
+
+def pin_bruteforce_small(orc):
+    """n <= 7: the output is a perfect matching over stored entries; the weight
+    never decreases from pass to pass; every pass but the last flips >= 1
+    cycle; at exit no positive-gain alternating 4-cycle remains (exhaustive
+    enumeration of column pairs); and the weight is at most the maximum over
+    all perfect matchings (exhaustive enumeration)."""
+    for integer in (False, True):
+        for g in _small_graphs(integer=integer):
+            out, st, trace = orc.improve(g, trace_cap=64)
+            assert brute.is_perfect(g, out)
+            assert st["converged"] == 1
+            ws, fs = trace
+            prev = st["weight_in"]
+            for t in range(len(ws)):
+                assert ws[t] >= prev
+                prev = ws[t]
+                if t < len(ws) - 1:
+                    assert fs[t] >= 1
+                    assert ws[t] > ws[t - 1] if t > 0 else ws[t] > st["weight_in"]
+            assert fs[-1] == 0
+            assert brute.positive_4cycles(g, out) == []
+            best, _ = brute.mwpm_bruteforce(g)
+            assert st["weight_out"] <= best + 1e-12
+            assert abs(brute.matching_weight(g, out) - st["weight_out"]) <= 1e-12
+
+
+def pin_one_pass_bruteforce(orc):
+    """One pass from random matchings equals the dense set-and-sort restatement
+    of Steps A-D (integer weights make ties frequent)."""
+    rng = np.random.default_rng(5)
+    for s in range(80):
+        n = 3 + s % 6
+        g = gen.random_small(n, 0.7, 2000 + s, integer_weights=(s % 2 == 0))
+        mats = list(brute.all_perfect_matchings(g))
+        for m in [mats[x] for x in rng.choice(len(mats), size=min(4, len(mats)), replace=False)]:
+            new, flips = brute.one_pass_bruteforce(g, m)
+            got, droot, counts = orc.one_pass(g, m)
+            assert got.tolist() == new.tolist(), (s, m, got, new)
+            assert sorted((int(droot[k]), k) for k in range(n) if droot[k] >= 0) == flips
+            assert counts[3] == len(flips)
+
+
+def pin_local_optimality_midsize(orc):
+    """Random sparse n = 2000 (the small workload): perfect output, no
+    positive-gain 4-cycle at exit (vectorised exhaustive check), weight at
+    most the exact maximum-weight perfect matching (LAPJVsp, scipy)."""
+    from scipy.optimize import linear_sum_assignment  # noqa: F401 (availability)
+    from scipy.sparse import csc_matrix
+    from scipy.sparse.csgraph import min_weight_full_bipartite_matching
+    g = gen.config1()
+    out, st, trace = orc.improve(g, trace_cap=256)
+    assert st["converged"] == 1
+    assert sorted(out.tolist()) == list(range(g.n))
+    assert brute.no_positive_4cycle_vectorized(g, out)
+    assert np.all(np.diff(np.concatenate([[st["weight_in"]], trace[0]])) >= 0)
+    # exact optimum: shift weights to be > 0 (zeros would vanish from the
+    # sparse pattern); a constant shift moves every perfect matching equally
+    shift = 1.0 - g.weight.min()
+    A = csc_matrix((g.weight + shift, g.rowidx, g.colptr), shape=(g.n, g.n))
+    r, c = min_weight_full_bipartite_matching(A, maximize=True)
+    opt = float(np.sum(np.asarray(A[r, c]).ravel())) - shift * g.n
+    assert st["weight_out"] <= opt + 1e-9 * abs(opt)
+    assert st["weight_out"] > st["weight_in"]
+
+
+def pin_validation(orc):
+    """Input checks: error classes for malformed inputs."""
+    g = gen.random_small(5, 0.6, 3)
+    assert orc.validate(g) == "OK"
+    bad = g.copy(); bad.mate[0] = bad.mate[1]
+    assert orc.validate(bad) == "NOT_PERFECT"
+    bad = g.copy(); bad.mate[0] = g.n
+    assert orc.validate(bad) == "NOT_PERFECT"
+    # a mate that is not a stored entry
+    W, S = brute.dense(g)
+    for j in range(g.n):
+        missing = [r for r in range(g.n) if not S[r, j]]
+        if missing:
+            bad = g.copy()
+            other = int(np.nonzero(bad.mate == missing[0])[0][0])
+            bad.mate[j], bad.mate[other] = missing[0], bad.mate[j]
+            assert orc.validate(bad) == "NOT_PERFECT"
+            break
+    bad = g.copy(); bad.weight[2] = np.inf
+    assert orc.validate(bad) == "NONFINITE"
+    bad = g.copy(); bad.weight[1] = np.nan
+    assert orc.validate(bad) == "NONFINITE"
+    bad = g.copy(); bad.rowidx[0] = -1
+    assert orc.validate(bad) == "INVALID_ARG"
+    bad = g.copy(); bad.colptr[1] = bad.colptr[2] + 1
+    assert orc.validate(bad) == "INVALID_ARG"
+    j = int(np.argmax(np.diff(g.colptr)))
+    bad = g.copy(); a, b = g.colptr[j], g.colptr[j] + 1
+    bad.rowidx[a], bad.rowidx[b] = g.rowidx[b], g.rowidx[a]
+    assert orc.validate(bad) == "UNSORTED_OR_DUP"
+
+
+def pin_resume(orc):
+    """Each pass is a function of (graph, matching) alone: stopping after t
+    passes and restarting from that matching gives the same final matching
+    and the same total number of passes."""
+    g = gen.config1()
+    full, st, _ = orc.improve(g)
+    for t in (1, 2, 3):
+        if t >= st["iterations"]:
+            break
+        mid, st1, _ = orc.improve(g, max_iters=t)
+        assert st1["iterations"] == t and st1["converged"] == 0
+        fin, st2, _ = orc.improve(g, mate=mid)
+        assert fin.tolist() == full.tolist()
+        assert t + st2["iterations"] == st["iterations"]
+
+
+def pin_paper_maxiters(orc):
+    """Algorithm 2 with maxiters = 10: at most 10 passes; converged only when
+    the last pass found nothing."""
+    g = gen.config1()
+    out, st, trace = orc.improve(g, max_iters=10, trace_cap=10)
+    assert st["iterations"] <= 10
+    assert st["converged"] == int(trace[1][-1] == 0)
+
+
+PINS = [pin_hand_cases, pin_2x2_closed_form, pin_block_diagonal, pin_six_cycle,
+        pin_bruteforce_small, pin_one_pass_bruteforce, pin_local_optimality_midsize,
+        pin_validation, pin_resume, pin_paper_maxiters]

@@ -1,0 +1,76 @@
+"""Planted mistakes in the CPU oracle must each be caught by a pin (no GPU).
+
+Each mutant is a copy of oracle/awpm_oracle.c with one plausible mistake
+(a dropped term, a wrong sign or index, a transposed operand, a wrong
+tie-break, a missing rule); it is compiled into a temporary library and the
+whole pin suite is run against it in a child process.  The test passes when at
+least one pin fails for every mutant.
+"""
+import os
+import subprocess
+import sys
+import textwrap
+
+import pytest
+
+import oracle
+
+MUTANTS = [
+    ("closing weight sign", "double g = a.wij + wq - wm[a.mi] - wm[a.j];",
+     "double g = a.wij - wq - wm[a.mi] - wm[a.j];"),
+    ("dropped root matched weight", "double g = a.wij + wq - wm[a.mi] - wm[a.j];",
+     "double g = a.wij + wq - wm[a.mi];"),
+    ("matched weight indexed by row", "double g = a.wij + wq - wm[a.mi] - wm[a.j];",
+     "double g = a.wij + wq - wm[a.mj] - wm[a.j];"),
+    ("closing weight replaced by own weight", "double g = a.wij + wq - wm[a.mi] - wm[a.j];",
+     "double g = a.wij + a.wij - wm[a.mi] - wm[a.j];"),
+    ("transposed closing lookup", "find_entry(colptr, rowidx, a.mj, a.mi);",
+     "find_entry(colptr, rowidx, a.mi, a.mj);"),
+    ("root filter dropped", "if (i > mj) {", "if (i != mj) {"),
+    ("root filter reversed", "if (i > mj) {", "if (i < mj) {"),
+    ("non-strict positivity", "if (g > 0.0) {", "if (g >= 0.0) {"),
+    ("step C keeps minimum", "breq[x].g > breq[cur].g ||", "breq[x].g < breq[cur].g ||"),
+    ("step C tie to highest row", "breq[x].i < breq[cur].i", "breq[x].i > breq[cur].i"),
+    ("step D tie to highest root", "c->j < breq[cur].j", "c->j > breq[cur].j"),
+    ("step D keeps minimum", "c->g > breq[cur].g ||", "c->g < breq[cur].g ||"),
+    ("step D discard rule dropped", "if (cwin[k] >= 0)\n            continue;\n        int64_t cur = dwin[k];",
+     "int64_t cur = dwin[k];"),
+    ("flip gives key column the wrong row", "mc[c.mi] = c.mj;", "mc[c.mi] = c.i;"),
+    ("flip forgets the row side", "mr[c.mj] = c.mi;", "mr[c.mj] = c.j;"),
+    ("flip keeps stale matched weight", "wm[c.mi] = c.wq;", "wm[c.mi] = c.wij;"),
+    ("stops one pass early", "if (f == 0) {", "if (f <= 1) {"),
+    ("duplicate mates accepted", "if (r < 0 || r >= n || seen[r] ||", "if (r < 0 || r >= n ||"),
+    ("non-finite weights accepted", "if (!isfinite(w[p]))", "if (0)"),
+]
+
+RUNNER = textwrap.dedent("""
+    import sys
+    sys.path[:0] = [{root!r}, {tests!r}]
+    import oracle, pins
+    orc = oracle.Oracle({so!r})
+    failed = []
+    for pin in pins.PINS:
+        try:
+            pin(orc)
+        except Exception as e:  # any failure of the pin counts
+            failed.append(pin.__name__)
+            break
+    print("FAILED_PINS", failed)
+    sys.exit(0 if failed else 3)
+""")
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, new):
+    src = open(oracle.SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    mpath = tmp_path / "mutant.c"
+    mpath.write_text(src.replace(old, new))
+    so = str(tmp_path / "mutant.so")
+    oracle.compile_oracle(str(mpath), so)
+    root = os.path.dirname(oracle.HERE)
+    tests = os.path.dirname(os.path.abspath(__file__))
+    code = RUNNER.format(root=root, tests=tests, so=so)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    # exit 0: a pin failed (caught); a crash (negative code) is caught too
+    assert r.returncode != 3, f"mutant '{name}' passed every pin:\n{r.stdout}\n{r.stderr}"
