@@ -1,0 +1,336 @@
+"""Benchmark of the weight-increasing 4-cycle phase on one GB300 (or N replicas).
+
+One step = one whole solve (validation, initialisation, every pass of
+Steps A-D until a pass finds nothing, final weight) of the R-MAT graph
+n = 4,194,304 (16 n samples, a = .57, b = c = .19, planted random perfect
+matching, log-normal weights with the per-column log transform), the
+largest single graph of the workload set.  Its CSC (833 MB) is larger than
+L2 (129 MB), so no L2 flush is needed between steps.
+
+Metric: edge-checks/s = (nnz - n) x passes / time.  `value` uses device-resident
+inputs; `e2e` the same call with pinned host buffers (host<->device copies
+inside the timed region).  `roofline` covers the cycle-search kernel, timed
+with CUDA events around each of its launches in a second timed region.
+`--impl reference` times the CPU oracle instead (one pass per step).
+Multi-GPU: independent replicas, one per rank (weak scaling, no collective
+on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AWPM edge-checks/s and HBM GB/s at 1 GB300"
+UNIT = "edge-checks/s"
+PROFILE = os.path.join(ROOT, "profiles", "k_search_rmat_s22.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1801_09809_gb300", "csrc", "awpm_kernels.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "stencil3d", "stencil2d"])
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1801_09809_gb300 import gen
+    if name == "rmat":
+        g = gen.config3b()
+        desc = ("R-MAT n=4,194,304 (scale 22), 16n samples a=.57 b=c=.19 d=.05 deduplicated, "
+                "rows/cols randomly relabelled, planted random perfect matching, "
+                "log-normal weights with per-column log transform")
+    elif name == "stencil3d":
+        g = gen.config3a()
+        desc = "3D 27-point stencil 96^3, random row+col permutations, log-normal weights"
+    else:
+        g = gen.config2()
+        desc = "2D 5-point stencil 1000^2, random row permutation, diag U[.5,1.5] offdiag N(0,1)"
+    return g, desc
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def profile_traffic():
+    """DRAM bytes per search launch from the committed ncu summary, or None
+    when the kernel source changed since the capture."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, _, v = line.strip()[2:].partition(":")
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            time.sleep(0.2)
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier_max(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(g, desc_sample="one full solve of the same graph (oracle)"):
+    import oracle
+    orc = oracle.get()
+    t0 = time.perf_counter()
+    _, st, _ = orc.improve(g)
+    dt = time.perf_counter() - t0
+    return {"value": st["edge_checks"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{desc_sample}: {st['iterations']} passes, {dt:.1f} s, single thread"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    g, desc = workload(args.workload)
+    orc = oracle.get()
+    mate = g.mate.copy()
+    for _ in range(args.warmup):
+        orc.one_pass(g, mate)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.one_pass(g, mate)
+    dt = time.perf_counter() - t0
+    units = (g.nnz - g.n) * args.steps
+    v = units / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "n": g.n, "nnz": g.nnz,
+                       "step": "one pass of Steps A-D + flip of the CPU oracle from the planted matching"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} single passes over the full graph"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_1801_09809_gb300 import awpm, build
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    g, desc = workload(args.workload)
+    n, nnz = g.n, g.nnz
+
+    stream = torch.cuda.Stream(device=dev)
+    ctx = awpm.awpm_create(device=local, stream=stream.cuda_stream)
+    tctx = awpm.awpm_create(device=local, stream=stream.cuda_stream, flags=awpm.FLAG_TIME_SEARCH)
+    cp = torch.from_numpy(g.colptr).to(dev)
+    ri = torch.from_numpy(g.rowidx).to(dev)
+    w = torch.from_numpy(g.weight).to(dev)
+    m_in = torch.from_numpy(g.mate).to(dev)
+    m_out = torch.empty_like(m_in)
+
+    def step(c):
+        return awpm.awpm_improve_ctx(c, n, cp, ri, w, m_in, m_out)
+
+    for _ in range(args.warmup):
+        st = step(ctx)
+    passes = st["iterations"]
+
+    # timed region 1: device-resident inputs, whole solves
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        checks = 0
+        for _ in range(args.steps):
+            st = step(ctx)
+            checks += st["edge_checks"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = e0.elapsed_time(e1)
+    ms_max = barrier_max(world, ms)
+    value = checks * world / (ms_max / 1e3)
+
+    # timed region 2: the same solves with CUDA events around every search launch
+    for _ in range(2):
+        step(tctx)
+    torch.cuda.synchronize()
+    search_ms = 0.0
+    launches = 0
+    cand = 0
+    for _ in range(args.steps):
+        st2 = step(tctx)
+        search_ms += st2["ms_search"]
+        launches += st2["iterations"]
+        cand += st2["candidates"]
+    pk, pk_kind = peaks()
+    # algorithmic bytes of the search (per pass): rowidx + w (12 B/nz), colptr,
+    # mc + wm of the root column (12 B/col), 32 B per candidate (mr[i], wm[m_i],
+    # colptr pair, closing row, closing weight), 20 B/col of Step-C output
+    alg_bytes = launches * (12.0 * nnz + 4.0 * (n + 1) + 12.0 * n + 20.0 * n) + 32.0 * cand
+    avg_ms = search_ms / max(launches, 1)
+    achieved = alg_bytes / launches / (avg_ms / 1e3) / 1e9
+    traffic = profile_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                "kernel": "k_search (Steps A+B+C)", "avg_launch_ms": avg_ms,
+                "alg_bytes_per_launch": alg_bytes / launches, "peak_kind": pk_kind}
+
+    # timed region 3: end to end through host (pinned) buffers
+    h_cp = torch.from_numpy(g.colptr).pin_memory()
+    h_ri = torch.from_numpy(g.rowidx).pin_memory()
+    h_w = torch.from_numpy(g.weight).pin_memory()
+    h_m = torch.from_numpy(g.mate).pin_memory()
+    h_out = torch.empty_like(h_m).pin_memory()
+    for _ in range(2):
+        awpm.awpm_improve_ctx(ctx, n, h_cp, h_ri, h_w, h_m, h_out)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    e2e_checks = 0
+    for _ in range(args.steps):
+        s3 = awpm.awpm_improve_ctx(ctx, n, h_cp, h_ri, h_w, h_m, h_out)
+        e2e_checks += s3["edge_checks"]
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = barrier_max(world, t0.elapsed_time(t1))
+    assert np.array_equal(h_out.numpy(), m_out.cpu().numpy())
+    h2d = 4 * (n + 1) + 12 * nnz + 4 * n
+    d2h = 4 * n + 88
+
+    kernels_per_step = 7 + 4 * passes + 2
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "nnz": nnz, "passes": passes,
+                       "cycles_applied": st["cycles_applied"], "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (CSC %.0f MB vs 129 MB L2): no flush" %
+                             ((4 * (n + 1) + 12 * nnz) / 1e6),
+                       "hbm_gbs_search": achieved},
+            "roofline": roofline,
+            "e2e": {"value": e2e_checks * world / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": kernels_per_step * args.steps,
+            "clocks": clk.summary()}
+    awpm.awpm_destroy(ctx)
+    awpm.awpm_destroy(tctx)
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(g) if world == 1 else None
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * awpm.h -- C ABI of the GB300 library for the weight-increasing alternating
+ * 4-cycle phase of heavy-weight perfect matching (Azad, Buluc, Li, Wang and
+ * Langguth, "A distributed-memory algorithm for computing a heavy-weight
+ * perfect matching on bipartite graphs", arXiv 1801.09809).
+ *
+ * Given a perfect matching M of a weighted bipartite graph (rows and columns of
+ * a sparse n x n matrix), the phase repeatedly finds vertex-disjoint
+ * alternating 4-cycles of positive gain and flips M along them, until a pass
+ * finds none (Section 5.3, Algorithms 2-6).  The gain of the cycle through
+ * column j, row i, and their mates m_j (a row) and m_i (a column) is
+ *     g(i, j, m_j, m_i) = w(i,j) + w(m_j,m_i) - w(i,m_i) - w(m_j,j)   (Section 3)
+ * evaluated left to right in IEEE double precision.
+ *
+ * Data conventions (all entry points):
+ *   - n: number of rows = number of columns, 0 <= n < 2^31.
+ *   - colptr[n+1] int32, rowidx[nnz] int32, weight[nnz] double: the matrix in
+ *     compressed sparse column form, nnz = colptr[n] < 2^31, colptr[0] = 0,
+ *     colptr non-decreasing, rows strictly increasing inside each column,
+ *     every weight finite.  The library never modifies them.
+ *   - mate_in[n] int32: the matching, mate_in[j] = row matched to column j.
+ *     It must be a permutation of 0..n-1 and every (mate_in[j], j) must be a
+ *     stored entry.  mate_out[n] int32 receives the result in the same
+ *     convention; it may alias mate_in.
+ *   - Each array pointer may be host memory (pageable or pinned) or device
+ *     memory of the context's GPU; the library tells them apart with
+ *     cudaPointerGetAttributes.  Host arrays are copied in (and mate_out out);
+ *     device arrays are read (or written) in place and are borrowed only
+ *     until the call returns.  The caller owns every array; the library never
+ *     frees caller memory.
+ *   - Every step of the computation (input validation included) runs in CUDA
+ *     kernels on the GPU.  There is no CPU fallback: without a usable GPU the
+ *     calls return AWPM_ERR_CUDA.
+ *
+ * Error behaviour: every entry point returns an int, AWPM_OK (0) on success or
+ * one of the AWPM_ERR_* codes; outputs are unspecified after an error.  When
+ * an input breaks several rules, the first class in this order is reported:
+ * INVALID_ARG, UNSORTED_OR_DUP, NONFINITE, NOT_PERFECT.  Reaching max_iters is
+ * not an error (stats.converged = 0).
+ *
+ * Thread safety: a context serialises its own calls with a mutex; distinct
+ * contexts may be used from different threads.
+ */
+#ifndef AWPM_H
+#define AWPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AWPM_OK 0
+#define AWPM_ERR_INVALID_ARG 1     /* bad n / pointer / colptr / row index / option   */
+#define AWPM_ERR_NOT_PERFECT 2     /* mate_in not a perfect matching of stored entries */
+#define AWPM_ERR_UNSORTED_OR_DUP 3 /* rows not strictly increasing within a column    */
+#define AWPM_ERR_NONFINITE 4       /* a weight is NaN or infinite                     */
+#define AWPM_ERR_OOM 5             /* device or pinned host allocation failed         */
+#define AWPM_ERR_BUDGET 6          /* the context's device-memory budget is exceeded  */
+#define AWPM_ERR_CUDA 7            /* a CUDA call failed (message: awpm_last_error)   */
+#define AWPM_ERR_TIMEOUT 8         /* a bounded device-side wait gave up              */
+#define AWPM_ERR_NOT_FOUND 9       /* unknown ticket                                  */
+
+/* Closing-edge lookup strategy of the cycle search (Step B). */
+#define AWPM_LOOKUP_AUTO 0    /* the library picks (per matrix)                         */
+#define AWPM_LOOKUP_BSEARCH 1 /* binary search in the sorted rows of column m_i         */
+#define AWPM_LOOKUP_HASH 2    /* per-column open-addressing table built once per solve  */
+
+/* awpm_options.flags */
+#define AWPM_FLAG_TIME_SEARCH 1u /* time every cycle-search launch with CUDA events
+                                    (host-driven pass loop instead of one CUDA graph) */
+
+/* Passes run when max_iters = 0 ("until a pass finds nothing") are capped here. */
+#define AWPM_PASS_CAP 65536
+
+typedef struct awpm_ctx awpm_ctx;
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal; -1 = the current device       */
+    int32_t max_iters;         /* at most this many passes; 0 = until none is found  */
+    int32_t lookup;            /* AWPM_LOOKUP_*                                      */
+    uint32_t flags;            /* AWPM_FLAG_*                                        */
+    void *stream;              /* cudaStream_t to run on; NULL = a stream the context
+                                  creates and owns                                   */
+    size_t mem_budget_bytes;   /* device bytes the context may hold; 0 = unlimited   */
+} awpm_options;
+
+typedef struct {
+    int32_t iterations;      /* passes of Steps A-D run, the last empty one included  */
+    int32_t converged;       /* 1 if the last pass found no weight-increasing cycle   */
+    int64_t cycles_applied;  /* 4-cycles flipped in total                              */
+    int64_t edge_checks;     /* (nnz - n) * iterations: non-matching entries examined  */
+    int64_t candidates;      /* entries (i, j) with i > m_j examined (Step A requests) */
+    int64_t closing_found;   /* candidates whose closing edge {m_j, m_i} exists        */
+    int64_t positive;        /* of those, gain > 0 (Step B requests)                   */
+    double weight_in;        /* sum of matched weights before / after                  */
+    double weight_out;       /*   (device reduction; order differs from a serial sum) */
+    double ms_total;         /* wall time of the call on the stream (CUDA events)      */
+    double ms_search;        /* summed cycle-search kernel time, only with
+                                AWPM_FLAG_TIME_SEARCH (else 0)                         */
+    int32_t lookup_used;     /* AWPM_LOOKUP_BSEARCH or AWPM_LOOKUP_HASH                */
+    int32_t reserved;
+} awpm_stats;
+
+/* Message of an error code (static string). */
+const char *awpm_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread (static per thread). */
+const char *awpm_last_error(void);
+
+/* Fill *opt with defaults: device -1, max_iters 0, lookup AUTO, no flags,
+ * NULL stream, no budget. */
+void awpm_default_options(awpm_options *opt);
+
+/*
+ * Create a context on opt->device (opt may be NULL: defaults).  The context
+ * owns its device workspace (grown on demand, kept between calls, bounded by
+ * mem_budget_bytes), its CUDA graphs and, unless opt->stream is given, its
+ * stream.  Errors: INVALID_ARG (out == NULL, bad option), CUDA.
+ */
+int awpm_create(awpm_ctx **out, const awpm_options *opt);
+
+/* Free everything the context owns.  NULL is accepted. */
+int awpm_destroy(awpm_ctx *ctx);
+
+/*
+ * The whole phase (Algorithm 2): validate the inputs, initialise mates and
+ * matched weights, then run passes of
+ *   Step A+B (Algorithms 3-4): every stored (i, j) with i > m_j looks up the
+ *            closing edge {m_j, m_i} and computes the gain;
+ *   Step C   (Algorithm 5): per root column j keep the maximum positive gain,
+ *            equal gains to the lowest row i;
+ *   Step D   (Algorithm 6): drop a winner whose second matched edge {i, m_i}
+ *            is the root edge of another Step-C winner; per matched edge
+ *            {i, m_i} keep the maximum gain, equal gains to the lowest root j;
+ *            flip the survivors;
+ * until a pass flips nothing or max_iters passes ran.  The pass loop runs on
+ * the device (a CUDA graph with a conditional while node); the host
+ * synchronises once, at the end, to read the statistics.
+ * Uses the calling thread's default context on the current device (created on
+ * first use, default options).  stats may be NULL.
+ */
+int awpm_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *weight,
+                 const int32_t *mate_in, int32_t *mate_out, awpm_stats *stats);
+
+/* awpm_improve on an explicit context (its device, stream, options). */
+int awpm_improve_ctx(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                     const double *weight, const int32_t *mate_in, int32_t *mate_out,
+                     awpm_stats *stats);
+
+/*
+ * One cycle search from a given matching without flipping anything: Steps
+ * A-C of a single pass (Algorithms 3-5).  For every column j,
+ * stepc_gain[j] / stepc_row[j] receive the Step-C winner rooted at j (its gain
+ * and row i), or 0.0 / -1 when j has no positive-gain 4-cycle.  stepc_gain
+ * and stepc_row are n-element host or device arrays.  stats (may be NULL)
+ * receives candidates, closing_found and positive of this search.
+ */
+int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                const double *weight, const int32_t *mate, double *stepc_gain,
+                int32_t *stepc_row, awpm_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AWPM_H */

@@ -1,0 +1,175 @@
+"""Python binding of libawpm (ctypes): argument marshalling only.
+
+Same names and argument order as the C ABI in include/awpm.h.  Arrays may be
+numpy arrays (host) or torch tensors (host or CUDA); the library tells host and
+device memory apart itself.  Every computation runs in the CUDA library; if
+it is not built this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libawpm.so")
+
+AWPM_OK = 0
+ERRORS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_PERFECT", 3: "UNSORTED_OR_DUP", 4: "NONFINITE",
+          5: "OOM", 6: "BUDGET", 7: "CUDA", 8: "TIMEOUT", 9: "NOT_FOUND"}
+LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_HASH = 0, 1, 2
+FLAG_TIME_SEARCH = 1
+PASS_CAP = 65536
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("lookup", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("stream", ctypes.c_void_p), ("mem_budget_bytes", ctypes.c_size_t)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("cycles_applied", ctypes.c_int64), ("edge_checks", ctypes.c_int64),
+                ("candidates", ctypes.c_int64), ("closing_found", ctypes.c_int64),
+                ("positive", ctypes.c_int64), ("weight_in", ctypes.c_double),
+                ("weight_out", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_search", ctypes.c_double), ("lookup_used", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class AwpmError(RuntimeError):
+    def __init__(self, code: int, detail: str = ""):
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+        super().__init__(f"awpm error {self.name}" + (f": {detail}" if detail else ""))
+
+
+_lib_handle = None
+
+# (name, restype, argtypes) of every exported entry point
+_VP = ctypes.c_void_p
+SIGNATURES = [
+    ("awpm_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("awpm_last_error", ctypes.c_char_p, []),
+    ("awpm_default_options", None, [ctypes.POINTER(Options)]),
+    ("awpm_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(Options)]),
+    ("awpm_destroy", ctypes.c_int, [_VP]),
+    ("awpm_improve", ctypes.c_int, [ctypes.c_int32, _VP, _VP, _VP, _VP, _VP,
+                                    ctypes.POINTER(Stats)]),
+    ("awpm_improve_ctx", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP,
+                                        ctypes.POINTER(Stats)]),
+    ("awpm_search", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP,
+                                   ctypes.POINTER(Stats)]),
+]
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_1801_09809_gb300.build.build() (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib_handle = L
+    return _lib_handle
+
+
+def _check(rc: int):
+    if rc != AWPM_OK:
+        detail = ""
+        if ERRORS.get(rc) in ("CUDA", "OOM"):
+            detail = (lib().awpm_last_error() or b"").decode()
+        raise AwpmError(rc, detail)
+
+
+_DT = {"int32": (np.int32, "torch.int32"), "float64": (np.float64, "torch.float64")}
+
+
+def _ptr(a, kind: str):
+    """Address of a C-contiguous numpy array or torch tensor of the given kind."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != _DT[kind][0] or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {kind} array")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype) != _DT[kind][1] or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {kind} tensor")
+        return a.data_ptr()
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream or None
+    return int(stream) or None
+
+
+class Context:
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __repr__(self):
+        return f"<awpm_ctx 0x{self.handle:x}>"
+
+
+def awpm_create(device: int = -1, max_iters: int = 0, lookup: int = LOOKUP_AUTO,
+                flags: int = 0, stream=None, mem_budget_bytes: int = 0) -> Context:
+    L = lib()
+    o = Options()
+    L.awpm_default_options(ctypes.byref(o))
+    o.device, o.max_iters, o.lookup, o.flags = device, max_iters, lookup, flags
+    o.stream = _stream_handle(stream)
+    o.mem_budget_bytes = mem_budget_bytes
+    h = _VP()
+    _check(L.awpm_create(ctypes.byref(h), ctypes.byref(o)))
+    return Context(h.value)
+
+
+def awpm_destroy(ctx: Context) -> None:
+    if ctx is not None and ctx.handle:
+        _check(lib().awpm_destroy(ctx.handle))
+        ctx.handle = 0
+
+
+def awpm_improve(n, colptr, rowidx, weight, mate_in, mate_out) -> dict:
+    st = Stats()
+    _check(lib().awpm_improve(int(n), _ptr(colptr, "int32"), _ptr(rowidx, "int32"),
+                              _ptr(weight, "float64"), _ptr(mate_in, "int32"),
+                              _ptr(mate_out, "int32"), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def awpm_improve_ctx(ctx: Context, n, colptr, rowidx, weight, mate_in, mate_out) -> dict:
+    st = Stats()
+    _check(lib().awpm_improve_ctx(ctx.handle, int(n), _ptr(colptr, "int32"),
+                                  _ptr(rowidx, "int32"), _ptr(weight, "float64"),
+                                  _ptr(mate_in, "int32"), _ptr(mate_out, "int32"),
+                                  ctypes.byref(st)))
+    return st.as_dict()
+
+
+def awpm_search(ctx: Context, n, colptr, rowidx, weight, mate, stepc_gain, stepc_row) -> dict:
+    st = Stats()
+    _check(lib().awpm_search(ctx.handle, int(n), _ptr(colptr, "int32"), _ptr(rowidx, "int32"),
+                             _ptr(weight, "float64"), _ptr(mate, "int32"),
+                             _ptr(stepc_gain, "float64"), _ptr(stepc_row, "int32"),
+                             ctypes.byref(st)))
+    return st.as_dict()
+
+
+def awpm_strerror(code: int) -> str:
+    return lib().awpm_strerror(code).decode()

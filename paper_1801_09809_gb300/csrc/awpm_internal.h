@@ -1,0 +1,85 @@
+// Internal declarations shared by the kernels and the host API of libawpm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace awpm {
+
+// Nonzeros handled by one warp per tile of the edge-parallel kernels.
+constexpr int kTile = 32;
+
+// Error bits raised by the device-side validation; the host maps the lowest
+// set bit to the public code (priority INVALID > UNSORTED > NONFINITE > NOTPERF).
+constexpr unsigned kErrInvalid = 1u;
+constexpr unsigned kErrUnsorted = 2u;
+constexpr unsigned kErrNonfinite = 4u;
+constexpr unsigned kErrNotPerfect = 8u;
+constexpr unsigned kErrInternal = 16u;  // a bounded retry loop gave up
+
+// Step-C record of a root column j (Algorithm 5): best positive gain, the
+// position p of (i, j) in column j and the position q of the closing entry
+// (m_j, m_i) in column m_i.  g == 0 means "no cycle".
+struct alignas(16) Rec {
+    double g;
+    int32_t p;
+    int32_t q;
+};
+
+// Step-D selection at a key column k (Algorithm 6): best gain and its root j.
+struct alignas(16) Sel {
+    double g;
+    int32_t j;
+    int32_t pad;
+};
+
+// Device-resident control block of one solve.
+struct Ctl {
+    unsigned int err;            // kErr* bits
+    int32_t active;              // 1 while the pass loop continues
+    int32_t iterations;          // passes run
+    int32_t converged;           // last pass flipped nothing
+    int32_t max_passes;          // cap on passes
+    int32_t pad0;
+    unsigned long long pass_flips;   // cycles flipped in the running pass
+    unsigned long long cycles;       // cycles flipped in total
+    unsigned long long candidates;   // Step A requests (i > m_j)
+    unsigned long long found;        // closing edge present
+    unsigned long long positive;     // closing edge present and g > 0
+    double weight_in;
+    double weight_out;
+};
+
+// Device pointers of one solve.
+struct Work {
+    int32_t n;
+    int32_t nnz;
+    int32_t ntiles;
+    const int32_t *colptr;
+    const int32_t *rowidx;
+    const double *w;
+    const int32_t *mate_in;
+    int32_t *mc;        // row matched to column j
+    int32_t *mr;        // column matched to row i
+    double *wm;         // w(mc[j], j)
+    Rec *best;          // Step-C records
+    Sel *dsel;          // Step-D selections
+    int32_t *tile_col;  // column holding the first nonzero of each tile
+    uint32_t *starts;   // bit p set when a column starts at nonzero p
+    Ctl *ctl;
+    double *wpart;      // partial sums of the weight reduction
+};
+
+constexpr int kWsumBlocks = 256;
+constexpr int kWsumThreads = 256;
+
+// Launchers (all asynchronous on `s`).  `num_sms` sizes persistent grids.
+void launch_init(const Work &wk, int max_passes, int num_sms, cudaStream_t s);
+void launch_weight_sum(const Work &wk, bool out, cudaStream_t s);
+void launch_search(const Work &wk, int lookup, int num_sms, cudaStream_t s);
+void launch_select_and_flip(const Work &wk, int num_sms, cudaStream_t s);
+void launch_control(const Work &wk, bool graph, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_export_stepc(const Work &wk, double *gain, int32_t *row, cudaStream_t s);
+void launch_reset_best(const Work &wk, cudaStream_t s);
+
+}  // namespace awpm
