@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "stencil3d", "stencil2d"])
+    ap.add_argument("--workload", default="rmat",
+                    choices=["rmat", "stencil3d", "stencil2d", "rmat20"])
     return ap.parse_args()
 
 
@@ -54,6 +55,10 @@ def workload(name):
         desc = ("R-MAT n=4,194,304 (scale 22), 16n samples a=.57 b=c=.19 d=.05 deduplicated, "
                 "rows/cols randomly relabelled, planted random perfect matching, "
                 "log-normal weights with per-column log transform")
+    elif name == "rmat20":
+        g = gen.rmat(1 << 20, 16, gen.SEED_BASE + 40, name="rmat_s20_ef16")
+        desc = ("R-MAT n=1,048,576 (scale 20), 16n samples, same recipe as the scale-22 graph "
+                "(profiling case: CSC 200 MB > L2)")
     elif name == "stencil3d":
         g = gen.config3a()
         desc = "3D 27-point stencil 96^3, random row+col permutations, log-normal weights"
