@@ -61,6 +61,7 @@ extern "C" {
 #define AWPM_ERR_CUDA 7            /* a CUDA call failed (message: awpm_last_error)   */
 #define AWPM_ERR_TIMEOUT 8         /* a bounded device-side wait gave up              */
 #define AWPM_ERR_NOT_FOUND 9       /* unknown ticket                                  */
+#define AWPM_ERR_TOO_LARGE 10      /* problem exceeds awpm_search_noalloc's scratch   */
 
 /* Closing-edge lookup strategy of the cycle search (Step B). */
 #define AWPM_LOOKUP_AUTO 0    /* the library picks (per matrix)                         */
@@ -160,6 +161,43 @@ int awpm_improve_ctx(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int3
 int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
                 const double *weight, const int32_t *mate, double *stepc_gain,
                 int32_t *stepc_row, awpm_stats *stats);
+
+/*
+ * Size limits of awpm_search_noalloc (its scratch is a fixed array of about
+ * 9 MB in device memory, held by every GPU that loads the library).
+ */
+#define AWPM_NOALLOC_MAX_N 262144
+#define AWPM_NOALLOC_MAX_NNZ 4194304
+
+/*
+ * awpm_search without any memory allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- for
+ * example a host framework whose memory pool has already reserved the GPU's
+ * memory, or code running where an allocation (which can synchronise the
+ * device) is not allowed.  It computes exactly what awpm_search computes
+ * (Step-C winner gain and row per column, and the request counters in stats)
+ * but allocates nothing: no cudaMalloc, no cudaFree, no pinned buffers, no
+ * allocating library routine.  Its scratch is one fixed __device__ array of
+ * about 9 MB inside the library, which every GPU that loads the library holds
+ * until the process exits.
+ *   - n <= AWPM_NOALLOC_MAX_N and nnz <= AWPM_NOALLOC_MAX_NNZ, otherwise
+ *     AWPM_ERR_TOO_LARGE.
+ *   - colptr, rowidx, weight, mate, stepc_gain and stepc_row must be device
+ *     memory of the current device (AWPM_ERR_INVALID_ARG otherwise); the
+ *     caller owns them.  stream is a cudaStream_t (NULL = the default stream);
+ *     the call waits on it before returning.  stats may be NULL (host).
+ *   - The first call on a device looks up the device address of the scratch
+ *     array (once per device, with that device current); make that first
+ *     call before any stream capture on the device.
+ *   - Every call on a device shares the one scratch array, which keeps the
+ *     contents of the last call; each call clears what must start at zero.
+ *     Calls whose work overlaps on the GPU (other threads, other streams)
+ *     race on the array: serialise them.
+ * Errors as awpm_search, plus AWPM_ERR_TOO_LARGE.
+ */
+int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                        const double *weight, const int32_t *mate, double *stepc_gain,
+                        int32_t *stepc_row, void *stream, awpm_stats *stats);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libawpm.so")
 
 AWPM_OK = 0
 ERRORS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_PERFECT", 3: "UNSORTED_OR_DUP", 4: "NONFINITE",
-          5: "OOM", 6: "BUDGET", 7: "CUDA", 8: "TIMEOUT", 9: "NOT_FOUND"}
+          5: "OOM", 6: "BUDGET", 7: "CUDA", 8: "TIMEOUT", 9: "NOT_FOUND", 10: "TOO_LARGE"}
 LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_HASH = 0, 1, 2
 FLAG_TIME_SEARCH = 1
 PASS_CAP = 65536
@@ -65,7 +65,11 @@ SIGNATURES = [
                                         ctypes.POINTER(Stats)]),
     ("awpm_search", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP,
                                    ctypes.POINTER(Stats)]),
+    ("awpm_search_noalloc", ctypes.c_int, [ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                           ctypes.POINTER(Stats)]),
 ]
+NOALLOC_MAX_N = 262144
+NOALLOC_MAX_NNZ = 4194304
 
 
 def lib():
@@ -168,6 +172,19 @@ def awpm_search(ctx: Context, n, colptr, rowidx, weight, mate, stepc_gain, stepc
                              _ptr(weight, "float64"), _ptr(mate, "int32"),
                              _ptr(stepc_gain, "float64"), _ptr(stepc_row, "int32"),
                              ctypes.byref(st)))
+    return st.as_dict()
+
+
+def awpm_search_noalloc(n, colptr, rowidx, weight, mate, stepc_gain, stepc_row,
+                        stream=None) -> dict:
+    """awpm_search for callers that cannot allocate device memory: device
+    arrays only, n <= NOALLOC_MAX_N, nnz <= NOALLOC_MAX_NNZ; scratch is a fixed
+    array inside the library shared by all calls on a device."""
+    st = Stats()
+    _check(lib().awpm_search_noalloc(int(n), _ptr(colptr, "int32"), _ptr(rowidx, "int32"),
+                                     _ptr(weight, "float64"), _ptr(mate, "int32"),
+                                     _ptr(stepc_gain, "float64"), _ptr(stepc_row, "int32"),
+                                     _stream_handle(stream), ctypes.byref(st)))
     return st.as_dict()
 
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libawpm.so")
-SOURCES = ["awpm_kernels.cu", "awpm_api.cu"]
+SOURCES = ["awpm_kernels.cu", "awpm_api.cu", "awpm_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "awpm_internal.h"), os.path.join(INCLUDE, "awpm.h")]
 
 NVCC = os.environ.get("NVCC", "nvcc")
