@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="rmat",
-                    choices=["rmat", "stencil3d", "stencil2d", "rmat20"])
+                    choices=["rmat", "stencil3d", "stencil2d", "rmat20", "rmat21"])
     return ap.parse_args()
 
 
@@ -59,6 +59,10 @@ def workload(name):
         g = gen.rmat(1 << 20, 16, gen.SEED_BASE + 40, name="rmat_s20_ef16")
         desc = ("R-MAT n=1,048,576 (scale 20), 16n samples, same recipe as the scale-22 graph "
                 "(profiling case: CSC 200 MB > L2)")
+    elif name == "rmat21":
+        g = gen.rmat(1 << 21, 16, gen.SEED_BASE + 41, name="rmat_s21_ef16")
+        desc = ("R-MAT n=2,097,152 (scale 21), 16n samples, same recipe as the scale-22 graph "
+                "(profiling case: row indices 136 MB > L2)")
     elif name == "stencil3d":
         g = gen.config3a()
         desc = "3D 27-point stencil 96^3, random row+col permutations, log-normal weights"

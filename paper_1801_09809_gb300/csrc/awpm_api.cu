@@ -74,7 +74,9 @@ struct awpm_ctx {
     bool own_stream = false;
     size_t held = 0;
     // workspace
-    DevBuf mc, mr, wm, best, dsel, tile_col, starts, ctl, wpart;
+    DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart;
+    int search_u = 1;
+    int search_bps = 1;
     // staging of host-resident arrays
     DevBuf s_colptr, s_rowidx, s_w, s_mate, s_gain, s_row;
     Ctl *h_ctl = nullptr;       // pinned
@@ -328,6 +330,8 @@ int setup_ctx(awpm_ctx *c, const awpm_options *opt)
     c->device = dev;
     CUDA_TRY(cudaSetDevice(dev));
     CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    c->search_u = default_search_u();
+    c->search_bps = search_blocks_per_sm(c->search_u);
     if (c->opt.stream) {
         c->stream = (cudaStream_t)c->opt.stream;
         c->own_stream = false;
@@ -352,7 +356,8 @@ void teardown_ctx(awpm_ctx *c)
     if (c->stream)
         cudaStreamSynchronize(c->stream);
     drop_graph(c);
-    DevBuf *bufs[] = {&c->mc, &c->mr, &c->wm, &c->best, &c->dsel, &c->tile_col, &c->starts,
+    DevBuf *bufs[] = {&c->mc, &c->mr, &c->wm, &c->rr, &c->wmr, &c->colsig, &c->best, &c->dsel,
+                      &c->tile_col, &c->starts,
                       &c->ctl, &c->wpart, &c->s_colptr, &c->s_rowidx, &c->s_w, &c->s_mate,
                       &c->s_gain, &c->s_row};
     for (DevBuf *b : bufs)
@@ -435,6 +440,9 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     AWPM_TRY(ensure(c, c->mc, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->mr, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->wm, sizeof(double) * n));
+    AWPM_TRY(ensure(c, c->rr, sizeof(RowRec) * n));
+    AWPM_TRY(ensure(c, c->wmr, sizeof(double) * n));
+    AWPM_TRY(ensure(c, c->colsig, sizeof(unsigned long long) * n));
     AWPM_TRY(ensure(c, c->best, sizeof(Rec) * n));
     AWPM_TRY(ensure(c, c->dsel, sizeof(Sel) * n));
     AWPM_TRY(ensure(c, c->tile_col, sizeof(int32_t) * ((size_t)ntiles + 1)));
@@ -447,6 +455,8 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     wk.n = n;
     wk.nnz = nnz;
     wk.ntiles = ntiles;
+    wk.search_u = c->search_u;
+    wk.search_bps = c->search_bps;
     AWPM_TRY(stage_in(c, c->s_colptr, colptr, (size_t)n + 1, l_colptr, &wk.colptr));
     AWPM_TRY(stage_in(c, c->s_rowidx, rowidx, (size_t)nnz, l_rowidx, &wk.rowidx));
     AWPM_TRY(stage_in(c, c->s_w, weight, (size_t)nnz, l_w, &wk.w));
@@ -454,6 +464,9 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     wk.mc = (int32_t *)c->mc.p;
     wk.mr = (int32_t *)c->mr.p;
     wk.wm = (double *)c->wm.p;
+    wk.rr = (RowRec *)c->rr.p;
+    wk.wmr = (double *)c->wmr.p;
+    wk.colsig = (unsigned long long *)c->colsig.p;
     wk.best = (Rec *)c->best.p;
     wk.dsel = (Sel *)c->dsel.p;
     wk.tile_col = (int32_t *)c->tile_col.p;

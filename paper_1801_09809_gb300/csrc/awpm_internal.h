@@ -26,6 +26,17 @@ struct alignas(16) Rec {
     int32_t q;
 };
 
+// Per-row view of the column matched to row i (m_i): where its rows sit in
+// the CSC arrays and a 64-bit signature of those rows (bit sig_bit(r) set for
+// every stored row r).  A clear bit proves that the closing entry (m_j, m_i)
+// is absent without touching the column; the record is rewritten whenever
+// row i changes mate.
+struct alignas(16) RowRec {
+    int32_t s;
+    int32_t e;
+    unsigned long long sig;
+};
+
 // Step-D selection at a key column k (Algorithm 6): best gain and its root j.
 struct alignas(16) Sel {
     double g;
@@ -55,6 +66,8 @@ struct Work {
     int32_t n;
     int32_t nnz;
     int32_t ntiles;
+    int32_t search_u;    // tiles in flight per warp in the search kernel (1, 2, 4)
+    int32_t search_bps;  // resident blocks per SM of that search kernel
     const int32_t *colptr;
     const int32_t *rowidx;
     const double *w;
@@ -62,6 +75,9 @@ struct Work {
     int32_t *mc;        // row matched to column j
     int32_t *mr;        // column matched to row i
     double *wm;         // w(mc[j], j)
+    RowRec *rr;         // per row i: rows of column mr[i] (range + signature)
+    double *wmr;        // per row i: wm[mr[i]] = w(i, mr[i])
+    unsigned long long *colsig;  // per column: signature of its rows
     Rec *best;          // Step-C records
     Sel *dsel;          // Step-D selections
     int32_t *tile_col;  // column holding the first nonzero of each tile
@@ -81,5 +97,11 @@ void launch_select_and_flip(const Work &wk, int num_sms, cudaStream_t s);
 void launch_control(const Work &wk, bool graph, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_export_stepc(const Work &wk, double *gain, int32_t *row, cudaStream_t s);
 void launch_reset_best(const Work &wk, cudaStream_t s);
+// Resident blocks per SM of the search kernel with u tiles in flight per
+// warp (for a one-wave grid).
+int search_blocks_per_sm(int u);
+// Default tiles in flight per warp; the environment variable AWPM_SEARCH_U
+// (1, 2 or 4) overrides it, as a tuning knob.
+int default_search_u();
 
 }  // namespace awpm

@@ -8,7 +8,9 @@
 // columns that straddle a tile boundary, and Step D is one compare-and-swap
 // selection per key column followed by an in-place flip.
 #include <math.h>
+#include <stdlib.h>
 
+#include "awpm.h"
 #include "awpm_internal.h"
 
 namespace awpm {
@@ -212,6 +214,91 @@ __global__ void k_wsum_final(const double *__restrict__ part, Ctl *ctl, int out)
 }
 
 // ---------------------------------------------------------------------------
+// Row records (range + signature of the column matched to each row)
+// ---------------------------------------------------------------------------
+
+// Bit of row r in a column signature (multiplicative hash, top 6 bits).
+__device__ __forceinline__ unsigned sig_bit(int32_t r)
+{
+    return ((uint32_t)r * 0x9E3779B1u) >> 26;
+}
+
+// Column of the lane's nonzero inside a tile of kTile consecutive nonzeros
+// starting in column c0: the lane counts the column ends <= p among the 32
+// ends colptr[c0+1 .. c0+32] held one per lane in `e` (a tile spans at most
+// 32 columns when no column is empty).
+__device__ __forceinline__ int32_t lane_column_offset(int32_t e, int32_t p)
+{
+    int32_t cnt = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        int32_t v = __shfl_sync(FULL_MASK, e, cnt + s - 1);
+        if (v <= p)
+            cnt += s;
+    }
+    int32_t v = __shfl_sync(FULL_MASK, e, cnt);
+    if (v <= p)
+        cnt += 1;
+    return cnt;
+}
+
+// Signature of every column: OR of 1 << sig_bit(r) over its rows.  Edge
+// parallel; lanes of one column are OR-ed inside the warp, then one atomic
+// per column segment.  colsig must be zero on entry.
+__global__ void __launch_bounds__(256)
+k_colsig(int32_t n, int32_t nnz, int32_t ntiles, const int32_t *__restrict__ colptr,
+         const int32_t *__restrict__ rowidx, const int32_t *__restrict__ tile_col,
+         unsigned long long *colsig, const Ctl *ctl)
+{
+    if (ctl->err)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp0; t < ntiles; t += nwarps) {
+        const int32_t base = (int32_t)(t * kTile);
+        const int32_t p = base + lane;
+        const bool valid = p < nnz;
+        const int32_t c0 = tile_col[t];
+        const int64_t ck = (int64_t)c0 + 1 + lane;
+        const int32_t e = (ck <= n) ? colptr[ck] : 0x7fffffff;
+        const int32_t cnt = lane_column_offset(e, p);
+        const int32_t j = valid ? c0 + cnt : -1 - lane;
+        unsigned long long v = valid ? (1ull << sig_bit(__ldcs(rowidx + p))) : 0ull;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long ov = __shfl_down_sync(FULL_MASK, v, off);
+            const int32_t oj = __shfl_down_sync(FULL_MASK, j, off);
+            if (lane + off < 32 && oj == j)
+                v |= ov;
+        }
+        const int32_t jprev = __shfl_up_sync(FULL_MASK, j, 1);
+        if (valid && (lane == 0 || jprev != j))
+            atomicOr(colsig + j, v);
+    }
+}
+
+// rr[r] and wmr[r] for the row r matched to column j.
+__global__ void k_init_rows(int32_t n, const int32_t *__restrict__ colptr,
+                            const int32_t *__restrict__ mc, const double *__restrict__ wm,
+                            const unsigned long long *__restrict__ colsig, RowRec *rr, double *wmr,
+                            const Ctl *ctl)
+{
+    if (ctl->err)
+        return;
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n)
+        return;
+    const int32_t r = mc[j];
+    RowRec x;
+    x.s = colptr[j];
+    x.e = colptr[j + 1];
+    x.sig = colsig[j];
+    rr[r] = x;
+    wmr[r] = wm[j];
+}
+
+// ---------------------------------------------------------------------------
 // Steps A + B + C (Algorithms 3, 4, 5): fused edge-parallel cycle search
 // ---------------------------------------------------------------------------
 
@@ -236,19 +323,52 @@ __device__ void rec_combine(Rec *addr, Rec mine, Ctl *ctl)
     raise_err(ctl, kErrInternal);
 }
 
-// One warp per tile of kTile consecutive nonzeros (lane = one nonzero).
+__device__ __forceinline__ unsigned long long policy_evict_last()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// 16-byte row record through the read-only path, kept in L2 (evict last).
+__device__ __forceinline__ RowRec ld_rowrec(const RowRec *ptr, unsigned long long pol)
+{
+    uint32_t a, b, c, d;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+                 : "l"(ptr), "l"(pol));
+    RowRec r;
+    r.s = (int32_t)a;
+    r.e = (int32_t)b;
+    r.sig = ((unsigned long long)d << 32) | c;
+    return r;
+}
+
+__device__ __forceinline__ int32_t ld_i32_last(const int32_t *ptr, unsigned long long pol)
+{
+    int32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+// One warp per tile of kTile consecutive nonzeros (lane = one nonzero), kU
+// tiles in flight per warp with their independent loads issued together.
 // Lane with nonzero p = (i, j): if i > m_j it is an A-request (Algorithm 3);
-// the closing entry (m_j, m_i) is looked up in column m_i (Algorithm 4) and
-// the gain evaluated in the fixed order ((w_ij + w_q) - w(i,m_i)) - w(m_j,j).
-// The warp then keeps, per column, the maximum positive gain with the lowest
-// row (Algorithm 5).
-template <int kLookup>
+// the closing entry (m_j, m_i) is looked up in column m_i (Algorithm 4): the
+// row record of i gives that column's range and signature, so a clear
+// signature bit settles "absent" at once, otherwise a binary search over the
+// column's rows finds it.  The gain is evaluated in the fixed order
+// ((w_ij + w_q) - w(i,m_i)) - w(m_j,j).  Per column the warp keeps the
+// maximum positive gain with the lowest row (Algorithm 5); columns cut by a
+// tile boundary are merged across warps by a 128-bit compare-and-swap.
+// `best` must be zero on entry: only positive records are written.
+template <int kLookup, int kU>
 __global__ void __launch_bounds__(256)
 k_search(int32_t n, int32_t nnz, int32_t ntiles, const int32_t *__restrict__ colptr,
          const int32_t *__restrict__ rowidx, const double *__restrict__ w,
          const int32_t *__restrict__ tile_col, const int32_t *__restrict__ mc,
-         const int32_t *__restrict__ mr, const double *__restrict__ wm, Rec *__restrict__ best,
-         Ctl *ctl)
+         const double *__restrict__ wm, const RowRec *__restrict__ rr,
+         const double *__restrict__ wmr, Rec *__restrict__ best, Ctl *ctl)
 {
     __shared__ int s_go;
     if (threadIdx.x == 0)
@@ -257,85 +377,136 @@ k_search(int32_t n, int32_t nnz, int32_t ntiles, const int32_t *__restrict__ col
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long pol = policy_evict_last();
     unsigned long long n_cand = 0, n_found = 0, n_pos = 0;
 
-    for (int64_t t = s_go ? warp0 : (int64_t)ntiles; t < ntiles; t += nwarps) {
-        const int32_t base = (int32_t)(t * kTile);
-        const int32_t p = base + lane;
-        const bool valid = p < nnz;
-        const int32_t c0 = __ldg(tile_col + t);
-        // ends of columns c0 .. c0+31; a tile spans at most 32 columns because
-        // every column holds at least its matched entry
-        const int64_t ck = (int64_t)c0 + 1 + lane;
-        const int32_t e = (ck <= n) ? __ldg(colptr + ck) : 0x7fffffff;
-        int32_t cnt = 0;
+    for (int64_t t0 = s_go ? warp0 : (int64_t)ntiles; t0 < ntiles; t0 += nwarps * kU) {
+        int32_t base[kU], p[kU], c0[kU], e[kU], c0s[kU], i[kU];
+        bool tv[kU], valid[kU];
 #pragma unroll
-        for (int s = 16; s >= 1; s >>= 1) {
-            int32_t v = __shfl_sync(FULL_MASK, e, cnt + s - 1);
-            if (v <= p)
-                cnt += s;
+        for (int u = 0; u < kU; ++u) {
+            const int64_t t = t0 + (int64_t)u * nwarps;
+            tv[u] = t < ntiles;
+            base[u] = (int32_t)(t * kTile);
+            p[u] = base[u] + lane;
+            valid[u] = tv[u] && p[u] < nnz;
+            c0[u] = tv[u] ? __ldg(tile_col + t) : 0;
         }
-        {
-            int32_t v = __shfl_sync(FULL_MASK, e, cnt);
-            if (v <= p)
-                cnt += 1;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t ck = (int64_t)c0[u] + 1 + lane;
+            e[u] = (tv[u] && ck <= n) ? __ldg(colptr + ck) : 0x7fffffff;
+            c0s[u] = tv[u] ? __ldg(colptr + c0[u]) : 0;
+            i[u] = valid[u] ? __ldcs(rowidx + p[u]) : 0;
         }
-        const int32_t colend = __shfl_sync(FULL_MASK, e, cnt & 31);
-        const int32_t c0start = __ldg(colptr + c0);
-        const int32_t j = valid ? c0 + cnt : -1 - lane;
-
-        double g = 0.0;
-        int32_t q = -1;
-        if (valid) {
-            const int32_t i = __ldcs(rowidx + p);
-            const int32_t mj = __ldg(mc + j);
-            if (i > mj) {
+        int32_t j[kU], colend[kU], mj[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int32_t cnt = lane_column_offset(e[u], p[u]);
+            colend[u] = __shfl_sync(FULL_MASK, e[u], cnt & 31);
+            j[u] = valid[u] ? c0[u] + cnt : -1 - lane;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            mj[u] = valid[u] ? ld_i32_last(mc + j[u], pol) : 0x7fffffff;
+        RowRec rec[kU];
+        bool cand[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            cand[u] = valid[u] && i[u] > mj[u];
+            rec[u].s = rec[u].e = 0;
+            rec[u].sig = 0ull;
+            if (cand[u]) {
                 ++n_cand;
-                const int32_t mi = __ldg(mr + i);
-                const int32_t s0 = __ldg(colptr + mi);
-                const int32_t s1 = __ldg(colptr + mi + 1);
-                q = find_row(rowidx, s0, s1, mj);
-                if (q >= 0) {
-                    ++n_found;
-                    const double wij = __ldcs(w + p);
-                    const double wq = __ldg(w + q);
-                    g = ((wij + wq) - __ldg(wm + mi)) - __ldg(wm + j);
-                    if (g > 0.0) {
-                        ++n_pos;
+                rec[u] = ld_rowrec(rr + i[u], pol);
+            }
+        }
+        int32_t lo[kU], len[kU], q[kU];
+        double wmi[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const bool pass = cand[u] && ((rec[u].sig >> sig_bit(mj[u])) & 1ull);
+            lo[u] = rec[u].s;
+            len[u] = pass ? rec[u].e - rec[u].s : 0;
+            q[u] = -1;
+            wmi[u] = pass ? __ldg(wmr + i[u]) : 0.0;
+        }
+        // merged binary searches (early exit on a hit)
+        for (;;) {
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                if (len[u] > 0) {
+                    any = true;
+                    const int32_t half = len[u] >> 1;
+                    const int32_t mid = lo[u] + half;
+                    const int32_t v = __ldg(rowidx + mid);
+                    if (v == mj[u]) {
+                        q[u] = mid;
+                        len[u] = 0;
+                    } else if (v < mj[u]) {
+                        lo[u] = mid + 1;
+                        len[u] -= half + 1;
                     } else {
-                        g = 0.0;
-                        q = -1;
+                        len[u] = half;
                     }
                 }
             }
+            if (!any)
+                break;
         }
-        // segmented arg-max over lanes of the same column (suffix direction)
-        int32_t bp = valid ? p : 0x7fffffff;
+        double g[kU];
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const double og = __shfl_down_sync(FULL_MASK, g, off);
-            const int32_t op = __shfl_down_sync(FULL_MASK, bp, off);
-            const int32_t oq = __shfl_down_sync(FULL_MASK, q, off);
-            const int32_t oj = __shfl_down_sync(FULL_MASK, j, off);
-            if (lane + off < 32 && oj == j && og > 0.0 && rec_better(og, op, g, bp)) {
-                g = og;
-                bp = op;
-                q = oq;
+        for (int u = 0; u < kU; ++u) {
+            g[u] = 0.0;
+            if (q[u] >= 0) {
+                ++n_found;
+                const double wij = __ldcs(w + p[u]);
+                const double wq = __ldg(w + q[u]);
+                const double gg = ((wij + wq) - wmi[u]) - __ldg(wm + j[u]);
+                if (gg > 0.0) {
+                    ++n_pos;
+                    g[u] = gg;
+                } else {
+                    q[u] = -1;
+                }
             }
         }
-        const int32_t jprev = __shfl_up_sync(FULL_MASK, j, 1);
-        const bool head = valid && (lane == 0 || jprev != j);
-        if (head) {
-            const bool starts_here = (j != c0) || (c0start >= base);
-            const bool complete = starts_here && colend <= base + kTile;
-            Rec r;
-            r.g = g;
-            r.p = g > 0.0 ? bp : 0;
-            r.q = g > 0.0 ? q : 0;
-            if (complete)
-                best[j] = r;
-            else if (g > 0.0)
-                rec_combine(best + j, r, ctl);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (!__any_sync(FULL_MASK, g[u] > 0.0))
+                continue;
+            // segmented arg-max over lanes of the same column (suffix direction)
+            double gg = g[u];
+            int32_t bp = valid[u] ? p[u] : 0x7fffffff;
+            int32_t bq = q[u];
+            const int32_t jj = j[u];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const double og = __shfl_down_sync(FULL_MASK, gg, off);
+                const int32_t op = __shfl_down_sync(FULL_MASK, bp, off);
+                const int32_t oq = __shfl_down_sync(FULL_MASK, bq, off);
+                const int32_t oj = __shfl_down_sync(FULL_MASK, jj, off);
+                if (lane + off < 32 && oj == jj && og > 0.0 && rec_better(og, op, gg, bp)) {
+                    gg = og;
+                    bp = op;
+                    bq = oq;
+                }
+            }
+            const int32_t jprev = __shfl_up_sync(FULL_MASK, jj, 1);
+            const bool head = valid[u] && (lane == 0 || jprev != jj);
+            if (head && gg > 0.0) {
+                const bool starts_here = (jj != c0[u]) || (c0s[u] >= base[u]);
+                const bool complete = starts_here && colend[u] <= base[u] + kTile;
+                Rec r;
+                r.g = gg;
+                r.p = bp;
+                r.q = bq;
+                if (complete)
+                    best[jj] = r;
+                else
+                    rec_combine(best + jj, r, ctl);
+            }
         }
     }
     block_add_u64(n_cand, &ctl->candidates);
@@ -393,11 +564,13 @@ __global__ void k_select(int32_t n, const int32_t *__restrict__ rowidx,
     }
 }
 
-// Flip every selected cycle: column j takes row i, key column k takes m_j.
-// The selected cycles are vertex-disjoint, so each thread owns its four
-// vertices.
-__global__ void k_flip(int32_t n, const int32_t *__restrict__ rowidx, const double *__restrict__ w,
-                       const Rec *__restrict__ best, Sel *dsel, int32_t *mc, int32_t *mr, double *wm,
+// Flip every selected cycle: column j takes row i, key column k takes m_j;
+// the row records of rows i and m_j follow their new mates.  The selected
+// cycles are vertex-disjoint, so each thread owns its four vertices.
+__global__ void k_flip(int32_t n, const int32_t *__restrict__ colptr,
+                       const int32_t *__restrict__ rowidx, const double *__restrict__ w,
+                       const unsigned long long *__restrict__ colsig, const Rec *__restrict__ best,
+                       Sel *dsel, int32_t *mc, int32_t *mr, double *wm, RowRec *rr, double *wmr,
                        Ctl *ctl)
 {
     unsigned long long flips = 0;
@@ -412,12 +585,26 @@ __global__ void k_flip(int32_t n, const int32_t *__restrict__ rowidx, const doub
             const Rec r = best[j];
             const int32_t i = rowidx[r.p];
             const int32_t mj = mc[j];
+            const double wij = w[r.p];
+            const double wq = w[r.q];
             mc[j] = i;
             mr[i] = j;
             mc[k] = mj;
             mr[mj] = (int32_t)k;
-            wm[j] = w[r.p];
-            wm[k] = w[r.q];
+            wm[j] = wij;
+            wm[k] = wq;
+            RowRec a;
+            a.s = colptr[j];
+            a.e = colptr[j + 1];
+            a.sig = colsig[j];
+            rr[i] = a;
+            wmr[i] = wij;
+            RowRec b;
+            b.s = colptr[k];
+            b.e = colptr[k + 1];
+            b.sig = colsig[k];
+            rr[mj] = b;
+            wmr[mj] = wq;
             ++flips;
         }
     }
@@ -480,6 +667,37 @@ static inline unsigned blocks_for(int64_t items, int threads)
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+constexpr int kSearchThreads = 256;
+
+int default_search_u()
+{
+    const char *v = getenv("AWPM_SEARCH_U");
+    if (v && (v[0] == '1' || v[0] == '2' || v[0] == '4') && v[1] == 0)
+        return v[0] - '0';
+    return 1;
+}
+
+// Resident blocks per SM of the search kernel with u tiles in flight per warp.
+int search_blocks_per_sm(int u)
+{
+    int b = 0;
+    cudaError_t e;
+    if (u == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<AWPM_LOOKUP_BSEARCH, 2>,
+                                                          kSearchThreads, 0);
+    else if (u == 4)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<AWPM_LOOKUP_BSEARCH, 4>,
+                                                          kSearchThreads, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<AWPM_LOOKUP_BSEARCH, 1>,
+                                                          kSearchThreads, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b < 1 ? 1 : b;
+}
+
 void launch_init(const Work &wk, int max_passes, int num_sms, cudaStream_t s)
 {
     const int T = 256;
@@ -488,6 +706,7 @@ void launch_init(const Work &wk, int max_passes, int num_sms, cudaStream_t s)
     cudaMemsetAsync(wk.starts, 0, sizeof(uint32_t) * (((size_t)wk.nnz + 31) / 32 + 1), s);
     cudaMemsetAsync(wk.best, 0, sizeof(Rec) * (size_t)wk.n, s);
     cudaMemsetAsync(wk.dsel, 0, sizeof(Sel) * (size_t)wk.n, s);
+    cudaMemsetAsync(wk.colsig, 0, sizeof(unsigned long long) * (size_t)wk.n, s);
     k_init_ctl<<<1, 1, 0, s>>>(wk.ctl, max_passes);
     k_check_colptr<<<blocks_for((int64_t)wk.n + 1, T), T, 0, s>>>(wk.n, wk.nnz, wk.colptr, wk.ctl);
     k_mark_starts<<<blocks_for(wk.n, T), T, 0, s>>>(wk.n, wk.colptr, wk.starts, wk.tile_col, wk.ctl);
@@ -497,6 +716,11 @@ void launch_init(const Work &wk, int max_passes, int num_sms, cudaStream_t s)
         wk.n, wk.nnz, wk.rowidx, wk.w, wk.starts, wk.ctl);
     k_init_mates<<<blocks_for(wk.n, T), T, 0, s>>>(wk.n, wk.colptr, wk.rowidx, wk.w, wk.mate_in,
                                                     wk.mc, wk.mr, wk.wm, wk.ctl);
+    int64_t twant = ((int64_t)wk.ntiles + (T / 32) - 1) / (T / 32);
+    k_colsig<<<(unsigned)(twant < 1 ? 1 : (twant < cap ? twant : cap)), T, 0, s>>>(
+        wk.n, wk.nnz, wk.ntiles, wk.colptr, wk.rowidx, wk.tile_col, wk.colsig, wk.ctl);
+    k_init_rows<<<blocks_for(wk.n, T), T, 0, s>>>(wk.n, wk.colptr, wk.mc, wk.wm, wk.colsig, wk.rr,
+                                                   wk.wmr, wk.ctl);
 }
 
 void launch_weight_sum(const Work &wk, bool out, cudaStream_t s)
@@ -510,15 +734,30 @@ void launch_reset_best(const Work &wk, cudaStream_t s)
     cudaMemsetAsync(wk.best, 0, sizeof(Rec) * (size_t)wk.n, s);
 }
 
+template <int kU>
+static void launch_search_u(const Work &wk, int num_sms, cudaStream_t s)
+{
+    const int T = kSearchThreads;
+    const int64_t per_block = (int64_t)(T / 32) * kU;
+    int64_t want = ((int64_t)wk.ntiles + per_block - 1) / per_block;
+    int64_t cap = (int64_t)num_sms * (wk.search_bps > 0 ? wk.search_bps : 1);
+    unsigned grid = (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+    k_search<AWPM_LOOKUP_BSEARCH, kU><<<grid, T, 0, s>>>(
+        wk.n, wk.nnz, wk.ntiles, wk.colptr, wk.rowidx, wk.w, wk.tile_col, wk.mc, wk.wm, wk.rr,
+        wk.wmr, wk.best, wk.ctl);
+}
+
 void launch_search(const Work &wk, int lookup, int num_sms, cudaStream_t s)
 {
     (void)lookup;
-    const int T = 256;
-    int64_t want = ((int64_t)wk.ntiles + (T / 32) - 1) / (T / 32);
-    int64_t cap = (int64_t)num_sms * 8;
-    unsigned grid = (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
-    k_search<1><<<grid, T, 0, s>>>(wk.n, wk.nnz, wk.ntiles, wk.colptr, wk.rowidx, wk.w,
-                                   wk.tile_col, wk.mc, wk.mr, wk.wm, wk.best, wk.ctl);
+    if (wk.search_u == 1)
+        launch_search_u<1>(wk, num_sms, s);
+    else if (wk.search_u == 4)
+        launch_search_u<4>(wk, num_sms, s);
+    else if (wk.search_u == 2)
+        launch_search_u<2>(wk, num_sms, s);
+    else
+        launch_search_u<1>(wk, num_sms, s);
 }
 
 void launch_select_and_flip(const Work &wk, int num_sms, cudaStream_t s)
@@ -528,7 +767,8 @@ void launch_select_and_flip(const Work &wk, int num_sms, cudaStream_t s)
     int64_t cap = (int64_t)num_sms * 8;
     unsigned grid = (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
     k_select<<<grid, T, 0, s>>>(wk.n, wk.rowidx, wk.mr, wk.best, wk.dsel, wk.ctl);
-    k_flip<<<grid, T, 0, s>>>(wk.n, wk.rowidx, wk.w, wk.best, wk.dsel, wk.mc, wk.mr, wk.wm, wk.ctl);
+    k_flip<<<grid, T, 0, s>>>(wk.n, wk.colptr, wk.rowidx, wk.w, wk.colsig, wk.best, wk.dsel,
+                              wk.mc, wk.mr, wk.wm, wk.rr, wk.wmr, wk.ctl);
 }
 
 void launch_control(const Work &wk, bool graph, cudaGraphConditionalHandle h, cudaStream_t s)

@@ -5,7 +5,7 @@
 // handed the whole GPU to its own memory pool, or code running where an
 // allocation (which may synchronise the device) is not allowed.  This entry
 // point therefore allocates nothing.  Its scratch lives in one file-scope
-// __device__ array of fixed size (kScratchBytes, about 9 MB), which every
+// __device__ array of fixed size (kScratchBytes, about 17 MB), which every
 // GPU that loads the library keeps until the process exits.  The caller
 // passes every input and output in device memory.
 #include <cuda_runtime.h>
@@ -37,7 +37,10 @@ constexpr size_t kOffCtl = 0;
 constexpr size_t kOffMc = kOffCtl + up(sizeof(Ctl));
 constexpr size_t kOffMr = kOffMc + up(sizeof(int32_t) * kMaxN);
 constexpr size_t kOffWm = kOffMr + up(sizeof(int32_t) * kMaxN);
-constexpr size_t kOffBest = kOffWm + up(sizeof(double) * kMaxN);
+constexpr size_t kOffRr = kOffWm + up(sizeof(double) * kMaxN);
+constexpr size_t kOffWmr = kOffRr + up(sizeof(RowRec) * kMaxN);
+constexpr size_t kOffSig = kOffWmr + up(sizeof(double) * kMaxN);
+constexpr size_t kOffBest = kOffSig + up(sizeof(unsigned long long) * kMaxN);
 constexpr size_t kOffTile = kOffBest + up(sizeof(Rec) * kMaxN);
 constexpr size_t kOffStarts = kOffTile + up(sizeof(int32_t) * kTilesMax);
 constexpr size_t kOffWpart = kOffStarts + up(sizeof(uint32_t) * (kMaxNnz / 32 + 1));
@@ -137,6 +140,8 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     wk.n = n;
     wk.nnz = nnz;
     wk.ntiles = (int32_t)(((int64_t)nnz + kTile - 1) / kTile);
+    wk.search_u = default_search_u();
+    wk.search_bps = search_blocks_per_sm(wk.search_u);
     wk.colptr = colptr;
     wk.rowidx = rowidx;
     wk.w = weight;
@@ -145,6 +150,9 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     wk.mc = (int32_t *)(base + kOffMc);
     wk.mr = (int32_t *)(base + kOffMr);
     wk.wm = (double *)(base + kOffWm);
+    wk.rr = (RowRec *)(base + kOffRr);
+    wk.wmr = (double *)(base + kOffWmr);
+    wk.colsig = (unsigned long long *)(base + kOffSig);
     wk.best = (Rec *)(base + kOffBest);
     // the search never selects (Step D): its selection records share the
     // Step-C area, which launch_init clears either way
@@ -154,7 +162,8 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     wk.wpart = (double *)(base + kOffWpart);
 
     // launch_init clears everything that must start at zero (control block,
-    // row mates, column-start bits, Step-C and Step-D records) before use.
+    // row mates, column-start bits, column signatures, Step-C and Step-D
+    // records) before use.
     launch_init(wk, 1, num_sms, s);
     launch_search(wk, AWPM_LOOKUP_BSEARCH, num_sms, s);
     launch_export_stepc(wk, stepc_gain, stepc_row, s);
