@@ -151,6 +151,30 @@ int awpm_improve_ctx(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int3
                      awpm_stats *stats);
 
 /*
+ * Many independent problems in one solve (batched form of awpm_improve).
+ * The `count` matrices are passed as one block-diagonal union in the same
+ * CSC conventions: matrix b owns the columns and rows [n_off[b], n_off[b+1])
+ * (n_off: count+1 non-decreasing int32 offsets from 0 to N = n_off[count]),
+ * colptr[N+1], rowidx and mate_in/mate_out[N] use global indices, and every
+ * stored row of a column must lie in that column's block.  No cycle crosses
+ * blocks, so each pass of the union is one pass (Algorithm 2) of every
+ * matrix; a matrix stops at its first empty pass (or after max_iters
+ * passes) and its tiles are skipped from then on.  Each matrix's matching,
+ * pass count, cycle count and weights equal those of awpm_improve on that
+ * matrix alone.  All matrices run in one CUDA-graph launch.
+ *   per_matrix[count] (may be NULL): iterations, converged, cycles_applied,
+ *     edge_checks, weight_in, weight_out of each matrix (candidate counters
+ *     are 0 there); total (may be NULL): the union (candidates, closing_found,
+ *     positive summed; iterations = passes of the longest matrix; converged
+ *     = every matrix converged; edge_checks summed over the matrices).
+ * Errors as awpm_improve; one invalid matrix, or a row outside its column's
+ * block (AWPM_ERR_INVALID_ARG), fails the whole call.
+ */
+int awpm_improve_batch(awpm_ctx *ctx, int32_t count, const int32_t *n_off, const int32_t *colptr,
+                       const int32_t *rowidx, const double *weight, const int32_t *mate_in,
+                       int32_t *mate_out, awpm_stats *per_matrix, awpm_stats *total);
+
+/*
  * One cycle search from a given matching without flipping anything: Steps
  * A-C of a single pass (Algorithms 3-5).  For every column j,
  * stepc_gain[j] / stepc_row[j] receive the Step-C winner rooted at j (its gain

@@ -65,6 +65,8 @@ SIGNATURES = [
                                         ctypes.POINTER(Stats)]),
     ("awpm_search", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP,
                                    ctypes.POINTER(Stats)]),
+    ("awpm_improve_batch", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP,
+                                          ctypes.POINTER(Stats), ctypes.POINTER(Stats)]),
     ("awpm_search_noalloc", ctypes.c_int, [ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                            ctypes.POINTER(Stats)]),
 ]
@@ -164,6 +166,19 @@ def awpm_improve_ctx(ctx: Context, n, colptr, rowidx, weight, mate_in, mate_out)
                                   _ptr(mate_in, "int32"), _ptr(mate_out, "int32"),
                                   ctypes.byref(st)))
     return st.as_dict()
+
+
+def awpm_improve_batch(ctx: Context, count, n_off, colptr, rowidx, weight, mate_in, mate_out,
+                       per_matrix: bool = True):
+    """Batched solve of a block-diagonal union; returns (total stats, list of
+    per-matrix stats or None)."""
+    tot = Stats()
+    pm = (Stats * max(int(count), 1))() if per_matrix else None
+    _check(lib().awpm_improve_batch(ctx.handle, int(count), _ptr(n_off, "int32"),
+                                    _ptr(colptr, "int32"), _ptr(rowidx, "int32"),
+                                    _ptr(weight, "float64"), _ptr(mate_in, "int32"),
+                                    _ptr(mate_out, "int32"), pm, ctypes.byref(tot)))
+    return tot.as_dict(), ([pm[b].as_dict() for b in range(int(count))] if per_matrix else None)
 
 
 def awpm_search(ctx: Context, n, colptr, rowidx, weight, mate, stepc_gain, stepc_row) -> dict:

@@ -54,12 +54,14 @@ struct DevBuf {
 };
 
 struct GraphKey {
-    int32_t n = -1, nnz = -1, max_passes = 0, lookup = 0;
-    const void *colptr = nullptr, *rowidx = nullptr, *w = nullptr, *mate_in = nullptr;
+    int32_t n = -1, nnz = -1, max_passes = 0, lookup = 0, count = 0;
+    const void *colptr = nullptr, *rowidx = nullptr, *w = nullptr, *mate_in = nullptr,
+               *n_off = nullptr;
     bool operator==(const GraphKey &o) const
     {
         return n == o.n && nnz == o.nnz && max_passes == o.max_passes && lookup == o.lookup &&
-               colptr == o.colptr && rowidx == o.rowidx && w == o.w && mate_in == o.mate_in;
+               count == o.count && colptr == o.colptr && rowidx == o.rowidx && w == o.w &&
+               mate_in == o.mate_in && n_off == o.n_off;
     }
 };
 
@@ -74,11 +76,15 @@ struct awpm_ctx {
     bool own_stream = false;
     size_t held = 0;
     // workspace
-    DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart;
+    DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
     int search_u = 1;
-    int search_bps = 1;
+    int search_bps[2][2] = {{1, 1}, {1, 1}};  // [batch][hash]: resident blocks per SM
     // staging of host-resident arrays
     DevBuf s_colptr, s_rowidx, s_w, s_mate, s_gain, s_row;
+    // batched solves
+    DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
+    void *h_batch = nullptr;  // pinned per-matrix results
+    size_t h_batch_bytes = 0;
     Ctl *h_ctl = nullptr;       // pinned
     int32_t *h_active = nullptr;  // pinned ring of the timed loop
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
@@ -199,6 +205,7 @@ int build_graph(awpm_ctx *c, const Work &wk, int max_passes, int lookup)
     }
     launch_init(wk, max_passes, c->num_sms, s);
     launch_weight_sum(wk, false, s);
+    launch_batch_weight_sum(wk, false, s);
     e = cudaStreamEndCapture(s, &g_init);
     if (e != cudaSuccess) {
         note_cuda(e, "capture of the initialisation", __LINE__);
@@ -207,6 +214,7 @@ int build_graph(awpm_ctx *c, const Work &wk, int max_passes, int lookup)
     e = cudaStreamBeginCapture(s, mode);
     if (e == cudaSuccess) {
         launch_weight_sum(wk, true, s);
+        launch_batch_weight_sum(wk, true, s);
         e = cudaStreamEndCapture(s, &g_final);
     }
     if (e != cudaSuccess) {
@@ -242,7 +250,7 @@ int build_graph(awpm_ctx *c, const Work &wk, int max_passes, int lookup)
         goto done;
     }
     launch_reset_best(wk, s);
-    launch_search(wk, lookup, c->num_sms, s);
+    launch_search(wk, c->num_sms, s);
     launch_select_and_flip(wk, c->num_sms, s);
     launch_control(wk, true, h, s);
     if ((e = cudaStreamEndCapture(s, &body)) != cudaSuccess) {
@@ -288,6 +296,7 @@ int run_timed(awpm_ctx *c, const Work &wk, int max_passes, int lookup, double *m
     cudaStream_t s = c->stream;
     launch_init(wk, max_passes, c->num_sms, s);
     launch_weight_sum(wk, false, s);
+    launch_batch_weight_sum(wk, false, s);
     AWPM_TRY(check_launch());
     int t = 0;
     for (; t < max_passes; ++t) {
@@ -300,7 +309,7 @@ int run_timed(awpm_ctx *c, const Work &wk, int max_passes, int lookup, double *m
         AWPM_TRY(ensure_timing_events(c, (size_t)t + 1));
         launch_reset_best(wk, s);
         CUDA_TRY(cudaEventRecord(c->tev[2 * t], s));
-        launch_search(wk, lookup, c->num_sms, s);
+        launch_search(wk, c->num_sms, s);
         CUDA_TRY(cudaEventRecord(c->tev[2 * t + 1], s));
         launch_select_and_flip(wk, c->num_sms, s);
         launch_control(wk, false, cudaGraphConditionalHandle(), s);
@@ -310,6 +319,7 @@ int run_timed(awpm_ctx *c, const Work &wk, int max_passes, int lookup, double *m
         CUDA_TRY(cudaEventRecord(c->flagev[t % kRing], s));
     }
     launch_weight_sum(wk, true, s);
+    launch_batch_weight_sum(wk, true, s);
     AWPM_TRY(check_launch());
     *passes_enqueued = t;
     *ms_search = 0.0;
@@ -331,7 +341,10 @@ int setup_ctx(awpm_ctx *c, const awpm_options *opt)
     CUDA_TRY(cudaSetDevice(dev));
     CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     c->search_u = default_search_u();
-    c->search_bps = search_blocks_per_sm(c->search_u);
+    for (int b = 0; b < 2; ++b) {
+        c->search_bps[b][0] = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, c->search_u, b == 1);
+        c->search_bps[b][1] = search_blocks_per_sm(AWPM_LOOKUP_HASH, 1, b == 1);
+    }
     if (c->opt.stream) {
         c->stream = (cudaStream_t)c->opt.stream;
         c->own_stream = false;
@@ -357,13 +370,16 @@ void teardown_ctx(awpm_ctx *c)
         cudaStreamSynchronize(c->stream);
     drop_graph(c);
     DevBuf *bufs[] = {&c->mc, &c->mr, &c->wm, &c->rr, &c->wmr, &c->colsig, &c->best, &c->dsel,
-                      &c->tile_col, &c->starts,
+                      &c->tile_col, &c->starts, &c->htab, &c->b_noff, &c->b_colmat,
+                      &c->b_tilemat, &c->b_i32, &c->b_u64, &c->b_f64,
                       &c->ctl, &c->wpart, &c->s_colptr, &c->s_rowidx, &c->s_w, &c->s_mate,
                       &c->s_gain, &c->s_row};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_ctl)
         cudaFreeHost(c->h_ctl);
+    if (c->h_batch)
+        cudaFreeHost(c->h_batch);
     if (c->h_active)
         cudaFreeHost(c->h_active);
     for (cudaEvent_t ev : c->tev)
@@ -397,7 +413,8 @@ int stage_in(awpm_ctx *c, DevBuf &buf, const T *src, size_t count, int loc, cons
 // search), results and statistics.
 int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *weight,
         const int32_t *mate_in, int32_t *mate_out, awpm_stats *st, bool search_only,
-        double *gain_out, int32_t *row_out)
+        double *gain_out, int32_t *row_out, int32_t count = 0, const int32_t *n_off = nullptr,
+        awpm_stats *per_matrix = nullptr)
 {
     if (!c || n < 0 || (n > 0 && (!colptr || !mate_in)) || (!search_only && n > 0 && !mate_out) ||
         (search_only && n > 0 && (!gain_out || !row_out)))
@@ -435,7 +452,7 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
         return AWPM_ERR_INVALID_ARG;
     const int32_t ntiles = (int32_t)(((int64_t)nnz + kTile - 1) / kTile);
     const int32_t max_passes = c->opt.max_iters > 0 ? c->opt.max_iters : AWPM_PASS_CAP;
-    const int lookup = AWPM_LOOKUP_BSEARCH;
+    const int lookup = c->opt.lookup == AWPM_LOOKUP_HASH ? AWPM_LOOKUP_HASH : AWPM_LOOKUP_BSEARCH;
 
     AWPM_TRY(ensure(c, c->mc, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->mr, sizeof(int32_t) * n));
@@ -449,18 +466,49 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     AWPM_TRY(ensure(c, c->starts, sizeof(uint32_t) * (((size_t)nnz + 31) / 32 + 1)));
     AWPM_TRY(ensure(c, c->ctl, sizeof(Ctl)));
     AWPM_TRY(ensure(c, c->wpart, sizeof(double) * kWsumBlocks));
+    if (lookup == AWPM_LOOKUP_HASH)
+        AWPM_TRY(ensure(c, c->htab, sizeof(unsigned long long) * 2 * (size_t)nnz));
 
     CUDA_TRY(cudaEventRecord(c->ev_a, c->stream));
     Work wk;
     wk.n = n;
     wk.nnz = nnz;
     wk.ntiles = ntiles;
-    wk.search_u = c->search_u;
-    wk.search_bps = c->search_bps;
+    wk.lookup = lookup;
+    wk.htab = lookup == AWPM_LOOKUP_HASH ? (unsigned long long *)c->htab.p : nullptr;
+    wk.search_u = lookup == AWPM_LOOKUP_HASH ? 1 : c->search_u;
+    wk.search_bps = c->search_bps[count > 0 ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0];
     AWPM_TRY(stage_in(c, c->s_colptr, colptr, (size_t)n + 1, l_colptr, &wk.colptr));
     AWPM_TRY(stage_in(c, c->s_rowidx, rowidx, (size_t)nnz, l_rowidx, &wk.rowidx));
     AWPM_TRY(stage_in(c, c->s_w, weight, (size_t)nnz, l_w, &wk.w));
     AWPM_TRY(stage_in(c, c->s_mate, mate_in, (size_t)n, l_mate, &wk.mate_in));
+    if (count > 0) {
+        const int l_off = where(c, n_off);
+        if (l_off < 0)
+            return AWPM_ERR_INVALID_ARG;
+        BatchWork &bw = wk.bw;
+        bw.count = count;
+        AWPM_TRY(stage_in(c, c->b_noff, n_off, (size_t)count + 1, l_off, &bw.n_off));
+        AWPM_TRY(ensure(c, c->b_colmat, sizeof(int32_t) * n));
+        AWPM_TRY(ensure(c, c->b_tilemat, sizeof(int32_t) * ((size_t)ntiles + 1)));
+        AWPM_TRY(ensure(c, c->b_i32, sizeof(int32_t) * (5 * (size_t)count + 1)));
+        AWPM_TRY(ensure(c, c->b_u64, sizeof(unsigned long long) * 2 * (size_t)count));
+        AWPM_TRY(ensure(c, c->b_f64, sizeof(double) * 2 * (size_t)count));
+        bw.colmat = (int32_t *)c->b_colmat.p;
+        bw.tilemat = (int32_t *)c->b_tilemat.p;
+        int32_t *i32 = (int32_t *)c->b_i32.p;
+        bw.mdone = i32;
+        bw.miter = i32 + count;
+        bw.mconv = i32 + 2 * (size_t)count;
+        bw.mnnz = i32 + 3 * (size_t)count;
+        bw.active = i32 + 5 * (size_t)count;
+        unsigned long long *u64 = (unsigned long long *)c->b_u64.p;
+        bw.mflips = u64;
+        bw.mcycles = u64 + count;
+        double *f64 = (double *)c->b_f64.p;
+        bw.mw_in = f64;
+        bw.mw_out = f64 + count;
+    }
     wk.mc = (int32_t *)c->mc.p;
     wk.mr = (int32_t *)c->mr.p;
     wk.wm = (double *)c->wm.p;
@@ -479,7 +527,7 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     const bool timed = (c->opt.flags & AWPM_FLAG_TIME_SEARCH) != 0;
     if (search_only) {
         launch_init(wk, 1, c->num_sms, c->stream);
-        launch_search(wk, lookup, c->num_sms, c->stream);
+        launch_search(wk, c->num_sms, c->stream);
         double *g = gain_out;
         int32_t *r = row_out;
         if (l_gain != 1) {
@@ -510,6 +558,8 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
         key.rowidx = wk.rowidx;
         key.w = wk.w;
         key.mate_in = wk.mate_in;
+        key.count = count;
+        key.n_off = wk.bw.n_off;
         if (!c->g_valid || !(c->g_key == key)) {
             drop_graph(c);
             AWPM_TRY(build_graph(c, wk, max_passes, lookup));
@@ -524,6 +574,25 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
                                  c->stream));
     }
     CUDA_TRY(cudaMemcpyAsync(c->h_ctl, wk.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    // per-matrix results: miter, mconv, mnnz (3 x i32), mcycles (u64), mw_in, mw_out (f64)
+    const size_t pm_bytes = (size_t)count * (3 * sizeof(int32_t) + 3 * 8);
+    if (count > 0 && per_matrix) {
+        if (c->h_batch_bytes < pm_bytes) {
+            if (c->h_batch)
+                cudaFreeHost(c->h_batch);
+            c->h_batch = nullptr;
+            c->h_batch_bytes = 0;
+            CUDA_TRY(cudaMallocHost(&c->h_batch, pm_bytes));
+            c->h_batch_bytes = pm_bytes;
+        }
+        char *hb = (char *)c->h_batch;
+        CUDA_TRY(cudaMemcpyAsync(hb, wk.bw.miter, sizeof(int32_t) * 3 * (size_t)count,
+                                 cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(hb + 12 * (size_t)count, wk.bw.mcycles, 8 * (size_t)count,
+                                 cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(hb + 20 * (size_t)count, wk.bw.mw_in, 16 * (size_t)count,
+                                 cudaMemcpyDeviceToHost, c->stream));
+    }
     CUDA_TRY(cudaEventRecord(c->ev_b, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
 
@@ -552,6 +621,43 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     S.ms_total = ms_total;
     S.ms_search = ms_search;
     S.lookup_used = lookup;
+    if (count > 0 && per_matrix) {
+        const char *hb = (const char *)c->h_batch;
+        const int32_t *miter = (const int32_t *)hb;
+        const int32_t *mconv = miter + count;
+        const int32_t *mnnz = miter + 2 * (size_t)count;
+        const unsigned long long *mcyc = (const unsigned long long *)(hb + 12 * (size_t)count);
+        const double *mwi = (const double *)(hb + 20 * (size_t)count);
+        const double *mwo = mwi + count;
+        std::vector<int32_t> off((size_t)count + 1);
+        if (where(c, n_off) == 1)
+            CUDA_TRY(cudaMemcpy(off.data(), n_off, sizeof(int32_t) * off.size(),
+                                cudaMemcpyDeviceToHost));
+        else
+            std::memcpy(off.data(), n_off, sizeof(int32_t) * off.size());
+        int all_conv = 1;
+        for (int32_t b = 0; b < count; ++b) {
+            awpm_stats &m = per_matrix[b];
+            std::memset(&m, 0, sizeof(m));
+            m.iterations = miter[b];
+            m.converged = mconv[b];
+            all_conv &= mconv[b];
+            m.cycles_applied = (int64_t)mcyc[b];
+            m.edge_checks = (int64_t)(mnnz[b] - (off[b + 1] - off[b])) * miter[b];
+            m.weight_in = mwi[b];
+            m.weight_out = mwo[b];
+            m.ms_total = ms_total;
+            m.lookup_used = lookup;
+        }
+        S.converged = all_conv;
+    }
+    if (count > 0) {
+        // edge checks of a batch: each matrix counts only its own passes
+        S.edge_checks = 0;
+        if (per_matrix)
+            for (int32_t b = 0; b < count; ++b)
+                S.edge_checks += per_matrix[b].edge_checks;
+    }
     if (st)
         *st = S;
     return AWPM_OK;
@@ -666,6 +772,47 @@ int awpm_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
         }
     }
     return awpm_improve_ctx(c, n, colptr, rowidx, weight, mate_in, mate_out, stats);
+}
+
+int awpm_improve_batch(awpm_ctx *ctx, int32_t count, const int32_t *n_off, const int32_t *colptr,
+                       const int32_t *rowidx, const double *weight, const int32_t *mate_in,
+                       int32_t *mate_out, awpm_stats *per_matrix, awpm_stats *total)
+{
+    if (!ctx || count < 0 || (count > 0 && !n_off))
+        return AWPM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (count == 0) {
+        if (total) {
+            std::memset(total, 0, sizeof(*total));
+            total->converged = 1;
+        }
+        return AWPM_OK;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) {
+        note_cuda(e, "cudaSetDevice", __LINE__);
+        return AWPM_ERR_CUDA;
+    }
+    int32_t n = 0;
+    if (where(ctx, n_off) == 1) {
+        e = cudaMemcpy(&n, n_off + count, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            note_cuda(e, "cudaMemcpy", __LINE__);
+            return AWPM_ERR_CUDA;
+        }
+    } else {
+        n = n_off[count];
+    }
+    if (n <= 0)
+        return AWPM_ERR_INVALID_ARG;
+    std::vector<awpm_stats> tmp;
+    awpm_stats *pm = per_matrix;
+    if (!pm) {
+        tmp.resize((size_t)count);
+        pm = tmp.data();
+    }
+    return run(ctx, n, colptr, rowidx, weight, mate_in, mate_out, total, false, nullptr, nullptr,
+               count, n_off, pm);
 }
 
 int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,

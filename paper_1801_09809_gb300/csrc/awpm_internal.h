@@ -61,11 +61,33 @@ struct Ctl {
     double weight_out;
 };
 
+// Batched solve of many independent matrices as one block-diagonal union
+// (count > 0).  Matrix b owns columns and rows [n_off[b], n_off[b+1]).
+struct BatchWork {
+    int32_t count = 0;
+    const int32_t *n_off = nullptr;  // count + 1 offsets
+    int32_t *colmat = nullptr;       // matrix of each column
+    int32_t *tilemat = nullptr;      // matrix of each tile's first nonzero | kTileSingle
+    int32_t *mdone = nullptr;        // matrix finished (converged or pass cap)
+    int32_t *miter = nullptr;        // passes run per matrix
+    int32_t *mconv = nullptr;        // converged per matrix
+    int32_t *mnnz = nullptr;         // nonzeros per matrix
+    unsigned long long *mflips = nullptr;   // cycles flipped in the running pass
+    unsigned long long *mcycles = nullptr;  // cycles flipped in total
+    double *mw_in = nullptr;
+    double *mw_out = nullptr;
+    int32_t *active = nullptr;       // matrices still running after a pass
+};
+
+// Tile whose nonzeros all belong to one matrix.
+constexpr int32_t kTileSingle = (int32_t)0x80000000;
+
 // Device pointers of one solve.
 struct Work {
     int32_t n;
     int32_t nnz;
     int32_t ntiles;
+    int32_t lookup;      // AWPM_LOOKUP_BSEARCH or AWPM_LOOKUP_HASH
     int32_t search_u;    // tiles in flight per warp in the search kernel (1, 2, 4)
     int32_t search_bps;  // resident blocks per SM of that search kernel
     const int32_t *colptr;
@@ -78,12 +100,14 @@ struct Work {
     RowRec *rr;         // per row i: rows of column mr[i] (range + signature)
     double *wmr;        // per row i: wm[mr[i]] = w(i, mr[i])
     unsigned long long *colsig;  // per column: signature of its rows
+    unsigned long long *htab;    // per-column hash tables (2 slots per nonzero), or null
     Rec *best;          // Step-C records
     Sel *dsel;          // Step-D selections
     int32_t *tile_col;  // column holding the first nonzero of each tile
     uint32_t *starts;   // bit p set when a column starts at nonzero p
     Ctl *ctl;
     double *wpart;      // partial sums of the weight reduction
+    BatchWork bw;       // batched solve (bw.count > 0), else unused
 };
 
 constexpr int kWsumBlocks = 256;
@@ -92,14 +116,16 @@ constexpr int kWsumThreads = 256;
 // Launchers (all asynchronous on `s`).  `num_sms` sizes persistent grids.
 void launch_init(const Work &wk, int max_passes, int num_sms, cudaStream_t s);
 void launch_weight_sum(const Work &wk, bool out, cudaStream_t s);
-void launch_search(const Work &wk, int lookup, int num_sms, cudaStream_t s);
+void launch_search(const Work &wk, int num_sms, cudaStream_t s);
 void launch_select_and_flip(const Work &wk, int num_sms, cudaStream_t s);
 void launch_control(const Work &wk, bool graph, cudaGraphConditionalHandle h, cudaStream_t s);
+// Per-matrix weight sums of a batched solve.
+void launch_batch_weight_sum(const Work &wk, bool out, cudaStream_t s);
 void launch_export_stepc(const Work &wk, double *gain, int32_t *row, cudaStream_t s);
 void launch_reset_best(const Work &wk, cudaStream_t s);
-// Resident blocks per SM of the search kernel with u tiles in flight per
-// warp (for a one-wave grid).
-int search_blocks_per_sm(int u);
+// Resident blocks per SM of the search kernel for a lookup strategy and u
+// tiles in flight per warp (for a one-wave grid).
+int search_blocks_per_sm(int lookup, int u, bool batch);
 // Default tiles in flight per warp; the environment variable AWPM_SEARCH_U
 // (1, 2 or 4) overrides it, as a tuning knob.
 int default_search_u();

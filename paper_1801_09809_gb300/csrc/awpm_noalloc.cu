@@ -140,8 +140,10 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     wk.n = n;
     wk.nnz = nnz;
     wk.ntiles = (int32_t)(((int64_t)nnz + kTile - 1) / kTile);
+    wk.lookup = AWPM_LOOKUP_BSEARCH;
+    wk.htab = nullptr;
     wk.search_u = default_search_u();
-    wk.search_bps = search_blocks_per_sm(wk.search_u);
+    wk.search_bps = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, wk.search_u, false);
     wk.colptr = colptr;
     wk.rowidx = rowidx;
     wk.w = weight;
@@ -165,7 +167,7 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     // row mates, column-start bits, column signatures, Step-C and Step-D
     // records) before use.
     launch_init(wk, 1, num_sms, s);
-    launch_search(wk, AWPM_LOOKUP_BSEARCH, num_sms, s);
+    launch_search(wk, num_sms, s);
     launch_export_stepc(wk, stepc_gain, stepc_row, s);
     if (cudaGetLastError() != cudaSuccess)
         return AWPM_ERR_CUDA;

@@ -402,3 +402,41 @@ def from_dense(w: np.ndarray, mask: np.ndarray, mate) -> Graph:
     col = _col_of_nz(colptr)
     weight = np.ascontiguousarray(w[rowidx, col], dtype=np.float64)
     return Graph(n, colptr, rowidx, weight, np.asarray(mate, dtype=np.int32), "dense")
+
+
+# ----------------------------------------------------------------------------
+# batched layout
+# ----------------------------------------------------------------------------
+
+def union(graphs):
+    """Pack matrices into one block-diagonal union: returns (n_off, Graph)
+    where matrix b owns columns and rows [n_off[b], n_off[b+1]) and indices
+    are global."""
+    ns = np.array([g.n for g in graphs], dtype=np.int64)
+    n_off = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(ns, out=n_off[1:])
+    nnzs = np.array([g.nnz for g in graphs], dtype=np.int64)
+    z_off = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(nnzs, out=z_off[1:])
+    N, NNZ = int(n_off[-1]), int(z_off[-1])
+    if N >= 2**31 or NNZ >= 2**31:
+        raise ValueError("union too large for int32 indices")
+    colptr = np.empty(N + 1, dtype=np.int32)
+    rowidx = np.empty(NNZ, dtype=np.int32)
+    weight = np.empty(NNZ, dtype=np.float64)
+    mate = np.empty(N, dtype=np.int32)
+    for b, g in enumerate(graphs):
+        a0, a1 = int(n_off[b]), int(n_off[b + 1])
+        z0, z1 = int(z_off[b]), int(z_off[b + 1])
+        colptr[a0:a1] = g.colptr[:-1] + z0
+        rowidx[z0:z1] = g.rowidx + a0
+        weight[z0:z1] = g.weight
+        mate[a0:a1] = g.mate + a0
+    colptr[N] = NNZ
+    return n_off.astype(np.int32), Graph(N, colptr, rowidx, weight, mate,
+                                         f"union({len(graphs)} matrices)")
+
+
+def split(n_off, mate):
+    """Per-matrix local matchings from a union matching."""
+    return [np.asarray(mate[n_off[b]:n_off[b + 1]]) - n_off[b] for b in range(len(n_off) - 1)]

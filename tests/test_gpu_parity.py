@@ -298,3 +298,21 @@ def test_context_reuse_across_sizes(ctx, orc, torch):
     for g in (gen.stencil_2d(20, 131), gen.stencil_2d(150, 132), gen.stencil_2d(20, 131),
               gen.rmat(5000, 6, 133), gen.stencil_2d(150, 132)):
         check(ctx, orc, g, torch)
+
+
+@pytest.mark.parametrize("lookup", [awpm.LOOKUP_BSEARCH, awpm.LOOKUP_HASH], ids=["bsearch", "hash"])
+def test_lookup_strategies(torch, orc, lookup):
+    """Both closing-edge lookups (binary search, per-column hash table) give
+    the oracle's result, ties and dense columns included."""
+    c = awpm.awpm_create(device=0, lookup=lookup)
+    try:
+        graphs = [gen.stencil_3d(14, 141), gen.rmat(1 << 14, 16, 142), gen.config1(),
+                  gen.random_small(300, 0.2, 143, integer_weights=True),
+                  gen.banded(5000, 13, 144)]
+        for g in graphs:
+            ref, rst, _ = orc.improve(g)
+            got, st = run_gpu(c, g, torch=torch)
+            assert_same_as_oracle(g, got, st, ref, rst, f"{g.name} lookup={lookup}")
+            assert st["lookup_used"] == lookup
+    finally:
+        awpm.awpm_destroy(c)
