@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched comparison")
+    ap.add_argument("--no-served", action="store_true", help="skip the served comparison")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-pool", type=int, default=16)
     ap.add_argument("--workload", default="rmat",
                     choices=["rmat", "stencil3d", "stencil2d", "rmat20", "rmat21"])
     return ap.parse_args()
@@ -219,6 +224,131 @@ def run_reference(args, rank, world):
     return 0
 
 
+def bench_batched(awpm, torch, dev, count):
+    """4,096 matrices (n log-uniform in [200, 20000], random sparse / 2D 5-point /
+    banded): one batched graph launch vs one launch per matrix, same GPU,
+    identical outputs required."""
+    from paper_1801_09809_gb300 import gen
+    graphs = gen.batch(count)
+    n_off, u = gen.union(graphs)
+    t = [torch.from_numpy(a).to(dev) for a in (n_off, u.colptr, u.rowidx, u.weight, u.mate)]
+    out = torch.empty_like(t[4])
+    ctx = awpm.awpm_create(device=dev.index or 0)
+    for _ in range(2):
+        tot, _ = awpm.awpm_improve_batch(ctx, count, *t, out, per_matrix=False)
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        tot, _ = awpm.awpm_improve_batch(ctx, count, *t, out, per_matrix=False)
+    batched_s = (time.perf_counter() - t0) / reps
+    batched = out.cpu().numpy()
+    # one launch (one awpm_improve call) per matrix, device-resident inputs
+    per = []
+    for g in graphs:
+        per.append([torch.from_numpy(a).to(dev) for a in (g.colptr, g.rowidx, g.weight, g.mate)])
+    outs = [torch.empty_like(p[3]) for p in per]
+    for g, p_, o in list(zip(graphs, per, outs))[:64]:
+        awpm.awpm_improve_ctx(ctx, g.n, *p_, o)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g, p_, o in zip(graphs, per, outs):
+        awpm.awpm_improve_ctx(ctx, g.n, *p_, o)
+    single_s = time.perf_counter() - t0
+    same = all(np.array_equal(batched[n_off[b]:n_off[b + 1]] - n_off[b], outs[b].cpu().numpy())
+               for b in range(count))
+    awpm.awpm_destroy(ctx)
+    return {"workload": f"{count} matrices, n log-uniform [200, 20000]: random sparse (deg 4-16), "
+                        "2D 5-point, banded (b 3-15); planted matchings, log-normal weights",
+            "n_total": int(u.n), "nnz_total": int(u.nnz), "passes": tot["iterations"],
+            "solves_per_s": count / batched_s, "ms_per_batch": 1e3 * batched_s,
+            "one_launch_per_matrix_solves_per_s": count / single_s,
+            "speedup_vs_one_launch_per_matrix": single_s / batched_s,
+            "identical_outputs": bool(same)}
+
+
+def bench_served(awpm, torch, dev, requests, pool_size, budget=100 * 10**9):
+    """Poisson stream of matching requests (n log-uniform in [1e3, 1e6]; random
+    sparse, 2D 5-point, 3D 27-point, R-MAT; degree 4-27) drawn from a pool of
+    distinct generated problems with pinned host inputs.  Served: the request
+    server (continuous batching over 4 slots, 100 GB budget).  Baseline: one
+    synchronous awpm_improve per request in arrival order.  Rate: 0.7 x the
+    served capacity measured on the same mix."""
+    from paper_1801_09809_gb300 import gen
+    specs = gen.serve_spec(pool_size, seed=gen.SEED_BASE + 6)
+    pool = [gen.build_spec(sp) for sp in specs]
+    pin = [[torch.from_numpy(a).pin_memory() for a in (g.colptr, g.rowidx, g.weight, g.mate)]
+           for g in pool]
+    rng = np.random.default_rng(gen.SEED_BASE + 66)
+    pick = rng.integers(0, pool_size, size=requests)
+    refs = {}
+    solo = awpm.awpm_create(device=dev.index or 0)
+    for k, g in enumerate(pool):
+        o = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        awpm.awpm_improve_ctx(solo, g.n, *pin[k], o)
+        refs[k] = o.numpy().copy()
+    outs = [torch.empty(pool[k].n, dtype=torch.int32).pin_memory() for k in pick]
+
+    def serve(arrivals):
+        ctx = awpm.awpm_create(device=dev.index or 0, slots=4, mem_budget_bytes=budget)
+        lat = np.zeros(requests)
+        t0 = time.perf_counter()
+        tickets = {}
+        nxt = 0
+        while nxt < requests or tickets:
+            now = time.perf_counter() - t0
+            while nxt < requests and arrivals[nxt] <= now:
+                k = pick[nxt]
+                g = pool[k]
+                tickets[nxt] = awpm.awpm_submit(ctx, g.n, *pin[k], outs[nxt], nnz=g.nnz)
+                nxt += 1
+            for r in list(tickets):
+                done, _ = awpm.awpm_poll(ctx, tickets[r])
+                if done:
+                    lat[r] = time.perf_counter() - t0 - arrivals[r]
+                    del tickets[r]
+            if nxt < requests and not tickets:
+                time.sleep(max(0.0, min(0.0005, arrivals[nxt] - (time.perf_counter() - t0))))
+        total = time.perf_counter() - t0
+        awpm.awpm_destroy(ctx)
+        return lat, total
+
+    def one_by_one(arrivals):
+        lat = np.zeros(requests)
+        t0 = time.perf_counter()
+        for r in range(requests):
+            now = time.perf_counter() - t0
+            if arrivals[r] > now:
+                time.sleep(arrivals[r] - now)
+            k = pick[r]
+            g = pool[k]
+            awpm.awpm_improve_ctx(solo, g.n, *pin[k], outs[r])
+            lat[r] = time.perf_counter() - t0 - arrivals[r]
+        return lat, time.perf_counter() - t0
+
+    # capacity of the served form on this mix (all requests at time 0)
+    lat0, total0 = serve(np.zeros(requests))
+    capacity = requests / total0
+    rate = 0.7 * capacity
+    arrivals = gen.poisson_arrivals(requests, rate)
+    lat_s, tot_s = serve(arrivals)
+    same_s = all(np.array_equal(outs[r].numpy(), refs[pick[r]]) for r in range(requests))
+    lat_b, tot_b = one_by_one(arrivals)
+    same_b = all(np.array_equal(outs[r].numpy(), refs[pick[r]]) for r in range(requests))
+    awpm.awpm_destroy(solo)
+    ms = lambda a, q: float(1e3 * np.percentile(a, q))
+    return {"workload": f"{requests} requests from a pool of {pool_size} generated problems "
+                        "(n log-uniform [1e3, 1e6]; random sparse, 2D, 3D, R-MAT; degree 4-27), "
+                        "pinned host inputs, Poisson arrivals",
+            "rate_per_s": rate, "served_capacity_solves_per_s": capacity,
+            "served": {"p50_ms": ms(lat_s, 50), "p99_ms": ms(lat_s, 99),
+                       "solves_per_s": requests / tot_s},
+            "one_launch_per_matrix": {"p50_ms": ms(lat_b, 50), "p99_ms": ms(lat_b, 99),
+                                      "solves_per_s": requests / tot_b},
+            "slots": 4, "budget_bytes": budget,
+            "identical_outputs": bool(same_s and same_b)}
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args.gpus)
@@ -316,7 +446,9 @@ def main():
     h2d = 4 * (n + 1) + 12 * nnz + 4 * n
     d2h = 4 * n + 88
 
-    kernels_per_step = 7 + 4 * passes + 2
+    # reset, colptr check, start marks, entries, mates, 2 weight-sum kernels;
+    # per pass: best reset, search, select, flip, control; final weight sum
+    kernels_per_step = 5 + 2 + 5 * passes + 2
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -332,6 +464,10 @@ def main():
             "clocks": clk.summary()}
     awpm.awpm_destroy(ctx)
     awpm.awpm_destroy(tctx)
+    if not args.no_batched:
+        line["batched"] = bench_batched(awpm, torch, dev, args.batch_count)
+    if not args.no_served:
+        line["served"] = bench_served(awpm, torch, dev, args.serve_requests, args.serve_pool)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(g) if world == 1 else None
         print(json.dumps(line))

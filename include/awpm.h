@@ -84,8 +84,23 @@ typedef struct {
     uint32_t flags;            /* AWPM_FLAG_*                                        */
     void *stream;              /* cudaStream_t to run on; NULL = a stream the context
                                   creates and owns                                   */
-    size_t mem_budget_bytes;   /* device bytes the context may hold; 0 = unlimited   */
+    size_t mem_budget_bytes;   /* device bytes the context may hold; 0 = unlimited;
+                                  for the request server: all its slots together     */
+    int32_t slots;             /* request server: concurrent solves (0 = 4)          */
+    int32_t reserved;
 } awpm_options;
+
+/* One request of the request server (awpm_submit). */
+typedef struct {
+    int32_t n;                 /* matrix order                                       */
+    int32_t nnz;               /* colptr[n]; -1 = read it (a device colptr then costs
+                                  a synchronisation at admission)                    */
+    const int32_t *colptr;     /* the awpm_improve arguments, host or device memory, */
+    const int32_t *rowidx;     /*   borrowed until awpm_poll reports the request done */
+    const double *weight;
+    const int32_t *mate_in;
+    int32_t *mate_out;
+} awpm_problem;
 
 typedef struct {
     int32_t iterations;      /* passes of Steps A-D run, the last empty one included  */
@@ -111,7 +126,7 @@ const char *awpm_strerror(int code);
 const char *awpm_last_error(void);
 
 /* Fill *opt with defaults: device -1, max_iters 0, lookup AUTO, no flags,
- * NULL stream, no budget. */
+ * NULL stream, no budget, 4 server slots. */
 void awpm_default_options(awpm_options *opt);
 
 /*
@@ -173,6 +188,31 @@ int awpm_improve_ctx(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int3
 int awpm_improve_batch(awpm_ctx *ctx, int32_t count, const int32_t *n_off, const int32_t *colptr,
                        const int32_t *rowidx, const double *weight, const int32_t *mate_in,
                        int32_t *mate_out, awpm_stats *per_matrix, awpm_stats *total);
+
+/*
+ * Request server (continuous batching of independent problems; the paper's
+ * static-pivoting use, Section 1, where every factorisation needs its own
+ * matching).  awpm_submit queues a problem and returns at once with a ticket.
+ * A scheduler thread of the context runs up to opt.slots solves
+ * concurrently, each on its own stream and workspace, and admits the next
+ * queued request as soon as a slot is free and the device bytes held by all
+ * slots stay within opt.mem_budget_bytes (a request that could never fit
+ * finishes with AWPM_ERR_BUDGET).  Every request is solved exactly as by
+ * awpm_improve alone: the same matching, passes and statistics, whatever else
+ * runs beside it.  The problem's arrays are borrowed until the request is
+ * reported done; mate_out is written then.  Device arrays must hold their
+ * data when submitted (the server's streams do not wait for other streams).
+ *   awpm_submit: AWPM_ERR_INVALID_ARG for a bad argument; errors of the solve
+ *     itself are reported by awpm_poll / awpm_wait.
+ *   awpm_poll: non-blocking.  *done = 0 while queued or running (returns
+ *     AWPM_OK).  Once done: *done = 1, *stats filled, the solve's own return
+ *     code returned, and the ticket released (AWPM_ERR_NOT_FOUND after).
+ *   awpm_wait: blocks until done, then as awpm_poll.
+ * awpm_destroy drains running solves and drops queued ones.
+ */
+int awpm_submit(awpm_ctx *ctx, const awpm_problem *p, uint64_t *ticket);
+int awpm_poll(awpm_ctx *ctx, uint64_t ticket, int *done, awpm_stats *stats);
+int awpm_wait(awpm_ctx *ctx, uint64_t ticket, awpm_stats *stats);
 
 /*
  * One cycle search from a given matching without flipping anything: Steps

@@ -26,7 +26,14 @@ PASS_CAP = 65536
 class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("lookup", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("stream", ctypes.c_void_p), ("mem_budget_bytes", ctypes.c_size_t)]
+                ("stream", ctypes.c_void_p), ("mem_budget_bytes", ctypes.c_size_t),
+                ("slots", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("colptr", ctypes.c_void_p),
+                ("rowidx", ctypes.c_void_p), ("weight", ctypes.c_void_p),
+                ("mate_in", ctypes.c_void_p), ("mate_out", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -67,6 +74,10 @@ SIGNATURES = [
                                    ctypes.POINTER(Stats)]),
     ("awpm_improve_batch", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP,
                                           ctypes.POINTER(Stats), ctypes.POINTER(Stats)]),
+    ("awpm_submit", ctypes.c_int, [_VP, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_uint64)]),
+    ("awpm_poll", ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(Stats)]),
+    ("awpm_wait", ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(Stats)]),
     ("awpm_search_noalloc", ctypes.c_int, [ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                            ctypes.POINTER(Stats)]),
 ]
@@ -133,13 +144,14 @@ class Context:
 
 
 def awpm_create(device: int = -1, max_iters: int = 0, lookup: int = LOOKUP_AUTO,
-                flags: int = 0, stream=None, mem_budget_bytes: int = 0) -> Context:
+                flags: int = 0, stream=None, mem_budget_bytes: int = 0, slots: int = 0) -> Context:
     L = lib()
     o = Options()
     L.awpm_default_options(ctypes.byref(o))
     o.device, o.max_iters, o.lookup, o.flags = device, max_iters, lookup, flags
     o.stream = _stream_handle(stream)
     o.mem_budget_bytes = mem_budget_bytes
+    o.slots = slots
     h = _VP()
     _check(L.awpm_create(ctypes.byref(h), ctypes.byref(o)))
     return Context(h.value)
@@ -200,6 +212,31 @@ def awpm_search_noalloc(n, colptr, rowidx, weight, mate, stepc_gain, stepc_row,
                                      _ptr(weight, "float64"), _ptr(mate, "int32"),
                                      _ptr(stepc_gain, "float64"), _ptr(stepc_row, "int32"),
                                      _stream_handle(stream), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def awpm_submit(ctx: Context, n, colptr, rowidx, weight, mate_in, mate_out, nnz=None) -> int:
+    """Queue one problem on the context's request server; returns the ticket.
+    The arrays must stay alive until awpm_poll/awpm_wait reports it done."""
+    p = Problem(int(n), int(nnz) if nnz is not None else -1, _ptr(colptr, "int32"),
+                _ptr(rowidx, "int32"), _ptr(weight, "float64"), _ptr(mate_in, "int32"),
+                _ptr(mate_out, "int32"))
+    t = ctypes.c_uint64()
+    _check(lib().awpm_submit(ctx.handle, ctypes.byref(p), ctypes.byref(t)))
+    return t.value
+
+
+def awpm_poll(ctx: Context, ticket: int):
+    """(done, stats or None); raises AwpmError if the finished solve failed."""
+    d = ctypes.c_int(0)
+    st = Stats()
+    _check(lib().awpm_poll(ctx.handle, ctypes.c_uint64(ticket), ctypes.byref(d), ctypes.byref(st)))
+    return (True, st.as_dict()) if d.value else (False, None)
+
+
+def awpm_wait(ctx: Context, ticket: int) -> dict:
+    st = Stats()
+    _check(lib().awpm_wait(ctx.handle, ctypes.c_uint64(ticket), ctypes.byref(st)))
     return st.as_dict()
 
 

@@ -16,8 +16,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libawpm.so")
-SOURCES = ["awpm_kernels.cu", "awpm_api.cu", "awpm_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "awpm_internal.h"), os.path.join(INCLUDE, "awpm.h")]
+SOURCES = ["awpm_kernels.cu", "awpm_api.cu", "awpm_serve.cu", "awpm_noalloc.cu"]
+HEADERS = [os.path.join(CSRC, "awpm_internal.h"), os.path.join(CSRC, "awpm_ctx.h"),
+           os.path.join(INCLUDE, "awpm.h")]
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,41 +1,49 @@
-// Host side of libawpm: the C ABI declared in include/awpm.h.
+// Host side of libawpm: contexts and the synchronous C ABI of include/awpm.h.
 //
 // A context owns a device workspace sized for the largest problem seen, the
-// staging buffers for host-resident inputs and a cache of instantiated CUDA
-// graphs.  One solve is one graph launch: validation and initialisation, a
-// conditional WHILE node whose body is one pass of Steps A-D (the control
-// kernel at the end of the body decides on the device whether another pass
-// runs, Algorithm 2), and the final weight reduction.  The host waits once,
-// at the end, to read the statistics.
+// staging buffers for host-resident inputs, a device-resident problem
+// descriptor (Work) and one instantiated CUDA graph per launch shape.  One
+// solve is: write the descriptor, launch the graph (validation and
+// initialisation; a conditional WHILE node whose body is one pass of Steps
+// A-D, the control kernel at the end of the body deciding on the device
+// whether another pass runs, Algorithm 2; the final weight reduction), copy
+// the results back.  The host waits once, at the end.  Because every kernel
+// reads the problem from the descriptor and runs a GPU-sized grid, the same
+// graph serves every problem of the context.
 #include <cuda_runtime.h>
 
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
-#include <string>
+#include <new>
 #include <vector>
 
 #include "awpm.h"
+#include "awpm_ctx.h"
 #include "awpm_internal.h"
 
 using namespace awpm;
 
-namespace {
+namespace awpm {
 
 thread_local char g_last_error[512] = "";
 
-void note_cuda(cudaError_t e, const char *what, int line)
+void note_cuda_error(cudaError_t e, const char *what, int line)
 {
-    snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at awpm_api.cu:%d: %s",
-             cudaGetErrorName(e), what, line, cudaGetErrorString(e));
+    snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at line %d: %s", cudaGetErrorName(e),
+             what, line, cudaGetErrorString(e));
 }
+
+}  // namespace awpm
+
+namespace {
 
 #define CUDA_TRY(x)                                                        \
     do {                                                                   \
         cudaError_t e_ = (x);                                              \
         if (e_ != cudaSuccess) {                                           \
-            note_cuda(e_, #x, __LINE__);                                   \
+            note_cuda_error(e_, #x, __LINE__);                             \
             return e_ == cudaErrorMemoryAllocation ? AWPM_ERR_OOM          \
                                                    : AWPM_ERR_CUDA;        \
         }                                                                  \
@@ -48,60 +56,10 @@ void note_cuda(cudaError_t e, const char *what, int line)
             return rc_;        \
     } while (0)
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
-struct GraphKey {
-    int32_t n = -1, nnz = -1, max_passes = 0, lookup = 0, count = 0;
-    const void *colptr = nullptr, *rowidx = nullptr, *w = nullptr, *mate_in = nullptr,
-               *n_off = nullptr;
-    bool operator==(const GraphKey &o) const
-    {
-        return n == o.n && nnz == o.nnz && max_passes == o.max_passes && lookup == o.lookup &&
-               count == o.count && colptr == o.colptr && rowidx == o.rowidx && w == o.w &&
-               mate_in == o.mate_in && n_off == o.n_off;
-    }
-};
-
-}  // namespace
-
-struct awpm_ctx {
-    std::mutex mu;
-    awpm_options opt{};
-    int device = 0;
-    int num_sms = 1;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    size_t held = 0;
-    // workspace
-    DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
-    int search_u = 1;
-    int search_bps[2][2] = {{1, 1}, {1, 1}};  // [batch][hash]: resident blocks per SM
-    // staging of host-resident arrays
-    DevBuf s_colptr, s_rowidx, s_w, s_mate, s_gain, s_row;
-    // batched solves
-    DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
-    void *h_batch = nullptr;  // pinned per-matrix results
-    size_t h_batch_bytes = 0;
-    Ctl *h_ctl = nullptr;       // pinned
-    int32_t *h_active = nullptr;  // pinned ring of the timed loop
-    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
-    std::vector<cudaEvent_t> tev;     // timing pairs of the timed loop
-    std::vector<cudaEvent_t> flagev;  // ring of the timed loop
-    // cached solve graph
-    bool g_valid = false;
-    GraphKey g_key;
-    cudaGraphExec_t g_exec = nullptr;
-};
-
-namespace {
-
 constexpr int kLookahead = 2;
 constexpr int kRing = 4;
 
-int release(awpm_ctx *c, DevBuf &b)
+void release(awpm_ctx *c, DevBuf &b)
 {
     if (b.p) {
         cudaFree(b.p);
@@ -109,15 +67,6 @@ int release(awpm_ctx *c, DevBuf &b)
         b.p = nullptr;
         b.bytes = 0;
     }
-    return AWPM_OK;
-}
-
-void drop_graph(awpm_ctx *c)
-{
-    if (c->g_exec)
-        cudaGraphExecDestroy(c->g_exec);
-    c->g_exec = nullptr;
-    c->g_valid = false;
 }
 
 int ensure(awpm_ctx *c, DevBuf &b, size_t bytes)
@@ -126,7 +75,6 @@ int ensure(awpm_ctx *c, DevBuf &b, size_t bytes)
         bytes = 16;
     if (b.bytes >= bytes)
         return AWPM_OK;
-    drop_graph(c);
     release(c, b);
     size_t want = bytes + bytes / 8;  // headroom against small growth steps
     if (c->opt.mem_budget_bytes && c->held + want > c->opt.mem_budget_bytes) {
@@ -137,7 +85,7 @@ int ensure(awpm_ctx *c, DevBuf &b, size_t bytes)
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, want);
     if (e != cudaSuccess) {
-        note_cuda(e, "cudaMalloc", __LINE__);
+        note_cuda_error(e, "cudaMalloc", __LINE__);
         cudaGetLastError();
         return AWPM_ERR_OOM;
     }
@@ -180,58 +128,60 @@ int code_of(unsigned err)
     return AWPM_OK;
 }
 
-int check_launch()
+int check_sink(const Sink &k)
 {
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        note_cuda(e, "kernel launch", __LINE__);
+    if (k.err != cudaSuccess) {
+        note_cuda_error(k.err, "kernel launch", __LINE__);
+        cudaGetLastError();
         return AWPM_ERR_CUDA;
     }
     return AWPM_OK;
 }
 
-int build_graph(awpm_ctx *c, const Work &wk, int max_passes, int lookup)
+Shape shape_of(const awpm_ctx *c, bool batch, int lookup)
 {
-    cudaStream_t s = c->stream;
-    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
-    cudaGraph_t g_init = nullptr, g_final = nullptr, top = nullptr;
-    int rc = AWPM_OK;
-    cudaError_t e;
+    Shape sh;
+    sh.num_sms = c->num_sms;
+    sh.batch = batch;
+    sh.lookup = lookup;
+    sh.search_bps = c->search_bps[batch ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0];
+    sh.pipe = c->search_pipe;
+    return sh;
+}
 
-    e = cudaStreamBeginCapture(s, mode);
-    if (e != cudaSuccess) {
-        note_cuda(e, "cudaStreamBeginCapture", __LINE__);
-        return AWPM_ERR_CUDA;
-    }
-    launch_init(wk, max_passes, c->num_sms, s);
-    launch_weight_sum(wk, false, s);
-    launch_batch_weight_sum(wk, false, s);
-    e = cudaStreamEndCapture(s, &g_init);
-    if (e != cudaSuccess) {
-        note_cuda(e, "capture of the initialisation", __LINE__);
-        return AWPM_ERR_CUDA;
-    }
-    e = cudaStreamBeginCapture(s, mode);
-    if (e == cudaSuccess) {
-        launch_weight_sum(wk, true, s);
-        launch_batch_weight_sum(wk, true, s);
-        e = cudaStreamEndCapture(s, &g_final);
-    }
-    if (e != cudaSuccess) {
-        note_cuda(e, "capture of the final reduction", __LINE__);
-        cudaGraphDestroy(g_init);
-        return AWPM_ERR_CUDA;
-    }
-
+// The solve graph of one launch shape: initialisation, WHILE{pass}, final
+// sum, assembled node by node (no stream capture).
+int build_graph(awpm_ctx *c, const Shape &sh, cudaGraphExec_t *out)
+{
+    const Work *d = (const Work *)c->d_work.p;
+    cudaGraph_t top = nullptr, g_init = nullptr, g_final = nullptr;
     cudaGraphNode_t n_init, n_cond, n_final;
     cudaGraphConditionalHandle h;
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    cudaGraph_t body = nullptr;
-    if ((e = cudaGraphCreate(&top, 0)) != cudaSuccess ||
-        (e = cudaGraphAddChildGraphNode(&n_init, top, nullptr, 0, g_init)) != cudaSuccess ||
+    int rc = AWPM_OK;
+    cudaError_t e;
+    Sink si, sf, sb;
+    if ((e = cudaGraphCreate(&g_init, 0)) != cudaSuccess ||
+        (e = cudaGraphCreate(&g_final, 0)) != cudaSuccess ||
+        (e = cudaGraphCreate(&top, 0)) != cudaSuccess) {
+        note_cuda_error(e, "cudaGraphCreate", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    si.graph = g_init;
+    launch_init(d, sh, si);
+    launch_weight_sum(d, sh, false, si);
+    sf.graph = g_final;
+    launch_weight_sum(d, sh, true, sf);
+    if (si.err != cudaSuccess || sf.err != cudaSuccess) {
+        note_cuda_error(si.err != cudaSuccess ? si.err : sf.err, "kernel nodes", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    if ((e = cudaGraphAddChildGraphNode(&n_init, top, nullptr, 0, g_init)) != cudaSuccess ||
         (e = cudaGraphConditionalHandleCreate(&h, top, 1, cudaGraphCondAssignDefault)) !=
             cudaSuccess) {
-        note_cuda(e, "graph assembly", __LINE__);
+        note_cuda_error(e, "graph assembly", __LINE__);
         rc = AWPM_ERR_CUDA;
         goto done;
     }
@@ -239,29 +189,24 @@ int build_graph(awpm_ctx *c, const Work &wk, int max_passes, int lookup)
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     if ((e = cudaGraphAddNode(&n_cond, top, &n_init, nullptr, 1, &cp)) != cudaSuccess) {
-        note_cuda(e, "conditional node", __LINE__);
+        note_cuda_error(e, "conditional node", __LINE__);
         rc = AWPM_ERR_CUDA;
         goto done;
     }
-    body = cp.conditional.phGraph_out[0];
-    if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, mode)) != cudaSuccess) {
-        note_cuda(e, "capture of the pass body", __LINE__);
-        rc = AWPM_ERR_CUDA;
-        goto done;
-    }
-    launch_reset_best(wk, s);
-    launch_search(wk, c->num_sms, s);
-    launch_select_and_flip(wk, c->num_sms, s);
-    launch_control(wk, true, h, s);
-    if ((e = cudaStreamEndCapture(s, &body)) != cudaSuccess) {
-        note_cuda(e, "capture of the pass body", __LINE__);
+    sb.graph = cp.conditional.phGraph_out[0];
+    launch_reset_best(d, sh, sb);
+    launch_search(d, sh, sb);
+    launch_select_and_flip(d, sh, sb);
+    launch_control(d, sh, true, h, sb);
+    if (sb.err != cudaSuccess) {
+        note_cuda_error(sb.err, "pass body nodes", __LINE__);
         rc = AWPM_ERR_CUDA;
         goto done;
     }
     if ((e = cudaGraphAddChildGraphNode(&n_final, top, &n_cond, 1, g_final)) != cudaSuccess ||
-        (e = cudaGraphInstantiate(&c->g_exec, top, 0)) != cudaSuccess) {
-        note_cuda(e, "graph instantiation", __LINE__);
-        c->g_exec = nullptr;
+        (e = cudaGraphInstantiate(out, top, 0)) != cudaSuccess) {
+        note_cuda_error(e, "graph instantiation", __LINE__);
+        *out = nullptr;
         rc = AWPM_ERR_CUDA;
         goto done;
     }
@@ -290,109 +235,40 @@ int ensure_timing_events(awpm_ctx *c, size_t pairs)
 // search launch; the host stays kLookahead passes ahead of the device and
 // stops enqueueing once a finished pass reports that the loop ended.  Passes
 // enqueued after the end are no-ops (every kernel checks ctl->active).
-int run_timed(awpm_ctx *c, const Work &wk, int max_passes, int lookup, double *ms_search,
-              int *passes_enqueued)
+int run_timed(awpm_ctx *c, const Shape &sh, int max_passes, int *passes_enqueued)
 {
     cudaStream_t s = c->stream;
-    launch_init(wk, max_passes, c->num_sms, s);
-    launch_weight_sum(wk, false, s);
-    launch_batch_weight_sum(wk, false, s);
-    AWPM_TRY(check_launch());
+    const Work *d = (const Work *)c->d_work.p;
+    Ctl *ctl = (Ctl *)c->ctl.p;
+    Sink k;
+    k.stream = s;
+    launch_init(d, sh, k);
+    launch_weight_sum(d, sh, false, k);
+    AWPM_TRY(check_sink(k));
     int t = 0;
     for (; t < max_passes; ++t) {
         if (t >= kLookahead) {
-            int slot = (t - kLookahead) % kRing;
+            const int slot = (t - kLookahead) % kRing;
             CUDA_TRY(cudaEventSynchronize(c->flagev[slot]));
             if (!c->h_active[slot])
                 break;
         }
         AWPM_TRY(ensure_timing_events(c, (size_t)t + 1));
-        launch_reset_best(wk, s);
+        launch_reset_best(d, sh, k);
         CUDA_TRY(cudaEventRecord(c->tev[2 * t], s));
-        launch_search(wk, c->num_sms, s);
+        launch_search(d, sh, k);
         CUDA_TRY(cudaEventRecord(c->tev[2 * t + 1], s));
-        launch_select_and_flip(wk, c->num_sms, s);
-        launch_control(wk, false, cudaGraphConditionalHandle(), s);
-        AWPM_TRY(check_launch());
-        CUDA_TRY(cudaMemcpyAsync(&c->h_active[t % kRing], &wk.ctl->active, sizeof(int32_t),
+        launch_select_and_flip(d, sh, k);
+        launch_control(d, sh, false, cudaGraphConditionalHandle(), k);
+        AWPM_TRY(check_sink(k));
+        CUDA_TRY(cudaMemcpyAsync(&c->h_active[t % kRing], &ctl->active, sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaEventRecord(c->flagev[t % kRing], s));
     }
-    launch_weight_sum(wk, true, s);
-    launch_batch_weight_sum(wk, true, s);
-    AWPM_TRY(check_launch());
+    launch_weight_sum(d, sh, true, k);
+    AWPM_TRY(check_sink(k));
     *passes_enqueued = t;
-    *ms_search = 0.0;
     return AWPM_OK;
-}
-
-int setup_ctx(awpm_ctx *c, const awpm_options *opt)
-{
-    if (opt)
-        c->opt = *opt;
-    else
-        awpm_default_options(&c->opt);
-    if (c->opt.max_iters < 0 || c->opt.lookup < 0 || c->opt.lookup > 2)
-        return AWPM_ERR_INVALID_ARG;
-    int dev = c->opt.device;
-    if (dev < 0)
-        CUDA_TRY(cudaGetDevice(&dev));
-    c->device = dev;
-    CUDA_TRY(cudaSetDevice(dev));
-    CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    c->search_u = default_search_u();
-    for (int b = 0; b < 2; ++b) {
-        c->search_bps[b][0] = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, c->search_u, b == 1);
-        c->search_bps[b][1] = search_blocks_per_sm(AWPM_LOOKUP_HASH, 1, b == 1);
-    }
-    if (c->opt.stream) {
-        c->stream = (cudaStream_t)c->opt.stream;
-        c->own_stream = false;
-    } else {
-        CUDA_TRY(cudaStreamCreate(&c->stream));
-        c->own_stream = true;
-    }
-    CUDA_TRY(cudaMallocHost((void **)&c->h_ctl, sizeof(Ctl)));
-    CUDA_TRY(cudaMallocHost((void **)&c->h_active, sizeof(int32_t) * kRing));
-    CUDA_TRY(cudaEventCreate(&c->ev_a));
-    CUDA_TRY(cudaEventCreate(&c->ev_b));
-    for (int i = 0; i < kRing; ++i) {
-        cudaEvent_t ev;
-        CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        c->flagev.push_back(ev);
-    }
-    return AWPM_OK;
-}
-
-void teardown_ctx(awpm_ctx *c)
-{
-    if (c->stream)
-        cudaStreamSynchronize(c->stream);
-    drop_graph(c);
-    DevBuf *bufs[] = {&c->mc, &c->mr, &c->wm, &c->rr, &c->wmr, &c->colsig, &c->best, &c->dsel,
-                      &c->tile_col, &c->starts, &c->htab, &c->b_noff, &c->b_colmat,
-                      &c->b_tilemat, &c->b_i32, &c->b_u64, &c->b_f64,
-                      &c->ctl, &c->wpart, &c->s_colptr, &c->s_rowidx, &c->s_w, &c->s_mate,
-                      &c->s_gain, &c->s_row};
-    for (DevBuf *b : bufs)
-        release(c, *b);
-    if (c->h_ctl)
-        cudaFreeHost(c->h_ctl);
-    if (c->h_batch)
-        cudaFreeHost(c->h_batch);
-    if (c->h_active)
-        cudaFreeHost(c->h_active);
-    for (cudaEvent_t ev : c->tev)
-        cudaEventDestroy(ev);
-    for (cudaEvent_t ev : c->flagev)
-        cudaEventDestroy(ev);
-    if (c->ev_a)
-        cudaEventDestroy(c->ev_a);
-    if (c->ev_b)
-        cudaEventDestroy(c->ev_b);
-    if (c->own_stream && c->stream)
-        cudaStreamDestroy(c->stream);
-    cudaGetLastError();
 }
 
 template <typename T>
@@ -409,50 +285,154 @@ int stage_in(awpm_ctx *c, DevBuf &buf, const T *src, size_t count, int loc, cons
     return AWPM_OK;
 }
 
-// The whole call: argument checks, staging, the solve (or the single
-// search), results and statistics.
-int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *weight,
-        const int32_t *mate_in, int32_t *mate_out, awpm_stats *st, bool search_only,
-        double *gain_out, int32_t *row_out, int32_t count = 0, const int32_t *n_off = nullptr,
-        awpm_stats *per_matrix = nullptr)
+std::mutex g_default_mu;
+std::map<int, awpm_ctx *> g_default;
+
+}  // namespace
+
+namespace awpm {
+
+size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup)
 {
-    if (!c || n < 0 || (n > 0 && (!colptr || !mate_in)) || (!search_only && n > 0 && !mate_out) ||
-        (search_only && n > 0 && (!gain_out || !row_out)))
+    const size_t N = (size_t)n, Z = (size_t)nnz, T = Z / kTile + 1;
+    size_t b = N * (4 + 4 + 8 + sizeof(RowRec) + 8 + 8 + sizeof(Rec) + sizeof(Sel)) + 4 * T +
+               4 * (Z / 32 + 1) + sizeof(Ctl) + 8 * kWsumBlocks;
+    if (lookup == AWPM_LOOKUP_HASH)
+        b += 16 * Z;
+    if (host_inputs)
+        b += 4 * (N + 1) + 12 * Z + 8 * N;
+    return b + b / 8;
+}
+
+size_t ctx_bytes_held(const awpm_ctx *c)
+{
+    return c->held;
+}
+
+int setup_ctx(awpm_ctx *c, const awpm_options *opt)
+{
+    if (opt)
+        c->opt = *opt;
+    else
+        awpm_default_options(&c->opt);
+    if (c->opt.max_iters < 0 || c->opt.lookup < 0 || c->opt.lookup > 2 || c->opt.slots < 0)
+        return AWPM_ERR_INVALID_ARG;
+    int dev = c->opt.device;
+    if (dev < 0)
+        CUDA_TRY(cudaGetDevice(&dev));
+    c->device = dev;
+    CUDA_TRY(cudaSetDevice(dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    c->search_pipe = default_search_pipe();
+    for (int b = 0; b < 2; ++b) {
+        c->search_bps[b][0] = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, b == 1, c->search_pipe);
+        c->search_bps[b][1] = search_blocks_per_sm(AWPM_LOOKUP_HASH, b == 1, c->search_pipe);
+    }
+    if (c->opt.stream) {
+        c->stream = (cudaStream_t)c->opt.stream;
+        c->own_stream = false;
+    } else {
+        CUDA_TRY(cudaStreamCreate(&c->stream));
+        c->own_stream = true;
+    }
+    AWPM_TRY(ensure(c, c->d_work, sizeof(Work)));
+    CUDA_TRY(cudaMallocHost((void **)&c->h_work, sizeof(Work)));
+    CUDA_TRY(cudaMallocHost((void **)&c->h_ctl, sizeof(Ctl)));
+    CUDA_TRY(cudaMallocHost((void **)&c->h_active, sizeof(int32_t) * kRing));
+    CUDA_TRY(cudaEventCreate(&c->ev_a));
+    CUDA_TRY(cudaEventCreate(&c->ev_b));
+    for (int i = 0; i < kRing; ++i) {
+        cudaEvent_t ev;
+        CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        c->flagev.push_back(ev);
+    }
+    return AWPM_OK;
+}
+
+void teardown_ctx(awpm_ctx *c)
+{
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    for (int b = 0; b < 2; ++b)
+        for (int h = 0; h < 2; ++h)
+            if (c->g_exec[b][h]) {
+                cudaGraphExecDestroy(c->g_exec[b][h]);
+                c->g_exec[b][h] = nullptr;
+            }
+    DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->wmr,
+                      &c->colsig,  &c->best,     &c->dsel,     &c->tile_col, &c->starts,
+                      &c->ctl,     &c->wpart,    &c->htab,     &c->b_noff,   &c->b_colmat,
+                      &c->b_tilemat, &c->b_i32,  &c->b_u64,    &c->b_f64,    &c->s_colptr,
+                      &c->s_rowidx, &c->s_w,     &c->s_mate,   &c->s_out,    &c->s_gain,
+                      &c->s_row,   &c->d_work};
+    for (DevBuf *b : bufs)
+        release(c, *b);
+    if (c->h_work)
+        cudaFreeHost(c->h_work);
+    if (c->h_ctl)
+        cudaFreeHost(c->h_ctl);
+    if (c->h_active)
+        cudaFreeHost(c->h_active);
+    if (c->h_batch)
+        cudaFreeHost(c->h_batch);
+    for (cudaEvent_t ev : c->tev)
+        cudaEventDestroy(ev);
+    for (cudaEvent_t ev : c->flagev)
+        cudaEventDestroy(ev);
+    if (c->ev_a)
+        cudaEventDestroy(c->ev_a);
+    if (c->ev_b)
+        cudaEventDestroy(c->ev_b);
+    if (c->own_stream && c->stream)
+        cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+}
+
+int ctx_enqueue(awpm_ctx *c, const Request &r)
+{
+    Pending &pd = c->pend;
+    pd = Pending();
+    const int32_t n = r.n;
+    if (n < 0 || (n > 0 && (!r.colptr || !r.mate_in)) ||
+        (!r.search_only && n > 0 && !r.mate_out) ||
+        (r.search_only && n > 0 && (!r.gain_out || !r.row_out)) || r.count < 0 ||
+        (r.count > 0 && !r.n_off))
         return AWPM_ERR_INVALID_ARG;
     CUDA_TRY(cudaSetDevice(c->device));
-    awpm_stats S;
-    std::memset(&S, 0, sizeof(S));
+    const int lookup = c->opt.lookup == AWPM_LOOKUP_HASH ? AWPM_LOOKUP_HASH : AWPM_LOOKUP_BSEARCH;
+    pd.lookup = lookup;
+    pd.search_only = r.search_only;
     if (n == 0) {
-        S.iterations = search_only ? 0 : 1;
-        S.converged = 1;
-        S.lookup_used = AWPM_LOOKUP_BSEARCH;
-        if (st)
-            *st = S;
+        pd.active = true;
+        pd.trivial = true;
         return AWPM_OK;
     }
-    const int l_colptr = where(c, colptr), l_rowidx = where(c, rowidx), l_w = where(c, weight),
-              l_mate = where(c, mate_in);
-    const int l_out = search_only ? 0 : where(c, mate_out);
-    const int l_gain = search_only ? where(c, gain_out) : 0;
-    const int l_row = search_only ? where(c, row_out) : 0;
+    const int l_colptr = where(c, r.colptr), l_rowidx = where(c, r.rowidx),
+              l_w = where(c, r.weight), l_mate = where(c, r.mate_in);
+    const int l_out = r.search_only ? 0 : where(c, r.mate_out);
+    const int l_gain = r.search_only ? where(c, r.gain_out) : 0;
+    const int l_row = r.search_only ? where(c, r.row_out) : 0;
+    const int l_off = r.count > 0 ? where(c, r.n_off) : 0;
     if (l_colptr < 0 || l_rowidx < 0 || l_w < 0 || l_mate < 0 || l_out < 0 || l_gain < 0 ||
-        l_row < 0)
+        l_row < 0 || l_off < 0)
         return AWPM_ERR_INVALID_ARG;
 
-    int32_t nnz = 0;
-    if (l_colptr == 1) {
-        CUDA_TRY(cudaMemcpyAsync(c->h_ctl, colptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                 c->stream));
-        CUDA_TRY(cudaStreamSynchronize(c->stream));
-        std::memcpy(&nnz, c->h_ctl, sizeof(int32_t));
-    } else {
-        nnz = colptr[n];
+    int32_t nnz = r.nnz;
+    if (nnz < 0) {
+        if (l_colptr == 1) {
+            CUDA_TRY(cudaMemcpyAsync(c->h_ctl, r.colptr + n, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            std::memcpy(&nnz, c->h_ctl, sizeof(int32_t));
+        } else {
+            nnz = r.colptr[n];
+        }
     }
-    if (nnz < 0 || (nnz > 0 && (!rowidx || !weight)))
+    if (nnz < 0 || (nnz > 0 && (!r.rowidx || !r.weight)))
         return AWPM_ERR_INVALID_ARG;
     const int32_t ntiles = (int32_t)(((int64_t)nnz + kTile - 1) / kTile);
     const int32_t max_passes = c->opt.max_iters > 0 ? c->opt.max_iters : AWPM_PASS_CAP;
-    const int lookup = c->opt.lookup == AWPM_LOOKUP_HASH ? AWPM_LOOKUP_HASH : AWPM_LOOKUP_BSEARCH;
+    const int32_t count = r.count;
 
     AWPM_TRY(ensure(c, c->mc, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->mr, sizeof(int32_t) * n));
@@ -470,25 +450,34 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
         AWPM_TRY(ensure(c, c->htab, sizeof(unsigned long long) * 2 * (size_t)nnz));
 
     CUDA_TRY(cudaEventRecord(c->ev_a, c->stream));
-    Work wk;
+    Work &wk = *c->h_work;
+    std::memset(&wk, 0, sizeof(Work));
     wk.n = n;
     wk.nnz = nnz;
     wk.ntiles = ntiles;
+    wk.max_passes = max_passes;
     wk.lookup = lookup;
+    AWPM_TRY(stage_in(c, c->s_colptr, r.colptr, (size_t)n + 1, l_colptr, &wk.colptr));
+    AWPM_TRY(stage_in(c, c->s_rowidx, r.rowidx, (size_t)nnz, l_rowidx, &wk.rowidx));
+    AWPM_TRY(stage_in(c, c->s_w, r.weight, (size_t)nnz, l_w, &wk.w));
+    AWPM_TRY(stage_in(c, c->s_mate, r.mate_in, (size_t)n, l_mate, &wk.mate_in));
+    wk.mc = (int32_t *)c->mc.p;
+    wk.mr = (int32_t *)c->mr.p;
+    wk.wm = (double *)c->wm.p;
+    wk.rr = (RowRec *)c->rr.p;
+    wk.wmr = (double *)c->wmr.p;
+    wk.colsig = (unsigned long long *)c->colsig.p;
     wk.htab = lookup == AWPM_LOOKUP_HASH ? (unsigned long long *)c->htab.p : nullptr;
-    wk.search_u = lookup == AWPM_LOOKUP_HASH ? 1 : c->search_u;
-    wk.search_bps = c->search_bps[count > 0 ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0];
-    AWPM_TRY(stage_in(c, c->s_colptr, colptr, (size_t)n + 1, l_colptr, &wk.colptr));
-    AWPM_TRY(stage_in(c, c->s_rowidx, rowidx, (size_t)nnz, l_rowidx, &wk.rowidx));
-    AWPM_TRY(stage_in(c, c->s_w, weight, (size_t)nnz, l_w, &wk.w));
-    AWPM_TRY(stage_in(c, c->s_mate, mate_in, (size_t)n, l_mate, &wk.mate_in));
+    wk.best = (Rec *)c->best.p;
+    wk.dsel = (Sel *)c->dsel.p;
+    wk.tile_col = (int32_t *)c->tile_col.p;
+    wk.starts = (uint32_t *)c->starts.p;
+    wk.ctl = (Ctl *)c->ctl.p;
+    wk.wpart = (double *)c->wpart.p;
     if (count > 0) {
-        const int l_off = where(c, n_off);
-        if (l_off < 0)
-            return AWPM_ERR_INVALID_ARG;
         BatchWork &bw = wk.bw;
         bw.count = count;
-        AWPM_TRY(stage_in(c, c->b_noff, n_off, (size_t)count + 1, l_off, &bw.n_off));
+        AWPM_TRY(stage_in(c, c->b_noff, r.n_off, (size_t)count + 1, l_off, &bw.n_off));
         AWPM_TRY(ensure(c, c->b_colmat, sizeof(int32_t) * n));
         AWPM_TRY(ensure(c, c->b_tilemat, sizeof(int32_t) * ((size_t)ntiles + 1)));
         AWPM_TRY(ensure(c, c->b_i32, sizeof(int32_t) * (5 * (size_t)count + 1)));
@@ -508,75 +497,58 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
         double *f64 = (double *)c->b_f64.p;
         bw.mw_in = f64;
         bw.mw_out = f64 + count;
+        pd.n_off.resize((size_t)count + 1);
+        if (l_off == 1)
+            CUDA_TRY(cudaMemcpyAsync(pd.n_off.data(), r.n_off, sizeof(int32_t) * (count + 1),
+                                     cudaMemcpyDeviceToHost, c->stream));
+        else
+            std::memcpy(pd.n_off.data(), r.n_off, sizeof(int32_t) * (count + 1));
     }
-    wk.mc = (int32_t *)c->mc.p;
-    wk.mr = (int32_t *)c->mr.p;
-    wk.wm = (double *)c->wm.p;
-    wk.rr = (RowRec *)c->rr.p;
-    wk.wmr = (double *)c->wmr.p;
-    wk.colsig = (unsigned long long *)c->colsig.p;
-    wk.best = (Rec *)c->best.p;
-    wk.dsel = (Sel *)c->dsel.p;
-    wk.tile_col = (int32_t *)c->tile_col.p;
-    wk.starts = (uint32_t *)c->starts.p;
-    wk.ctl = (Ctl *)c->ctl.p;
-    wk.wpart = (double *)c->wpart.p;
-
-    int passes_enqueued = 0;
-    double ms_search = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(c->d_work.p, c->h_work, sizeof(Work), cudaMemcpyHostToDevice,
+                             c->stream));
+    const Work *d = (const Work *)c->d_work.p;
+    const Shape sh = shape_of(c, count > 0, lookup);
     const bool timed = (c->opt.flags & AWPM_FLAG_TIME_SEARCH) != 0;
-    if (search_only) {
-        launch_init(wk, 1, c->num_sms, c->stream);
-        launch_search(wk, c->num_sms, c->stream);
-        double *g = gain_out;
-        int32_t *r = row_out;
+
+    if (r.search_only) {
+        Sink k;
+        k.stream = c->stream;
+        launch_init(d, sh, k);
+        launch_search(d, sh, k);
+        double *g = r.gain_out;
+        int32_t *row = r.row_out;
         if (l_gain != 1) {
             AWPM_TRY(ensure(c, c->s_gain, sizeof(double) * n));
             g = (double *)c->s_gain.p;
         }
         if (l_row != 1) {
             AWPM_TRY(ensure(c, c->s_row, sizeof(int32_t) * n));
-            r = (int32_t *)c->s_row.p;
+            row = (int32_t *)c->s_row.p;
         }
-        launch_export_stepc(wk, g, r, c->stream);
-        AWPM_TRY(check_launch());
+        launch_export_stepc(d, sh, g, row, k);
+        AWPM_TRY(check_sink(k));
         if (l_gain != 1)
-            CUDA_TRY(cudaMemcpyAsync(gain_out, g, sizeof(double) * n, cudaMemcpyDeviceToHost,
+            CUDA_TRY(cudaMemcpyAsync(r.gain_out, g, sizeof(double) * n, cudaMemcpyDeviceToHost,
                                      c->stream));
         if (l_row != 1)
-            CUDA_TRY(cudaMemcpyAsync(row_out, r, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+            CUDA_TRY(cudaMemcpyAsync(r.row_out, row, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
                                      c->stream));
     } else if (timed) {
-        AWPM_TRY(run_timed(c, wk, max_passes, lookup, &ms_search, &passes_enqueued));
+        AWPM_TRY(run_timed(c, sh, max_passes, &pd.passes_enqueued));
     } else {
-        GraphKey key;
-        key.n = n;
-        key.nnz = nnz;
-        key.max_passes = max_passes;
-        key.lookup = lookup;
-        key.colptr = wk.colptr;
-        key.rowidx = wk.rowidx;
-        key.w = wk.w;
-        key.mate_in = wk.mate_in;
-        key.count = count;
-        key.n_off = wk.bw.n_off;
-        if (!c->g_valid || !(c->g_key == key)) {
-            drop_graph(c);
-            AWPM_TRY(build_graph(c, wk, max_passes, lookup));
-            c->g_key = key;
-            c->g_valid = true;
-        }
-        CUDA_TRY(cudaGraphLaunch(c->g_exec, c->stream));
+        cudaGraphExec_t &g = c->g_exec[count > 0 ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0];
+        if (!g)
+            AWPM_TRY(build_graph(c, sh, &g));
+        CUDA_TRY(cudaGraphLaunch(g, c->stream));
     }
-    if (!search_only) {
-        CUDA_TRY(cudaMemcpyAsync(mate_out, wk.mc, sizeof(int32_t) * n,
+    if (!r.search_only)
+        CUDA_TRY(cudaMemcpyAsync(r.mate_out, wk.mc, sizeof(int32_t) * n,
                                  l_out == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                  c->stream));
-    }
     CUDA_TRY(cudaMemcpyAsync(c->h_ctl, wk.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
-    // per-matrix results: miter, mconv, mnnz (3 x i32), mcycles (u64), mw_in, mw_out (f64)
-    const size_t pm_bytes = (size_t)count * (3 * sizeof(int32_t) + 3 * 8);
-    if (count > 0 && per_matrix) {
+    if (count > 0) {
+        // per-matrix results: miter, mconv, mnnz (i32), mcycles (u64), mw_in, mw_out (f64)
+        const size_t pm_bytes = (size_t)count * (3 * sizeof(int32_t) + 3 * 8);
         if (c->h_batch_bytes < pm_bytes) {
             if (c->h_batch)
                 cudaFreeHost(c->h_batch);
@@ -594,14 +566,38 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
                                  cudaMemcpyDeviceToHost, c->stream));
     }
     CUDA_TRY(cudaEventRecord(c->ev_b, c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    pd.active = true;
+    pd.timed = timed && !r.search_only;
+    pd.n = n;
+    pd.nnz = nnz;
+    pd.count = count;
+    return AWPM_OK;
+}
 
+int ctx_finish(awpm_ctx *c, awpm_stats *st, awpm_stats *per_matrix)
+{
+    Pending &pd = c->pend;
+    if (!pd.active)
+        return AWPM_ERR_INVALID_ARG;
+    pd.active = false;
+    awpm_stats S;
+    std::memset(&S, 0, sizeof(S));
+    S.lookup_used = pd.lookup;
+    if (pd.trivial) {
+        S.iterations = pd.search_only ? 0 : 1;
+        S.converged = 1;
+        if (st)
+            *st = S;
+        return AWPM_OK;
+    }
+    CUDA_TRY(cudaEventSynchronize(c->ev_b));
     const Ctl &h = *c->h_ctl;
-    int rc = code_of(h.err);
+    const int rc = code_of(h.err);
     if (rc != AWPM_OK)
         return rc;
-    if (timed && !search_only) {
-        for (int t = 0; t < h.iterations && t < passes_enqueued; ++t) {
+    double ms_search = 0.0;
+    if (pd.timed) {
+        for (int t = 0; t < h.iterations && t < pd.passes_enqueued; ++t) {
             float ms = 0.f;
             CUDA_TRY(cudaEventElapsedTime(&ms, c->tev[2 * t], c->tev[2 * t + 1]));
             ms_search += ms;
@@ -612,16 +608,16 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     S.iterations = h.iterations;
     S.converged = h.converged;
     S.cycles_applied = (int64_t)h.cycles;
-    S.edge_checks = (int64_t)(nnz - n) * (int64_t)(search_only ? 1 : h.iterations);
+    S.edge_checks = (int64_t)(pd.nnz - pd.n) * (int64_t)(pd.search_only ? 1 : h.iterations);
     S.candidates = (int64_t)h.candidates;
     S.closing_found = (int64_t)h.found;
     S.positive = (int64_t)h.positive;
     S.weight_in = h.weight_in;
-    S.weight_out = search_only ? h.weight_in : h.weight_out;
+    S.weight_out = pd.search_only ? h.weight_in : h.weight_out;
     S.ms_total = ms_total;
     S.ms_search = ms_search;
-    S.lookup_used = lookup;
-    if (count > 0 && per_matrix) {
+    if (pd.count > 0) {
+        const int32_t count = pd.count;
         const char *hb = (const char *)c->h_batch;
         const int32_t *miter = (const int32_t *)hb;
         const int32_t *mconv = miter + count;
@@ -629,44 +625,33 @@ int run(awpm_ctx *c, int32_t n, const int32_t *colptr, const int32_t *rowidx, co
         const unsigned long long *mcyc = (const unsigned long long *)(hb + 12 * (size_t)count);
         const double *mwi = (const double *)(hb + 20 * (size_t)count);
         const double *mwo = mwi + count;
-        std::vector<int32_t> off((size_t)count + 1);
-        if (where(c, n_off) == 1)
-            CUDA_TRY(cudaMemcpy(off.data(), n_off, sizeof(int32_t) * off.size(),
-                                cudaMemcpyDeviceToHost));
-        else
-            std::memcpy(off.data(), n_off, sizeof(int32_t) * off.size());
         int all_conv = 1;
+        S.edge_checks = 0;
         for (int32_t b = 0; b < count; ++b) {
+            const int64_t ec = (int64_t)(mnnz[b] - (pd.n_off[b + 1] - pd.n_off[b])) * miter[b];
+            S.edge_checks += ec;
+            all_conv &= mconv[b];
+            if (!per_matrix)
+                continue;
             awpm_stats &m = per_matrix[b];
             std::memset(&m, 0, sizeof(m));
             m.iterations = miter[b];
             m.converged = mconv[b];
-            all_conv &= mconv[b];
             m.cycles_applied = (int64_t)mcyc[b];
-            m.edge_checks = (int64_t)(mnnz[b] - (off[b + 1] - off[b])) * miter[b];
+            m.edge_checks = ec;
             m.weight_in = mwi[b];
             m.weight_out = mwo[b];
             m.ms_total = ms_total;
-            m.lookup_used = lookup;
+            m.lookup_used = pd.lookup;
         }
         S.converged = all_conv;
-    }
-    if (count > 0) {
-        // edge checks of a batch: each matrix counts only its own passes
-        S.edge_checks = 0;
-        if (per_matrix)
-            for (int32_t b = 0; b < count; ++b)
-                S.edge_checks += per_matrix[b].edge_checks;
     }
     if (st)
         *st = S;
     return AWPM_OK;
 }
 
-std::mutex g_default_mu;
-std::map<int, awpm_ctx *> g_default;
-
-}  // namespace
+}  // namespace awpm
 
 extern "C" {
 
@@ -683,6 +668,7 @@ const char *awpm_strerror(int code)
     case AWPM_ERR_CUDA: return "CUDA error";
     case AWPM_ERR_TIMEOUT: return "bounded device wait gave up";
     case AWPM_ERR_NOT_FOUND: return "unknown ticket";
+    case AWPM_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of awpm_search_noalloc";
     default: return "unknown error";
     }
 }
@@ -703,6 +689,7 @@ void awpm_default_options(awpm_options *opt)
     opt->flags = 0;
     opt->stream = nullptr;
     opt->mem_budget_bytes = 0;
+    opt->slots = 0;
 }
 
 int awpm_create(awpm_ctx **out, const awpm_options *opt)
@@ -723,10 +710,13 @@ int awpm_create(awpm_ctx **out, const awpm_options *opt)
     return AWPM_OK;
 }
 
+void awpm_server_shutdown(awpm_ctx *ctx);
+
 int awpm_destroy(awpm_ctx *ctx)
 {
     if (!ctx)
         return AWPM_OK;
+    awpm_server_shutdown(ctx);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         cudaSetDevice(ctx->device);
@@ -736,14 +726,34 @@ int awpm_destroy(awpm_ctx *ctx)
     return AWPM_OK;
 }
 
+static int solve_sync(awpm_ctx *c, const Request &r, awpm_stats *st, awpm_stats *per_matrix)
+{
+    std::lock_guard<std::mutex> lk(c->mu);
+    int rc = ctx_enqueue(c, r);
+    if (rc != AWPM_OK) {
+        if (c->stream)
+            cudaStreamSynchronize(c->stream);
+        cudaGetLastError();
+        c->pend.active = false;
+        return rc;
+    }
+    return ctx_finish(c, st, per_matrix);
+}
+
 int awpm_improve_ctx(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
                      const double *weight, const int32_t *mate_in, int32_t *mate_out,
                      awpm_stats *stats)
 {
     if (!ctx)
         return AWPM_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    return run(ctx, n, colptr, rowidx, weight, mate_in, mate_out, stats, false, nullptr, nullptr);
+    Request r;
+    r.n = n;
+    r.colptr = colptr;
+    r.rowidx = rowidx;
+    r.weight = weight;
+    r.mate_in = mate_in;
+    r.mate_out = mate_out;
+    return solve_sync(ctx, r, stats, nullptr);
 }
 
 int awpm_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *weight,
@@ -752,7 +762,7 @@ int awpm_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
-        note_cuda(e, "cudaGetDevice", __LINE__);
+        note_cuda_error(e, "cudaGetDevice", __LINE__);
         return AWPM_ERR_CUDA;
     }
     awpm_ctx *c = nullptr;
@@ -780,7 +790,6 @@ int awpm_improve_batch(awpm_ctx *ctx, int32_t count, const int32_t *n_off, const
 {
     if (!ctx || count < 0 || (count > 0 && !n_off))
         return AWPM_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(ctx->mu);
     if (count == 0) {
         if (total) {
             std::memset(total, 0, sizeof(*total));
@@ -788,31 +797,31 @@ int awpm_improve_batch(awpm_ctx *ctx, int32_t count, const int32_t *n_off, const
         }
         return AWPM_OK;
     }
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) {
-        note_cuda(e, "cudaSetDevice", __LINE__);
-        return AWPM_ERR_CUDA;
-    }
     int32_t n = 0;
-    if (where(ctx, n_off) == 1) {
-        e = cudaMemcpy(&n, n_off + count, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e == cudaSuccess && where(ctx, n_off) == 1)
+            e = cudaMemcpy(&n, n_off + count, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        else if (e == cudaSuccess)
+            n = n_off[count];
         if (e != cudaSuccess) {
-            note_cuda(e, "cudaMemcpy", __LINE__);
+            note_cuda_error(e, "reading the batch offsets", __LINE__);
             return AWPM_ERR_CUDA;
         }
-    } else {
-        n = n_off[count];
     }
     if (n <= 0)
         return AWPM_ERR_INVALID_ARG;
-    std::vector<awpm_stats> tmp;
-    awpm_stats *pm = per_matrix;
-    if (!pm) {
-        tmp.resize((size_t)count);
-        pm = tmp.data();
-    }
-    return run(ctx, n, colptr, rowidx, weight, mate_in, mate_out, total, false, nullptr, nullptr,
-               count, n_off, pm);
+    Request r;
+    r.n = n;
+    r.colptr = colptr;
+    r.rowidx = rowidx;
+    r.weight = weight;
+    r.mate_in = mate_in;
+    r.mate_out = mate_out;
+    r.count = count;
+    r.n_off = n_off;
+    return solve_sync(ctx, r, total, per_matrix);
 }
 
 int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
@@ -821,8 +830,16 @@ int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
 {
     if (!ctx)
         return AWPM_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    return run(ctx, n, colptr, rowidx, weight, mate, nullptr, stats, true, stepc_gain, stepc_row);
+    Request r;
+    r.n = n;
+    r.colptr = colptr;
+    r.rowidx = rowidx;
+    r.weight = weight;
+    r.mate_in = mate;
+    r.search_only = true;
+    r.gain_out = stepc_gain;
+    r.row_out = stepc_row;
+    return solve_sync(ctx, r, stats, nullptr);
 }
 
 }  // extern "C"

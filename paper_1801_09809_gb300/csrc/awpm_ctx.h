@@ -1,0 +1,91 @@
+// Host-side context of libawpm, shared by the synchronous entry points
+// (awpm_api.cu) and the request server (awpm_serve.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "awpm.h"
+#include "awpm_internal.h"
+
+namespace awpm {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// One problem handed to a context (single, batched or search only).
+struct Request {
+    int32_t n = 0;
+    int32_t nnz = -1;  // -1: read colptr[n]
+    const int32_t *colptr = nullptr;
+    const int32_t *rowidx = nullptr;
+    const double *weight = nullptr;
+    const int32_t *mate_in = nullptr;
+    int32_t *mate_out = nullptr;
+    int32_t count = 0;  // > 0: batched union with offsets n_off
+    const int32_t *n_off = nullptr;
+    bool search_only = false;
+    double *gain_out = nullptr;
+    int32_t *row_out = nullptr;
+};
+
+// What finish() needs to turn the device results into statistics.
+struct Pending {
+    bool active = false;
+    int32_t n = 0, nnz = 0, count = 0, lookup = 0;
+    bool search_only = false, timed = false, trivial = false;
+    int passes_enqueued = 0;
+    std::vector<int32_t> n_off;  // host copy of the batch offsets
+};
+
+int setup_ctx(struct ::awpm_ctx *c, const awpm_options *opt);
+void teardown_ctx(struct ::awpm_ctx *c);
+// Enqueue a whole solve on the context's stream without waiting for it;
+// the context's done event is recorded after the last copy.
+int ctx_enqueue(struct ::awpm_ctx *c, const Request &r);
+// Wait for the enqueued solve (a no-op if it already finished) and fill the
+// statistics (per_matrix: count entries for a batch, may be null).
+int ctx_finish(struct ::awpm_ctx *c, awpm_stats *st, awpm_stats *per_matrix);
+// Device bytes a context needs to solve a problem of this size.
+size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup);
+size_t ctx_bytes_held(const struct ::awpm_ctx *c);
+void note_cuda_error(cudaError_t e, const char *what, int line);
+
+}  // namespace awpm
+
+struct awpm_ctx {
+    std::mutex mu;
+    awpm_options opt{};
+    int device = 0;
+    int num_sms = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t held = 0;
+    int search_bps[2][2] = {{1, 1}, {1, 1}};  // [batch][hash]
+    bool search_pipe = true;
+    // per-solve device workspace
+    awpm::DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
+    awpm::DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
+    // staging of host-resident arrays
+    awpm::DevBuf s_colptr, s_rowidx, s_w, s_mate, s_out, s_gain, s_row;
+    awpm::DevBuf d_work;             // device copy of the Work descriptor
+    awpm::Work *h_work = nullptr;    // pinned
+    awpm::Ctl *h_ctl = nullptr;      // pinned
+    int32_t *h_active = nullptr;     // pinned ring of the timed loop
+    void *h_batch = nullptr;         // pinned per-matrix results
+    size_t h_batch_bytes = 0;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    std::vector<cudaEvent_t> tev;     // timing pairs of the timed loop
+    std::vector<cudaEvent_t> flagev;  // ring of the timed loop
+    // one instantiated graph per [batch][hash]
+    cudaGraphExec_t g_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    awpm::Pending pend;
+    // the request server of this context (awpm_submit), created on first use
+    struct awpm_server_impl *server = nullptr;
+};

@@ -1,4 +1,4 @@
-// Internal declarations shared by the kernels and the host API of libawpm.
+// Internal declarations shared by the kernels and the host side of libawpm.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -6,11 +6,13 @@
 
 namespace awpm {
 
-// Nonzeros handled by one warp per tile of the edge-parallel kernels.
+// Nonzeros handled by one warp per tile of the edge-parallel kernels; tiles
+// start at multiples of kTile, so tile t owns word t of the column-start
+// bitmap.
 constexpr int kTile = 32;
 
-// Error bits raised by the device-side validation; the host maps the lowest
-// set bit to the public code (priority INVALID > UNSORTED > NONFINITE > NOTPERF).
+// Error bits raised by the device-side validation; the host maps them to the
+// public code (priority INVALID > UNSORTED > NONFINITE > NOTPERF).
 constexpr unsigned kErrInvalid = 1u;
 constexpr unsigned kErrUnsorted = 2u;
 constexpr unsigned kErrNonfinite = 4u;
@@ -64,32 +66,36 @@ struct Ctl {
 // Batched solve of many independent matrices as one block-diagonal union
 // (count > 0).  Matrix b owns columns and rows [n_off[b], n_off[b+1]).
 struct BatchWork {
-    int32_t count = 0;
-    const int32_t *n_off = nullptr;  // count + 1 offsets
-    int32_t *colmat = nullptr;       // matrix of each column
-    int32_t *tilemat = nullptr;      // matrix of each tile's first nonzero | kTileSingle
-    int32_t *mdone = nullptr;        // matrix finished (converged or pass cap)
-    int32_t *miter = nullptr;        // passes run per matrix
-    int32_t *mconv = nullptr;        // converged per matrix
-    int32_t *mnnz = nullptr;         // nonzeros per matrix
-    unsigned long long *mflips = nullptr;   // cycles flipped in the running pass
-    unsigned long long *mcycles = nullptr;  // cycles flipped in total
-    double *mw_in = nullptr;
-    double *mw_out = nullptr;
-    int32_t *active = nullptr;       // matrices still running after a pass
+    int32_t count;
+    int32_t pad;
+    const int32_t *n_off;   // count + 1 offsets
+    int32_t *colmat;        // matrix of each column
+    int32_t *tilemat;       // matrix of each tile's first nonzero | kTileSingle
+    int32_t *mdone;         // matrix finished (converged or pass cap)
+    int32_t *miter;         // passes run per matrix
+    int32_t *mconv;         // converged per matrix
+    int32_t *mnnz;          // nonzeros per matrix
+    unsigned long long *mflips;   // cycles flipped in the running pass
+    unsigned long long *mcycles;  // cycles flipped in total
+    double *mw_in;
+    double *mw_out;
+    int32_t *active;        // matrices still running after a pass
 };
 
 // Tile whose nonzeros all belong to one matrix.
 constexpr int32_t kTileSingle = (int32_t)0x80000000;
 
-// Device pointers of one solve.
+// Descriptor of one solve.  It lives in device memory and every kernel reads
+// it from there, so launch configurations do not depend on the problem and
+// one instantiated CUDA graph serves every problem of a context: a new
+// problem only rewrites the descriptor before the graph launch.
 struct Work {
     int32_t n;
     int32_t nnz;
     int32_t ntiles;
-    int32_t lookup;      // AWPM_LOOKUP_BSEARCH or AWPM_LOOKUP_HASH
-    int32_t search_u;    // tiles in flight per warp in the search kernel (1, 2, 4)
-    int32_t search_bps;  // resident blocks per SM of that search kernel
+    int32_t max_passes;
+    int32_t lookup;     // AWPM_LOOKUP_BSEARCH or AWPM_LOOKUP_HASH
+    int32_t pad;
     const int32_t *colptr;
     const int32_t *rowidx;
     const double *w;
@@ -107,27 +113,46 @@ struct Work {
     uint32_t *starts;   // bit p set when a column starts at nonzero p
     Ctl *ctl;
     double *wpart;      // partial sums of the weight reduction
-    BatchWork bw;       // batched solve (bw.count > 0), else unused
+    BatchWork bw;       // batched solve (bw.count > 0), else zero
+};
+
+// Launch shape of a context: fixed grids sized by the GPU, not the problem.
+struct Shape {
+    int num_sms;
+    int search_bps;     // resident blocks per SM of the chosen search kernel
+    int lookup;         // AWPM_LOOKUP_BSEARCH or AWPM_LOOKUP_HASH
+    bool batch;
+    bool pipe;          // search kernel prefetches the next tile
 };
 
 constexpr int kWsumBlocks = 256;
 constexpr int kWsumThreads = 256;
 
-// Launchers (all asynchronous on `s`).  `num_sms` sizes persistent grids.
-void launch_init(const Work &wk, int max_passes, int num_sms, cudaStream_t s);
-void launch_weight_sum(const Work &wk, bool out, cudaStream_t s);
-void launch_search(const Work &wk, int num_sms, cudaStream_t s);
-void launch_select_and_flip(const Work &wk, int num_sms, cudaStream_t s);
-void launch_control(const Work &wk, bool graph, cudaGraphConditionalHandle h, cudaStream_t s);
-// Per-matrix weight sums of a batched solve.
-void launch_batch_weight_sum(const Work &wk, bool out, cudaStream_t s);
-void launch_export_stepc(const Work &wk, double *gain, int32_t *row, cudaStream_t s);
-void launch_reset_best(const Work &wk, cudaStream_t s);
-// Resident blocks per SM of the search kernel for a lookup strategy and u
-// tiles in flight per warp (for a one-wave grid).
-int search_blocks_per_sm(int lookup, int u, bool batch);
-// Default tiles in flight per warp; the environment variable AWPM_SEARCH_U
-// (1, 2 or 4) overrides it, as a tuning knob.
-int default_search_u();
+// Where launches go: a stream (launched at once, asynchronously) or a graph
+// (appended as kernel nodes, each depending on the previous one).  Graphs are
+// built node by node rather than by stream capture, so building one never
+// interacts with work other threads submit meanwhile.
+struct Sink {
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphNode_t last = nullptr;
+    cudaError_t err = cudaSuccess;
+    void launch(const void *func, unsigned grid, unsigned block, void **args);
+};
+
+// Launch sequences; `d` is the device copy of the Work.
+void launch_init(const Work *d, const Shape &sh, Sink &k);
+void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k);
+void launch_reset_best(const Work *d, const Shape &sh, Sink &k);
+void launch_search(const Work *d, const Shape &sh, Sink &k);
+void launch_select_and_flip(const Work *d, const Shape &sh, Sink &k);
+void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,
+                    Sink &k);
+void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k);
+// Resident blocks per SM of the search kernel for a lookup strategy.
+int search_blocks_per_sm(int lookup, bool batch, bool pipe);
+// Whether the search kernel prefetches the next tile (default on; the
+// environment variable AWPM_SEARCH_PIPE=0/1 overrides it, a tuning knob).
+bool default_search_pipe();
 
 }  // namespace awpm

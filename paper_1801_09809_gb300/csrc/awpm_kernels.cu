@@ -7,6 +7,10 @@
 // segmented arg-max inside each warp plus a 128-bit compare-and-swap for the
 // columns that straddle a tile boundary, and Step D is one compare-and-swap
 // selection per key column followed by an in-place flip.
+//
+// Every kernel reads the problem from a device-resident descriptor (Work) and
+// runs a fixed, GPU-sized grid with grid-stride loops, so one instantiated
+// CUDA graph serves every problem of a context.
 #include <math.h>
 #include <stdlib.h>
 
@@ -22,6 +26,25 @@ namespace awpm {
 // the loop ends long before this; the bound only turns a broken invariant
 // into an error bit instead of a hang).
 constexpr int kCasRetryCap = 1 << 20;
+
+// Closing-edge ranges longer than this go to the warp-cooperative search.
+constexpr int32_t kCoopMin = 32;
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int64_t gtid()
+{
+    return blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+}
+
+__device__ __forceinline__ int64_t gstride()
+{
+    return (int64_t)gridDim.x * blockDim.x;
+}
 
 __device__ __forceinline__ void raise_err(Ctl *ctl, unsigned bits)
 {
@@ -78,96 +101,7 @@ __device__ void block_add_u64(unsigned long long v, unsigned long long *dst)
     }
 }
 
-// ---------------------------------------------------------------------------
-// Initialisation and validation (before the loop of Algorithm 2)
-// ---------------------------------------------------------------------------
-
-__global__ void k_init_ctl(Ctl *ctl, int32_t max_passes)
-{
-    ctl->active = 1;
-    ctl->max_passes = max_passes;
-}
-
-// colptr[0] = 0, non-decreasing, colptr[n] = nnz.
-__global__ void k_check_colptr(int32_t n, int32_t nnz, const int32_t *__restrict__ colptr, Ctl *ctl)
-{
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j > n)
-        return;
-    int32_t c = colptr[j];
-    bool bad = (j == 0 && c != 0) || (j < n && colptr[j + 1] < c) || (j == n && c != nnz);
-    if (bad)
-        raise_err(ctl, kErrInvalid);
-}
-
-// Column-start bitmap and the first column of every tile.
-__global__ void k_mark_starts(int32_t n, const int32_t *__restrict__ colptr, uint32_t *starts,
-                              int32_t *tile_col, Ctl *ctl)
-{
-    if (ctl->err)
-        return;
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n)
-        return;
-    int32_t s = colptr[j], e = colptr[j + 1];
-    if (s < e) {
-        atomicOr(&starts[s >> 5], 1u << (s & 31));
-        for (int64_t t = ((int64_t)s + kTile - 1) / kTile; t * kTile < e; ++t)
-            tile_col[t] = (int32_t)j;
-    }
-}
-
-// Row range, sortedness inside columns, finite weights.
-__global__ void k_check_entries(int32_t n, int32_t nnz, const int32_t *__restrict__ rowidx,
-                                const double *__restrict__ w, const uint32_t *__restrict__ starts,
-                                Ctl *ctl)
-{
-    if (ctl->err & kErrInvalid)
-        return;
-    unsigned bits = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += stride) {
-        int32_t r = __ldcs(rowidx + p);
-        if (r < 0 || r >= n)
-            bits |= kErrInvalid;
-        if (!isfinite(__ldcs(w + p)))
-            bits |= kErrNonfinite;
-        if (p > 0 && !((starts[p >> 5] >> (p & 31)) & 1u) && rowidx[p - 1] >= r)
-            bits |= kErrUnsorted;
-    }
-    bits = __reduce_or_sync(FULL_MASK, bits);
-    if ((threadIdx.x & 31) == 0 && bits)
-        raise_err(ctl, bits);
-}
-
-// mc = mate_in, mr = its inverse, wm[j] = w(mate_in[j], j); checks that
-// mate_in is a permutation over stored entries.  mr must hold -1 on entry.
-__global__ void k_init_mates(int32_t n, const int32_t *__restrict__ colptr,
-                             const int32_t *__restrict__ rowidx, const double *__restrict__ w,
-                             const int32_t *__restrict__ mate_in, int32_t *mc, int32_t *mr,
-                             double *wm, Ctl *ctl)
-{
-    if (ctl->err)
-        return;
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n)
-        return;
-    int32_t r = mate_in[j];
-    mc[j] = r;
-    if (r < 0 || r >= n) {
-        raise_err(ctl, kErrNotPerfect);
-        return;
-    }
-    if (atomicCAS(&mr[r], -1, (int32_t)j) != -1)
-        raise_err(ctl, kErrNotPerfect);
-    int32_t q = find_row(rowidx, colptr[j], colptr[j + 1], r);
-    if (q < 0)
-        raise_err(ctl, kErrNotPerfect);
-    else
-        wm[j] = w[q];
-}
-
-// Deterministic two-stage sum of wm (fixed grid, fixed tree).
+// Deterministic block sum (fixed tree).  All threads call.
 __device__ double block_sum_f64(double v)
 {
     __shared__ double sm[32];
@@ -189,118 +123,34 @@ __device__ double block_sum_f64(double v)
     return v;
 }
 
-__global__ void k_wsum_partial(int32_t n, const double *__restrict__ wm, double *part, const Ctl *ctl)
-{
-    double s = 0.0;
-    if (ctl->err == 0u) {
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += stride)
-            s += wm[j];
-    }
-    s = block_sum_f64(s);
-    if (threadIdx.x == 0)
-        part[blockIdx.x] = s;
-}
-
-__global__ void k_wsum_final(const double *__restrict__ part, Ctl *ctl, int out)
-{
-    double s = block_sum_f64(part[threadIdx.x]);
-    if (threadIdx.x == 0) {
-        if (out)
-            ctl->weight_out = s;
-        else
-            ctl->weight_in = s;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Row records (range + signature of the column matched to each row)
-// ---------------------------------------------------------------------------
-
 // Bit of row r in a column signature (multiplicative hash, top 6 bits).
 __device__ __forceinline__ unsigned sig_bit(int32_t r)
 {
     return ((uint32_t)r * 0x9E3779B1u) >> 26;
 }
 
-// Column of the lane's nonzero inside a tile of kTile consecutive nonzeros
-// starting in column c0: the lane counts the column ends <= p among the 32
-// ends colptr[c0+1 .. c0+32] held one per lane in `e` (a tile spans at most
-// 32 columns when no column is empty).
-__device__ __forceinline__ int32_t lane_column_offset(int32_t e, int32_t p)
+// Column of the lane's nonzero: c0 (column of the tile's first nonzero) plus
+// the columns starting after the tile's first nonzero and up to this lane.
+// Exact when no column is empty (guaranteed once the matching validated).
+__device__ __forceinline__ int32_t lane_column(int32_t c0, uint32_t mask, int lane)
 {
-    int32_t cnt = 0;
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        int32_t v = __shfl_sync(FULL_MASK, e, cnt + s - 1);
-        if (v <= p)
-            cnt += s;
-    }
-    int32_t v = __shfl_sync(FULL_MASK, e, cnt);
-    if (v <= p)
-        cnt += 1;
-    return cnt;
+    return c0 + __popc(mask & ((2u << lane) - 1u) & ~1u);
 }
 
-// Signature of every column: OR of 1 << sig_bit(r) over its rows.  Edge
-// parallel; lanes of one column are OR-ed inside the warp, then one atomic
-// per column segment.  colsig must be zero on entry.
-__global__ void __launch_bounds__(256)
-k_colsig(int32_t n, int32_t nnz, int32_t ntiles, const int32_t *__restrict__ colptr,
-         const int32_t *__restrict__ rowidx, const int32_t *__restrict__ tile_col,
-         unsigned long long *colsig, const Ctl *ctl)
+// The segment of a column that starts at `lane` covers the whole column when
+// the column starts here and ends inside the tile: a later start bit, the
+// end of the matrix, or a column starting the next tile.
+__device__ __forceinline__ bool segment_complete(uint32_t mask, int lane, int32_t base,
+                                                 int32_t nnz, const uint32_t *starts, int64_t t)
 {
-    if (ctl->err)
-        return;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = warp0; t < ntiles; t += nwarps) {
-        const int32_t base = (int32_t)(t * kTile);
-        const int32_t p = base + lane;
-        const bool valid = p < nnz;
-        const int32_t c0 = tile_col[t];
-        const int64_t ck = (int64_t)c0 + 1 + lane;
-        const int32_t e = (ck <= n) ? colptr[ck] : 0x7fffffff;
-        const int32_t cnt = lane_column_offset(e, p);
-        const int32_t j = valid ? c0 + cnt : -1 - lane;
-        unsigned long long v = valid ? (1ull << sig_bit(__ldcs(rowidx + p))) : 0ull;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const unsigned long long ov = __shfl_down_sync(FULL_MASK, v, off);
-            const int32_t oj = __shfl_down_sync(FULL_MASK, j, off);
-            if (lane + off < 32 && oj == j)
-                v |= ov;
-        }
-        const int32_t jprev = __shfl_up_sync(FULL_MASK, j, 1);
-        if (valid && (lane == 0 || jprev != j))
-            atomicOr(colsig + j, v);
-    }
+    const bool starts_here = (mask >> lane) & 1u;
+    if (!starts_here)
+        return false;
+    const uint32_t later = lane == 31 ? 0u : (mask >> (lane + 1));
+    return later != 0u || base + kTile >= nnz || (__ldg(starts + t + 1) & 1u);
 }
 
-// rr[r] and wmr[r] for the row r matched to column j.
-__global__ void k_init_rows(int32_t n, const int32_t *__restrict__ colptr,
-                            const int32_t *__restrict__ mc, const double *__restrict__ wm,
-                            const unsigned long long *__restrict__ colsig, RowRec *rr, double *wmr,
-                            const Ctl *ctl)
-{
-    if (ctl->err)
-        return;
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n)
-        return;
-    const int32_t r = mc[j];
-    RowRec x;
-    x.s = colptr[j];
-    x.e = colptr[j + 1];
-    x.sig = colsig[j];
-    rr[r] = x;
-    wmr[r] = wm[j];
-}
-
-// ---------------------------------------------------------------------------
-// Per-column open-addressing tables (closing-edge lookup by hashing)
-// ---------------------------------------------------------------------------
+// ---- per-column open-addressing tables -------------------------------------
 // Column c owns the 2 * deg(c) slots [2 colptr[c], 2 colptr[c+1]) of htab;
 // a slot holds (position << 32 | row), all ones when empty.  Linear probing
 // from slot_start(); the table is at most half full, so every probe sequence
@@ -324,53 +174,14 @@ __device__ __forceinline__ int32_t slot_start(int32_t r, int32_t base, int32_t s
     return base + (int32_t)__umulhi(row_mix(r), (uint32_t)size);
 }
 
-__global__ void __launch_bounds__(256)
-k_hash_build(int32_t n, int32_t nnz, int32_t ntiles, const int32_t *__restrict__ colptr,
-             const int32_t *__restrict__ rowidx, const int32_t *__restrict__ tile_col,
-             unsigned long long *htab, Ctl *ctl)
-{
-    if (ctl->err)
-        return;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = warp0; t < ntiles; t += nwarps) {
-        const int32_t p = (int32_t)(t * kTile) + lane;
-        const bool valid = p < nnz;
-        const int32_t c0 = tile_col[t];
-        const int64_t ck = (int64_t)c0 + 1 + lane;
-        const int32_t e = (ck <= n) ? colptr[ck] : 0x7fffffff;
-        const int32_t cnt = lane_column_offset(e, p);
-        if (!valid)
-            continue;
-        const int32_t j = c0 + cnt;
-        const int32_t r = __ldcs(rowidx + p);
-        const int32_t base = 2 * colptr[j];
-        const int32_t size = 2 * (colptr[j + 1] - colptr[j]);
-        const unsigned long long v = ((unsigned long long)(uint32_t)p << 32) | (uint32_t)r;
-        int32_t pos = slot_start(r, base, size);
-        int k = 0;
-        for (; k < size; ++k) {
-            if (atomicCAS(htab + pos, kSlotEmpty, v) == kSlotEmpty)
-                break;
-            if (++pos == base + size)
-                pos = base;
-        }
-        if (k == size)
-            raise_err(ctl, kErrInternal);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Steps A + B + C (Algorithms 3, 4, 5): fused edge-parallel cycle search
-// ---------------------------------------------------------------------------
+// ---- lock-free arg-max records ----------------------------------------------
 
 __device__ __forceinline__ bool rec_better(double g, int32_t p, double cg, int32_t cp)
 {
     return g > cg || (g == cg && p < cp);
 }
 
-// Lock-free maximum of (g, lowest p) into a Step-C record.
+// Maximum of (g, lowest p) into a Step-C record.
 __device__ void rec_combine(Rec *addr, Rec mine, Ctl *ctl)
 {
     Rec cur = *addr;
@@ -385,6 +196,29 @@ __device__ void rec_combine(Rec *addr, Rec mine, Ctl *ctl)
     }
     raise_err(ctl, kErrInternal);
 }
+
+__device__ __forceinline__ bool sel_better(double g, int32_t j, double cg, int32_t cj)
+{
+    return g > cg || (g == cg && j < cj);
+}
+
+// Maximum of (g, lowest root j) into a Step-D selection.
+__device__ void sel_combine(Sel *addr, Sel mine, Ctl *ctl)
+{
+    Sel cur = *addr;
+    for (int it = 0; it < kCasRetryCap; ++it) {
+        if (!sel_better(mine.g, mine.j, cur.g, cur.j))
+            return;
+        Sel old = atomicCAS(addr, cur, mine);
+        if (__double_as_longlong(old.g) == __double_as_longlong(cur.g) && old.j == cur.j &&
+            old.pad == cur.pad)
+            return;
+        cur = old;
+    }
+    raise_err(ctl, kErrInternal);
+}
+
+// ---- cache-policy loads -------------------------------------------------------
 
 __device__ __forceinline__ unsigned long long policy_evict_last()
 {
@@ -439,8 +273,318 @@ __device__ __forceinline__ int32_t coop_find(const int32_t *__restrict__ rowidx,
     return eq ? s + __ffs(eq) - 1 : -1;
 }
 
-// Closing-edge ranges longer than this go to the warp-cooperative search.
-constexpr int32_t kCoopMin = 32;
+// ---------------------------------------------------------------------------
+// Initialisation and validation (before the loop of Algorithm 2)
+// ---------------------------------------------------------------------------
+
+// Clear everything a solve expects to start at zero (or empty).
+__global__ void k_reset(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (gtid() == 0) {
+        Ctl *c = w.ctl;
+        c->err = 0u;
+        c->active = 1;
+        c->iterations = 0;
+        c->converged = 0;
+        c->max_passes = w.max_passes;
+        c->pass_flips = 0ull;
+        c->cycles = 0ull;
+        c->candidates = 0ull;
+        c->found = 0ull;
+        c->positive = 0ull;
+        c->weight_in = 0.0;
+        c->weight_out = 0.0;
+        if (w.bw.count > 0)
+            *w.bw.active = 0;
+    }
+    for (int64_t j = gtid(); j < w.n; j += gstride()) {
+        w.mr[j] = -1;
+        w.best[j] = Rec{0.0, 0, 0};
+        w.dsel[j] = Sel{0.0, 0, 0};
+        w.colsig[j] = 0ull;
+    }
+    const int64_t words = ((int64_t)w.nnz + 31) / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride())
+        w.starts[x] = 0u;
+    if (w.lookup == AWPM_LOOKUP_HASH && w.htab)
+        for (int64_t x = gtid(); x < 2 * (int64_t)w.nnz; x += gstride())
+            w.htab[x] = kSlotEmpty;
+    for (int64_t b = gtid(); b < w.bw.count; b += gstride()) {
+        w.bw.mdone[b] = 0;
+        w.bw.miter[b] = 0;
+        w.bw.mconv[b] = 0;
+        w.bw.mflips[b] = 0ull;
+        w.bw.mcycles[b] = 0ull;
+    }
+}
+
+// colptr[0] = 0, non-decreasing, colptr[n] = nnz.
+__global__ void k_check_colptr(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    for (int64_t j = gtid(); j <= w.n; j += gstride()) {
+        const int32_t c = w.colptr[j];
+        const bool bad = (j == 0 && c != 0) || (j < w.n && w.colptr[j + 1] < c) ||
+                         (j == w.n && c != w.nnz);
+        if (bad)
+            raise_err(w.ctl, kErrInvalid);
+    }
+}
+
+// Column-start bitmap and the first column of every tile.
+__global__ void k_mark_starts(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    for (int64_t j = gtid(); j < w.n; j += gstride()) {
+        const int32_t s = w.colptr[j], e = w.colptr[j + 1];
+        if (s < e) {
+            atomicOr(&w.starts[s >> 5], 1u << (s & 31));
+            for (int64_t t = ((int64_t)s + kTile - 1) / kTile; t * kTile < e; ++t)
+                w.tile_col[t] = (int32_t)j;
+        }
+    }
+}
+
+// One pass over the entries: row range, sortedness inside columns, finite
+// weights, and the column signatures (OR of 1 << sig_bit(row) over each
+// column; lanes of one column are OR-ed in the warp, whole columns stored,
+// columns cut by a tile boundary merged with atomics).
+__global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err & kErrInvalid)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    const int32_t n = w.n, nnz = w.nnz;
+    unsigned bits = 0;
+    for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
+        const int32_t base = (int32_t)(t * kTile);
+        const int32_t p = base + lane;
+        const bool valid = p < nnz;
+        const int32_t c0 = w.tile_col[t];
+        const uint32_t mask = w.starts[t];
+        const int32_t r = valid ? __ldcs(w.rowidx + p) : 0;
+        if (valid) {
+            if (r < 0 || r >= n)
+                bits |= kErrInvalid;
+            if (!isfinite(__ldcs(w.w + p)))
+                bits |= kErrNonfinite;
+            if (p > 0 && !((mask >> lane) & 1u) && w.rowidx[p - 1] >= r)
+                bits |= kErrUnsorted;
+        }
+        const int32_t j = valid ? lane_column(c0, mask, lane) : -1 - lane;
+        unsigned long long v = (valid && r >= 0 && r < n) ? (1ull << sig_bit(r)) : 0ull;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long ov = __shfl_down_sync(FULL_MASK, v, off);
+            const int32_t oj = __shfl_down_sync(FULL_MASK, j, off);
+            if (lane + off < 32 && oj == j)
+                v |= ov;
+        }
+        const bool head = valid && (lane == 0 || ((mask >> lane) & 1u));
+        if (head && j < n) {
+            if (segment_complete(mask, lane, base, nnz, w.starts, t))
+                w.colsig[j] = v;
+            else if (v)
+                atomicOr(w.colsig + j, v);
+        }
+    }
+    bits = __reduce_or_sync(FULL_MASK, bits);
+    if (lane == 0 && bits)
+        raise_err(w.ctl, bits);
+}
+
+// mc = mate_in, mr = its inverse, wm[j] = w(mate_in[j], j), and the row
+// record and matched weight of every row; checks that mate_in is a
+// permutation over stored entries.
+__global__ void k_init_mates(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    for (int64_t j = gtid(); j < w.n; j += gstride()) {
+        const int32_t r = w.mate_in[j];
+        w.mc[j] = r;
+        if (r < 0 || r >= w.n) {
+            raise_err(w.ctl, kErrNotPerfect);
+            continue;
+        }
+        if (atomicCAS(&w.mr[r], -1, (int32_t)j) != -1)
+            raise_err(w.ctl, kErrNotPerfect);
+        const int32_t s = w.colptr[j], e = w.colptr[j + 1];
+        const int32_t q = find_row(w.rowidx, s, e, r);
+        if (q < 0) {
+            raise_err(w.ctl, kErrNotPerfect);
+            continue;
+        }
+        const double x = w.w[q];
+        w.wm[j] = x;
+        RowRec rec;
+        rec.s = s;
+        rec.e = e;
+        rec.sig = w.colsig[j];
+        w.rr[r] = rec;
+        w.wmr[r] = x;
+    }
+}
+
+// Per-column hash tables (only for AWPM_LOOKUP_HASH).
+__global__ void __launch_bounds__(kThreads) k_hash_build(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err || w.lookup != AWPM_LOOKUP_HASH || !w.htab)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
+        const int32_t p = (int32_t)(t * kTile) + lane;
+        if (p >= w.nnz)
+            continue;
+        const int32_t j = lane_column(w.tile_col[t], w.starts[t], lane);
+        const int32_t r = __ldcs(w.rowidx + p);
+        const int32_t base = 2 * w.colptr[j];
+        const int32_t size = 2 * (w.colptr[j + 1] - w.colptr[j]);
+        const unsigned long long v = ((unsigned long long)(uint32_t)p << 32) | (uint32_t)r;
+        int32_t pos = slot_start(r, base, size);
+        int k = 0;
+        for (; k < size; ++k) {
+            if (atomicCAS(w.htab + pos, kSlotEmpty, v) == kSlotEmpty)
+                break;
+            if (++pos == base + size)
+                pos = base;
+        }
+        if (k == size)
+            raise_err(w.ctl, kErrInternal);
+    }
+}
+
+__global__ void k_wsum_partial(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    double s = 0.0;
+    if (w.ctl->err == 0u)
+        for (int64_t j = gtid(); j < w.n; j += gstride())
+            s += w.wm[j];
+    s = block_sum_f64(s);
+    if (threadIdx.x == 0)
+        w.wpart[blockIdx.x] = s;
+}
+
+__global__ void k_wsum_final(const Work *__restrict__ W, int out)
+{
+    const Work &w = *W;
+    const double s = block_sum_f64(w.wpart[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        if (out)
+            w.ctl->weight_out = s;
+        else
+            w.ctl->weight_in = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched solves: many matrices as one block-diagonal union
+// ---------------------------------------------------------------------------
+// Cycles never cross blocks (no entry joins two blocks), so every pass of
+// the union is one pass of each matrix.  A matrix whose pass flips nothing
+// (or that reached the pass cap) is finished: its tiles are skipped from then
+// on and its counters stop, which gives each matrix exactly the passes,
+// flips and result of a solve on its own.
+
+// Offsets non-decreasing from 0 to n; matrix of every column.
+__global__ void k_batch_cols(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    const int32_t count = w.bw.count;
+    const int32_t *n_off = w.bw.n_off;
+    for (int64_t x = gtid(); x <= count; x += gstride()) {
+        const int32_t o = n_off[x];
+        if ((x == 0 && o != 0) || (x == count && o != w.n) || (x < count && n_off[x + 1] < o))
+            raise_err(w.ctl, kErrInvalid);
+    }
+    for (int64_t x = gtid(); x < w.n; x += gstride()) {
+        // number of matrices ending at or before column x = its matrix
+        int32_t lo = 0, len = count;
+        while (len > 0) {
+            const int32_t half = len >> 1;
+            if (__ldg(n_off + lo + half + 1) <= x) {
+                lo += half + 1;
+                len -= half + 1;
+            } else {
+                len = half;
+            }
+        }
+        w.bw.colmat[x] = lo < count ? lo : count - 1;
+    }
+}
+
+// Every stored row lies in its column's block; nonzeros per matrix; the
+// matrix of each tile and whether the tile stays inside one matrix.
+__global__ void __launch_bounds__(kThreads) k_batch_check(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    const BatchWork &bw = w.bw;
+    unsigned bad = 0;
+    for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
+        const int32_t p = (int32_t)(t * kTile) + lane;
+        const int32_t c0 = w.tile_col[t];
+        if (p < w.nnz) {
+            const int32_t b = bw.colmat[lane_column(c0, w.starts[t], lane)];
+            const int32_t r = w.rowidx[p];
+            if (r < bw.n_off[b] || r >= bw.n_off[b + 1])
+                bad = 1;
+        }
+        if (lane == 0) {
+            const int32_t b0 = bw.colmat[c0];
+            const int32_t b1 =
+                (t + 1 < w.ntiles) ? bw.colmat[w.tile_col[t + 1]] : bw.colmat[w.n - 1];
+            bw.tilemat[t] = b0 | (b0 == b1 ? kTileSingle : 0);
+        }
+    }
+    if (__any_sync(FULL_MASK, bad) && lane == 0)
+        raise_err(w.ctl, kErrInvalid);
+    for (int64_t b = gtid(); b < bw.count; b += gstride())
+        bw.mnnz[b] = w.colptr[bw.n_off[b + 1]] - w.colptr[bw.n_off[b]];
+}
+
+// One block per matrix (grid-stride over matrices): deterministic sum of its
+// matched weights.
+__global__ void k_batch_wsum(const Work *__restrict__ W, int out)
+{
+    const Work &w = *W;
+    const BatchWork &bw = w.bw;
+    for (int64_t b = blockIdx.x; b < bw.count; b += gridDim.x) {
+        double s = 0.0;
+        if (w.ctl->err == 0u)
+            for (int64_t j = bw.n_off[b] + threadIdx.x; j < bw.n_off[b + 1]; j += blockDim.x)
+                s += w.wm[j];
+        s = block_sum_f64(s);
+        if (threadIdx.x == 0)
+            (out ? bw.mw_out : bw.mw_in)[b] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Steps A + B + C (Algorithms 3, 4, 5): fused edge-parallel cycle search
+// ---------------------------------------------------------------------------
+
+// A new pass starts with no Step-C record.
+__global__ void k_reset_best(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (!gate(w.ctl))
+        return;
+    for (int64_t j = gtid(); j < w.n; j += gstride())
+        w.best[j] = Rec{0.0, 0, 0};
+}
 
 // One warp per tile of kTile consecutive nonzeros (lane = one nonzero).
 // The lane's column comes from the tile's first column and its word of the
@@ -455,34 +599,69 @@ constexpr int32_t kCoopMin = 32;
 // cut by a tile boundary are merged across warps by a 128-bit
 // compare-and-swap.  `best` must be zero on entry: only positive records are
 // written.  In a batched solve, tiles of finished matrices are skipped.
-template <int kLookup, bool kBatch>
-__global__ void __launch_bounds__(256)
-k_search(int32_t n, int32_t nnz, int32_t ntiles, const int32_t *__restrict__ rowidx,
-         const double *__restrict__ w, const int32_t *__restrict__ tile_col,
-         const uint32_t *__restrict__ starts, const int32_t *__restrict__ mc,
-         const double *__restrict__ wm, const RowRec *__restrict__ rr,
-         const double *__restrict__ wmr, const unsigned long long *__restrict__ htab,
-         Rec *__restrict__ best, Ctl *ctl, const int32_t *__restrict__ tilemat,
-         const int32_t *__restrict__ colmat, const int32_t *__restrict__ mdone)
+template <int kLookup, bool kBatch, bool kPipe>
+__global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__ W)
 {
     __shared__ int s_go;
     if (threadIdx.x == 0)
-        s_go = gate(ctl) ? 1 : 0;
+        s_go = gate(W->ctl) ? 1 : 0;
     __syncthreads();
+    const int32_t nnz = W->nnz;
+    const int32_t ntiles = W->ntiles;
+    const int32_t *__restrict__ rowidx = W->rowidx;
+    const double *__restrict__ wv = W->w;
+    const int32_t *__restrict__ tile_col = W->tile_col;
+    const uint32_t *__restrict__ starts = W->starts;
+    const int32_t *__restrict__ mc = W->mc;
+    const double *__restrict__ wm = W->wm;
+    const RowRec *__restrict__ rr = W->rr;
+    const double *__restrict__ wmr = W->wmr;
+    const unsigned long long *__restrict__ htab = W->htab;
+    Rec *__restrict__ best = W->best;
+    Ctl *ctl = W->ctl;
+    const int32_t *__restrict__ tilemat = W->bw.tilemat;
+    const int32_t *__restrict__ colmat = W->bw.colmat;
+    const int32_t *__restrict__ mdone = W->bw.mdone;
+
     const int lane = threadIdx.x & 31;
-    const uint32_t le_mask = (2u << lane) - 1u;  // lanes 0..lane
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nwarps = gstride() >> 5;
     const unsigned long long pol = policy_evict_last();
     unsigned long long n_cand = 0, n_found = 0, n_pos = 0;
 
-    for (int64_t t = s_go ? warp0 : (int64_t)ntiles; t < ntiles; t += nwarps) {
+    // kPipe: the next tile's first column, start bits and row indices are
+    // loaded while the current tile is processed, so the latency of the
+    // streamed row indices overlaps the current tile's gathers
+    int64_t t = s_go ? (gtid() >> 5) : (int64_t)ntiles;
+    int32_t pf_c0 = 0, pf_i = 0;
+    uint32_t pf_mask = 0u;
+    if (kPipe && t < ntiles) {
+        pf_c0 = __ldg(tile_col + t);
+        pf_mask = __ldg(starts + t);
+        const int32_t pp = (int32_t)(t * kTile) + lane;
+        pf_i = pp < nnz ? __ldcs(rowidx + pp) : 0;
+    }
+    for (; t < ntiles; t += nwarps) {
         const int32_t base = (int32_t)(t * kTile);
         const int32_t p = base + lane;
         bool valid = p < nnz;
         bool mixed = false;
-        const int32_t c0 = __ldg(tile_col + t);
-        const uint32_t mask = __ldg(starts + t);
+        int32_t c0, i_now = 0;
+        uint32_t mask;
+        if (kPipe) {
+            c0 = pf_c0;
+            mask = pf_mask;
+            i_now = pf_i;
+            const int64_t tn = t + nwarps;
+            if (tn < ntiles) {
+                pf_c0 = __ldg(tile_col + tn);
+                pf_mask = __ldg(starts + tn);
+                const int32_t pn = (int32_t)(tn * kTile) + lane;
+                pf_i = pn < nnz ? __ldcs(rowidx + pn) : 0;
+            }
+        } else {
+            c0 = __ldg(tile_col + t);
+            mask = __ldg(starts + t);
+        }
         if (kBatch) {
             // a tile of one finished matrix has nothing left to do
             const int32_t tm = __ldg(tilemat + t);
@@ -493,8 +672,8 @@ k_search(int32_t n, int32_t nnz, int32_t ntiles, const int32_t *__restrict__ row
                 mixed = true;
             }
         }
-        const int32_t i = valid ? __ldcs(rowidx + p) : 0;
-        const int32_t j = valid ? c0 + __popc(mask & le_mask & ~1u) : -1 - lane;
+        const int32_t i = valid ? (kPipe ? i_now : __ldcs(rowidx + p)) : 0;
+        const int32_t j = valid ? lane_column(c0, mask, lane) : -1 - lane;
         int32_t mj = valid ? ld_i32_last(mc + j, pol) : 0x7fffffff;
         if (kBatch && mixed && valid && __ldg(mdone + __ldg(colmat + j)))
             mj = 0x7fffffff;  // finished matrix: no candidate
@@ -561,8 +740,8 @@ k_search(int32_t n, int32_t nnz, int32_t ntiles, const int32_t *__restrict__ row
         double g = 0.0;
         if (q >= 0) {
             ++n_found;
-            const double wij = __ldcs(w + p);
-            const double wq = __ldg(w + q);
+            const double wij = __ldcs(wv + p);
+            const double wq = __ldg(wv + q);
             const double gg = ((wij + wq) - wmi) - __ldg(wm + j);
             if (gg > 0.0) {
                 ++n_pos;
@@ -589,18 +768,11 @@ k_search(int32_t n, int32_t nnz, int32_t ntiles, const int32_t *__restrict__ row
         }
         const bool head = valid && (lane == 0 || ((mask >> lane) & 1u));
         if (head && g > 0.0) {
-            // the segment covers its whole column when the column starts here
-            // and ends inside the tile (a later start bit, the end of the
-            // matrix, or a column starting the next tile)
-            const bool starts_here = (mask >> lane) & 1u;
-            const uint32_t later = lane == 31 ? 0u : (mask >> (lane + 1));
-            const bool ends_here = later != 0u || base + kTile >= nnz ||
-                                   (__ldg(starts + t + 1) & 1u);
             Rec r;
             r.g = g;
             r.p = bp;
             r.q = q;
-            if (starts_here && ends_here)
+            if (segment_complete(mask, lane, base, nnz, starts, t))
                 best[j] = r;
             else
                 rec_combine(best + j, r, ctl);
@@ -615,99 +787,73 @@ k_search(int32_t n, int32_t nnz, int32_t ntiles, const int32_t *__restrict__ row
 // Step D (Algorithm 6): conflicts, per-key selection, flip
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ bool sel_better(double g, int32_t j, double cg, int32_t cj)
-{
-    return g > cg || (g == cg && j < cj);
-}
-
-__device__ void sel_combine(Sel *addr, Sel mine, Ctl *ctl)
-{
-    Sel cur = *addr;
-    for (int it = 0; it < kCasRetryCap; ++it) {
-        if (!sel_better(mine.g, mine.j, cur.g, cur.j))
-            return;
-        Sel old = atomicCAS(addr, cur, mine);
-        if (__double_as_longlong(old.g) == __double_as_longlong(cur.g) && old.j == cur.j &&
-            old.pad == cur.pad)
-            return;
-        cur = old;
-    }
-    raise_err(ctl, kErrInternal);
-}
-
 // For every Step-C winner rooted at j with second matched edge at column
 // k = m_i: drop it if column k is itself the root of a Step-C winner,
 // otherwise compete for key k (maximum gain, then lowest root j).
-__global__ void k_select(int32_t n, const int32_t *__restrict__ rowidx,
-                         const int32_t *__restrict__ mr, const Rec *__restrict__ best, Sel *dsel,
-                         Ctl *ctl)
+__global__ void k_select(const Work *__restrict__ W)
 {
-    if (!gate(ctl))
+    const Work &w = *W;
+    if (!gate(w.ctl))
         return;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += stride) {
-        const Rec r = best[j];
+    for (int64_t j = gtid(); j < w.n; j += gstride()) {
+        const Rec r = w.best[j];
         if (!(r.g > 0.0))
             continue;
-        const int32_t i = __ldg(rowidx + r.p);
-        const int32_t k = __ldg(mr + i);
-        if (best[k].g > 0.0)
+        const int32_t i = __ldg(w.rowidx + r.p);
+        const int32_t k = w.mr[i];
+        if (w.best[k].g > 0.0)
             continue;
         Sel s;
         s.g = r.g;
         s.j = (int32_t)j;
         s.pad = 0;
-        sel_combine(dsel + k, s, ctl);
+        sel_combine(w.dsel + k, s, w.ctl);
     }
 }
 
 // Flip every selected cycle: column j takes row i, key column k takes m_j;
 // the row records of rows i and m_j follow their new mates.  The selected
 // cycles are vertex-disjoint, so each thread owns its four vertices.
-__global__ void k_flip(int32_t n, const int32_t *__restrict__ colptr,
-                       const int32_t *__restrict__ rowidx, const double *__restrict__ w,
-                       const unsigned long long *__restrict__ colsig, const Rec *__restrict__ best,
-                       Sel *dsel, int32_t *mc, int32_t *mr, double *wm, RowRec *rr, double *wmr,
-                       Ctl *ctl, const int32_t *__restrict__ colmat, unsigned long long *mflips)
+__global__ void k_flip(const Work *__restrict__ W)
 {
+    const Work &w = *W;
     unsigned long long flips = 0;
-    if (gate(ctl)) {
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) {
-            const Sel s = dsel[k];
+    if (gate(w.ctl)) {
+        for (int64_t k = gtid(); k < w.n; k += gstride()) {
+            const Sel s = w.dsel[k];
             if (!(s.g > 0.0))
                 continue;
-            dsel[k] = Sel{0.0, 0, 0};
+            w.dsel[k] = Sel{0.0, 0, 0};
             const int32_t j = s.j;
-            const Rec r = best[j];
-            const int32_t i = rowidx[r.p];
-            const int32_t mj = mc[j];
-            const double wij = w[r.p];
-            const double wq = w[r.q];
-            mc[j] = i;
-            mr[i] = j;
-            mc[k] = mj;
-            mr[mj] = (int32_t)k;
-            wm[j] = wij;
-            wm[k] = wq;
+            const Rec r = w.best[j];
+            const int32_t i = w.rowidx[r.p];
+            const int32_t mj = w.mc[j];
+            const double wij = w.w[r.p];
+            const double wq = w.w[r.q];
+            w.mc[j] = i;
+            w.mr[i] = j;
+            w.mc[k] = mj;
+            w.mr[mj] = (int32_t)k;
+            w.wm[j] = wij;
+            w.wm[k] = wq;
             RowRec a;
-            a.s = colptr[j];
-            a.e = colptr[j + 1];
-            a.sig = colsig[j];
-            rr[i] = a;
-            wmr[i] = wij;
+            a.s = w.colptr[j];
+            a.e = w.colptr[j + 1];
+            a.sig = w.colsig[j];
+            w.rr[i] = a;
+            w.wmr[i] = wij;
             RowRec b;
-            b.s = colptr[k];
-            b.e = colptr[k + 1];
-            b.sig = colsig[k];
-            rr[mj] = b;
-            wmr[mj] = wq;
+            b.s = w.colptr[k];
+            b.e = w.colptr[k + 1];
+            b.sig = w.colsig[k];
+            w.rr[mj] = b;
+            w.wmr[mj] = wq;
             ++flips;
-            if (mflips)
-                atomicAdd(mflips + colmat[k], 1ull);
+            if (w.bw.count > 0)
+                atomicAdd(w.bw.mflips + w.bw.colmat[k], 1ull);
         }
     }
-    block_add_u64(flips, &ctl->pass_flips);
+    block_add_u64(flips, &w.ctl->pass_flips);
 }
 
 // End of a pass (Algorithm 2): count it, stop when nothing was flipped or
@@ -733,127 +879,45 @@ __device__ __forceinline__ int control_step(Ctl *ctl)
     return ctl->active;
 }
 
-__global__ void k_control(Ctl *ctl)
+__global__ void k_control(const Work *__restrict__ W)
 {
-    control_step(ctl);
+    control_step(W->ctl);
 }
 
-__global__ void k_control_graph(Ctl *ctl, cudaGraphConditionalHandle h)
+__global__ void k_control_graph(const Work *__restrict__ W, cudaGraphConditionalHandle h)
 {
-    cudaGraphSetConditional(h, control_step(ctl) ? 1u : 0u);
-}
-
-__global__ void k_export_stepc(int32_t n, const int32_t *__restrict__ rowidx,
-                               const Rec *__restrict__ best, double *gain, int32_t *row,
-                               const Ctl *ctl)
-{
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n || ctl->err)
-        return;
-    const Rec r = best[j];
-    const bool has = r.g > 0.0;
-    gain[j] = has ? r.g : 0.0;
-    row[j] = has ? rowidx[r.p] : -1;
-}
-
-// ---------------------------------------------------------------------------
-// Batched solves: many matrices as one block-diagonal union
-// ---------------------------------------------------------------------------
-// Cycles never cross blocks (no entry joins two blocks), so every pass of
-// the union is one pass of each matrix.  A matrix whose pass flips nothing
-// (or that reached the pass cap) is finished: its tiles are skipped from then
-// on and its counters stop, which gives each matrix exactly the passes,
-// flips and result of a solve on its own.
-
-// Offsets non-decreasing from 0 to n; matrix of every column.
-__global__ void k_batch_cols(int32_t n, int32_t count, const int32_t *__restrict__ n_off,
-                             int32_t *colmat, Ctl *ctl)
-{
-    const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (x <= count) {
-        const int32_t o = n_off[x];
-        if ((x == 0 && o != 0) || (x == count && o != n) || (x < count && n_off[x + 1] < o))
-            raise_err(ctl, kErrInvalid);
-    }
-    if (x >= n)
-        return;
-    // last b with n_off[b] <= x (empty matrices are skipped over)
-    int32_t lo = 0, len = count;
-    while (len > 0) {
-        const int32_t half = len >> 1;
-        if (__ldg(n_off + lo + half + 1) <= x) {
-            lo += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    colmat[x] = lo < count ? lo : count - 1;
-}
-
-// Every stored row lies in its column's block; nonzeros per matrix; the
-// matrix of each tile and whether the tile stays inside one matrix.
-__global__ void __launch_bounds__(256)
-k_batch_check(int32_t n, int32_t nnz, int32_t ntiles, int32_t count, const int32_t *__restrict__ colptr,
-              const int32_t *__restrict__ rowidx, const int32_t *__restrict__ tile_col,
-              const int32_t *__restrict__ n_off, const int32_t *__restrict__ colmat,
-              int32_t *tilemat, int32_t *mnnz, Ctl *ctl)
-{
-    if (ctl->err)
-        return;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned bad = 0;
-    for (int64_t t = warp0; t < ntiles; t += nwarps) {
-        const int32_t p = (int32_t)(t * kTile) + lane;
-        const bool valid = p < nnz;
-        const int32_t c0 = tile_col[t];
-        const int64_t ck = (int64_t)c0 + 1 + lane;
-        const int32_t e = (ck <= n) ? colptr[ck] : 0x7fffffff;
-        const int32_t cnt = lane_column_offset(e, p);
-        if (valid) {
-            const int32_t b = colmat[c0 + cnt];
-            const int32_t r = rowidx[p];
-            if (r < n_off[b] || r >= n_off[b + 1])
-                bad = 1;
-        }
-        if (lane == 0) {
-            const int32_t b0 = colmat[c0];
-            const int32_t b1 = (t + 1 < ntiles) ? colmat[tile_col[t + 1]] : colmat[n - 1];
-            tilemat[t] = b0 | (b0 == b1 ? kTileSingle : 0);
-        }
-    }
-    if (__any_sync(FULL_MASK, bad) && lane == 0)
-        raise_err(ctl, kErrInvalid);
-    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b < count)
-        mnnz[b] = colptr[n_off[b + 1]] - colptr[n_off[b]];
+    cudaGraphSetConditional(h, control_step(W->ctl) ? 1u : 0u);
 }
 
 // End of a pass for every matrix still running: count the pass, stop the
 // matrix when it flipped nothing or reached the cap; count the running ones.
-__global__ void k_batch_control(int32_t count, BatchWork bw, Ctl *ctl)
+__global__ void k_batch_control(const Work *__restrict__ W)
 {
-    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int still = 0;
-    if (b < count && !ctl->err && !bw.mdone[b]) {
-        const unsigned long long f = bw.mflips[b];
-        bw.mflips[b] = 0;
-        bw.miter[b] += 1;
-        bw.mcycles[b] += f;
-        if (f == 0) {
-            bw.mconv[b] = 1;
-            bw.mdone[b] = 1;
-        } else if (bw.miter[b] >= ctl->max_passes) {
-            bw.mdone[b] = 1;
-        } else {
-            still = 1;
+    const Work &w = *W;
+    const BatchWork &bw = w.bw;
+    const bool go = !w.ctl->err && w.ctl->active;
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < bw.count;
+         b0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = b0 + threadIdx.x;
+        int still = 0;
+        if (go && b < bw.count && !bw.mdone[b]) {
+            const unsigned long long f = bw.mflips[b];
+            bw.mflips[b] = 0;
+            bw.miter[b] += 1;
+            bw.mcycles[b] += f;
+            if (f == 0) {
+                bw.mconv[b] = 1;
+                bw.mdone[b] = 1;
+            } else if (bw.miter[b] >= w.ctl->max_passes) {
+                bw.mdone[b] = 1;
+            } else {
+                still = 1;
+            }
         }
+        still = __syncthreads_count(still);
+        if (threadIdx.x == 0 && still)
+            atomicAdd(bw.active, still);
     }
-    still = __syncthreads_count(still);
-    if (threadIdx.x == 0 && still)
-        atomicAdd(bw.active, still);
 }
 
 // Pass counter of the whole batch; another pass runs while any matrix runs.
@@ -875,203 +939,182 @@ __device__ __forceinline__ int batch_step(Ctl *ctl, int32_t *active)
     return ctl->active;
 }
 
-__global__ void k_batch_step(Ctl *ctl, int32_t *active)
+__global__ void k_batch_step(const Work *__restrict__ W)
 {
-    batch_step(ctl, active);
+    batch_step(W->ctl, W->bw.active);
 }
 
-__global__ void k_batch_step_graph(Ctl *ctl, int32_t *active, cudaGraphConditionalHandle h)
+__global__ void k_batch_step_graph(const Work *__restrict__ W, cudaGraphConditionalHandle h)
 {
-    cudaGraphSetConditional(h, batch_step(ctl, active) ? 1u : 0u);
+    cudaGraphSetConditional(h, batch_step(W->ctl, W->bw.active) ? 1u : 0u);
 }
 
-// One block per matrix: deterministic sum of its matched weights.
-__global__ void k_batch_wsum(int32_t count, const int32_t *__restrict__ n_off,
-                             const double *__restrict__ wm, double *out, const Ctl *ctl)
+__global__ void k_export_stepc(const Work *__restrict__ W, double *gain, int32_t *row)
 {
-    const int32_t b = blockIdx.x;
-    double s = 0.0;
-    if (ctl->err == 0u)
-        for (int64_t j = n_off[b] + threadIdx.x; j < n_off[b + 1]; j += blockDim.x)
-            s += wm[j];
-    s = block_sum_f64(s);
-    if (threadIdx.x == 0)
-        out[b] = s;
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    for (int64_t j = gtid(); j < w.n; j += gstride()) {
+        const Rec r = w.best[j];
+        const bool has = r.g > 0.0;
+        gain[j] = has ? r.g : 0.0;
+        row[j] = has ? w.rowidx[r.p] : -1;
+    }
 }
 
 // ---------------------------------------------------------------------------
-// launchers
+// launchers: fixed grids (a multiple of the SM count)
 // ---------------------------------------------------------------------------
 
-static inline unsigned blocks_for(int64_t items, int threads)
+static inline unsigned util_grid(const Shape &sh)
 {
-    int64_t b = (items + threads - 1) / threads;
-    return (unsigned)(b < 1 ? 1 : b);
+    return (unsigned)(sh.num_sms * 4);
 }
 
-constexpr int kSearchThreads = 256;
-
-int default_search_u()
+static inline unsigned tile_grid(const Shape &sh)
 {
-    const char *v = getenv("AWPM_SEARCH_U");
-    if (v && (v[0] == '1' || v[0] == '2' || v[0] == '4') && v[1] == 0)
-        return v[0] - '0';
-    return 1;
+    return (unsigned)(sh.num_sms * 8);
 }
 
-// Resident blocks per SM of the search kernel.
-template <bool kBatch>
-static int search_bps(int lookup)
+void Sink::launch(const void *func, unsigned grid, unsigned block, void **args)
+{
+    if (err != cudaSuccess)
+        return;
+    if (graph) {
+        cudaKernelNodeParams p;
+        p.func = const_cast<void *>(func);
+        p.gridDim = dim3(grid);
+        p.blockDim = dim3(block);
+        p.sharedMemBytes = 0;
+        p.kernelParams = args;
+        p.extra = nullptr;
+        cudaGraphNode_t node;
+        err = cudaGraphAddKernelNode(&node, graph, last ? &last : nullptr, last ? 1 : 0, &p);
+        if (err == cudaSuccess)
+            last = node;
+    } else {
+        err = cudaLaunchKernel(func, dim3(grid), dim3(block), args, 0, stream);
+    }
+}
+
+void launch_init(const Work *d, const Shape &sh, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_reset, util_grid(sh), kThreads, a);
+    k.launch((const void *)k_check_colptr, util_grid(sh), kThreads, a);
+    k.launch((const void *)k_mark_starts, util_grid(sh), kThreads, a);
+    k.launch((const void *)k_entries, tile_grid(sh), kThreads, a);
+    if (sh.batch)
+        k.launch((const void *)k_batch_cols, util_grid(sh), kThreads, a);
+    k.launch((const void *)k_init_mates, util_grid(sh), kThreads, a);
+    if (sh.batch)
+        k.launch((const void *)k_batch_check, tile_grid(sh), kThreads, a);
+    if (sh.lookup == AWPM_LOOKUP_HASH)
+        k.launch((const void *)k_hash_build, tile_grid(sh), kThreads, a);
+}
+
+void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k)
+{
+    int o = out ? 1 : 0;
+    void *a[] = {(void *)&d};
+    void *ao[] = {(void *)&d, (void *)&o};
+    k.launch((const void *)k_wsum_partial, kWsumBlocks, kWsumThreads, a);
+    k.launch((const void *)k_wsum_final, 1, kWsumBlocks, ao);
+    if (sh.batch)
+        k.launch((const void *)k_batch_wsum, util_grid(sh), kThreads, ao);
+}
+
+void launch_reset_best(const Work *d, const Shape &sh, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_reset_best, util_grid(sh), kThreads, a);
+}
+
+template <int kLookup, bool kBatch, bool kPipe>
+static int bps_of()
 {
     int b = 0;
-    cudaError_t e;
-    const int T = kSearchThreads;
-    if (lookup == AWPM_LOOKUP_HASH)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<AWPM_LOOKUP_HASH, kBatch>,
-                                                          T, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &b, k_search<AWPM_LOOKUP_BSEARCH, kBatch>, T, 0);
-    if (e != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<kLookup, kBatch, kPipe>,
+                                                      kThreads, 0) != cudaSuccess) {
         cudaGetLastError();
         b = 1;
     }
     return b < 1 ? 1 : b;
 }
 
-int search_blocks_per_sm(int lookup, int u, bool batch)
+template <bool kPipe>
+static const void *search_fn(int lookup, bool batch)
 {
-    (void)u;
-    return batch ? search_bps<true>(lookup) : search_bps<false>(lookup);
+    if (lookup == AWPM_LOOKUP_HASH)
+        return batch ? (const void *)k_search<AWPM_LOOKUP_HASH, true, kPipe>
+                     : (const void *)k_search<AWPM_LOOKUP_HASH, false, kPipe>;
+    return batch ? (const void *)k_search<AWPM_LOOKUP_BSEARCH, true, kPipe>
+                 : (const void *)k_search<AWPM_LOOKUP_BSEARCH, false, kPipe>;
 }
 
-void launch_init(const Work &wk, int max_passes, int num_sms, cudaStream_t s)
+int search_blocks_per_sm(int lookup, bool batch, bool pipe)
 {
-    const int T = 256;
-    cudaMemsetAsync(wk.ctl, 0, sizeof(Ctl), s);
-    cudaMemsetAsync(wk.mr, 0xff, sizeof(int32_t) * (size_t)wk.n, s);
-    cudaMemsetAsync(wk.starts, 0, sizeof(uint32_t) * (((size_t)wk.nnz + 31) / 32 + 1), s);
-    cudaMemsetAsync(wk.best, 0, sizeof(Rec) * (size_t)wk.n, s);
-    cudaMemsetAsync(wk.dsel, 0, sizeof(Sel) * (size_t)wk.n, s);
-    cudaMemsetAsync(wk.colsig, 0, sizeof(unsigned long long) * (size_t)wk.n, s);
-    k_init_ctl<<<1, 1, 0, s>>>(wk.ctl, max_passes);
-    k_check_colptr<<<blocks_for((int64_t)wk.n + 1, T), T, 0, s>>>(wk.n, wk.nnz, wk.colptr, wk.ctl);
-    k_mark_starts<<<blocks_for(wk.n, T), T, 0, s>>>(wk.n, wk.colptr, wk.starts, wk.tile_col, wk.ctl);
-    int64_t want = ((int64_t)wk.nnz + T - 1) / T;
-    int64_t cap = (int64_t)num_sms * 16;
-    k_check_entries<<<(unsigned)(want < 1 ? 1 : (want < cap ? want : cap)), T, 0, s>>>(
-        wk.n, wk.nnz, wk.rowidx, wk.w, wk.starts, wk.ctl);
-    const BatchWork &bw = wk.bw;
-    if (bw.count > 0) {
-        cudaMemsetAsync(bw.mdone, 0, sizeof(int32_t) * (size_t)bw.count, s);
-        cudaMemsetAsync(bw.miter, 0, sizeof(int32_t) * (size_t)bw.count, s);
-        cudaMemsetAsync(bw.mconv, 0, sizeof(int32_t) * (size_t)bw.count, s);
-        cudaMemsetAsync(bw.mflips, 0, sizeof(unsigned long long) * (size_t)bw.count, s);
-        cudaMemsetAsync(bw.mcycles, 0, sizeof(unsigned long long) * (size_t)bw.count, s);
-        cudaMemsetAsync(bw.active, 0, sizeof(int32_t), s);
-        int64_t items = (int64_t)wk.n > (int64_t)bw.count + 1 ? (int64_t)wk.n : (int64_t)bw.count + 1;
-        k_batch_cols<<<blocks_for(items, T), T, 0, s>>>(wk.n, bw.count, bw.n_off, bw.colmat, wk.ctl);
+    if (pipe) {
+        if (lookup == AWPM_LOOKUP_HASH)
+            return batch ? bps_of<AWPM_LOOKUP_HASH, true, true>()
+                         : bps_of<AWPM_LOOKUP_HASH, false, true>();
+        return batch ? bps_of<AWPM_LOOKUP_BSEARCH, true, true>()
+                     : bps_of<AWPM_LOOKUP_BSEARCH, false, true>();
     }
-    k_init_mates<<<blocks_for(wk.n, T), T, 0, s>>>(wk.n, wk.colptr, wk.rowidx, wk.w, wk.mate_in,
-                                                    wk.mc, wk.mr, wk.wm, wk.ctl);
-    int64_t twant = ((int64_t)wk.ntiles + (T / 32) - 1) / (T / 32);
-    k_colsig<<<(unsigned)(twant < 1 ? 1 : (twant < cap ? twant : cap)), T, 0, s>>>(
-        wk.n, wk.nnz, wk.ntiles, wk.colptr, wk.rowidx, wk.tile_col, wk.colsig, wk.ctl);
-    if (bw.count > 0) {
-        int64_t g = twant > blocks_for(bw.count, T) ? twant : blocks_for(bw.count, T);
-        k_batch_check<<<(unsigned)(g < 1 ? 1 : g), T, 0, s>>>(wk.n, wk.nnz, wk.ntiles, bw.count,
-                                                           wk.colptr, wk.rowidx, wk.tile_col,
-                                                           bw.n_off, bw.colmat, bw.tilemat,
-                                                           bw.mnnz, wk.ctl);
-    }
-    k_init_rows<<<blocks_for(wk.n, T), T, 0, s>>>(wk.n, wk.colptr, wk.mc, wk.wm, wk.colsig, wk.rr,
-                                                   wk.wmr, wk.ctl);
-    if (wk.lookup == AWPM_LOOKUP_HASH && wk.htab) {
-        cudaMemsetAsync(wk.htab, 0xff, sizeof(unsigned long long) * 2 * (size_t)wk.nnz, s);
-        k_hash_build<<<(unsigned)(twant < 1 ? 1 : (twant < cap ? twant : cap)), T, 0, s>>>(
-            wk.n, wk.nnz, wk.ntiles, wk.colptr, wk.rowidx, wk.tile_col, wk.htab, wk.ctl);
-    }
+    if (lookup == AWPM_LOOKUP_HASH)
+        return batch ? bps_of<AWPM_LOOKUP_HASH, true, false>()
+                     : bps_of<AWPM_LOOKUP_HASH, false, false>();
+    return batch ? bps_of<AWPM_LOOKUP_BSEARCH, true, false>()
+                 : bps_of<AWPM_LOOKUP_BSEARCH, false, false>();
 }
 
-void launch_weight_sum(const Work &wk, bool out, cudaStream_t s)
+bool default_search_pipe()
 {
-    k_wsum_partial<<<kWsumBlocks, kWsumThreads, 0, s>>>(wk.n, wk.wm, wk.wpart, wk.ctl);
-    k_wsum_final<<<1, kWsumBlocks, 0, s>>>(wk.wpart, wk.ctl, out ? 1 : 0);
+    const char *v = getenv("AWPM_SEARCH_PIPE");
+    if (v && (v[0] == '0' || v[0] == '1') && v[1] == 0)
+        return v[0] == '1';
+    return true;
 }
 
-void launch_reset_best(const Work &wk, cudaStream_t s)
+void launch_search(const Work *d, const Shape &sh, Sink &k)
 {
-    cudaMemsetAsync(wk.best, 0, sizeof(Rec) * (size_t)wk.n, s);
+    const unsigned grid = (unsigned)(sh.num_sms * (sh.search_bps > 0 ? sh.search_bps : 1));
+    void *a[] = {(void *)&d};
+    const void *f = sh.pipe ? search_fn<true>(sh.lookup, sh.batch)
+                            : search_fn<false>(sh.lookup, sh.batch);
+    k.launch(f, grid, kThreads, a);
 }
 
-template <int kLookup, bool kBatch>
-static void launch_search_k(const Work &wk, int num_sms, cudaStream_t s)
+void launch_select_and_flip(const Work *d, const Shape &sh, Sink &k)
 {
-    const int T = kSearchThreads;
-    const int64_t per_block = T / 32;
-    int64_t want = ((int64_t)wk.ntiles + per_block - 1) / per_block;
-    int64_t cap = (int64_t)num_sms * (wk.search_bps > 0 ? wk.search_bps : 1);
-    unsigned grid = (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
-    k_search<kLookup, kBatch><<<grid, T, 0, s>>>(
-        wk.n, wk.nnz, wk.ntiles, wk.rowidx, wk.w, wk.tile_col, wk.starts, wk.mc, wk.wm, wk.rr,
-        wk.wmr, wk.htab, wk.best, wk.ctl, wk.bw.tilemat, wk.bw.colmat, wk.bw.mdone);
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_select, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_flip, tile_grid(sh), kThreads, a);
 }
 
-template <bool kBatch>
-static void launch_search_b(const Work &wk, int num_sms, cudaStream_t s)
+void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,
+                    Sink &k)
 {
-    if (wk.lookup == AWPM_LOOKUP_HASH)
-        launch_search_k<AWPM_LOOKUP_HASH, kBatch>(wk, num_sms, s);
-    else
-        launch_search_k<AWPM_LOOKUP_BSEARCH, kBatch>(wk, num_sms, s);
-}
-
-void launch_search(const Work &wk, int num_sms, cudaStream_t s)
-{
-    if (wk.bw.count > 0)
-        launch_search_b<true>(wk, num_sms, s);
-    else
-        launch_search_b<false>(wk, num_sms, s);
-}
-
-void launch_select_and_flip(const Work &wk, int num_sms, cudaStream_t s)
-{
-    const int T = 256;
-    int64_t want = ((int64_t)wk.n + T - 1) / T;
-    int64_t cap = (int64_t)num_sms * 8;
-    unsigned grid = (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
-    k_select<<<grid, T, 0, s>>>(wk.n, wk.rowidx, wk.mr, wk.best, wk.dsel, wk.ctl);
-    k_flip<<<grid, T, 0, s>>>(wk.n, wk.colptr, wk.rowidx, wk.w, wk.colsig, wk.best, wk.dsel,
-                              wk.mc, wk.mr, wk.wm, wk.rr, wk.wmr, wk.ctl, wk.bw.colmat,
-                              wk.bw.count > 0 ? wk.bw.mflips : nullptr);
-}
-
-void launch_control(const Work &wk, bool graph, cudaGraphConditionalHandle h, cudaStream_t s)
-{
-    if (wk.bw.count > 0) {
-        k_batch_control<<<blocks_for(wk.bw.count, 256), 256, 0, s>>>(wk.bw.count, wk.bw, wk.ctl);
+    void *a[] = {(void *)&d};
+    void *ah[] = {(void *)&d, (void *)&h};
+    if (sh.batch) {
+        k.launch((const void *)k_batch_control, util_grid(sh), kThreads, a);
         if (graph)
-            k_batch_step_graph<<<1, 1, 0, s>>>(wk.ctl, wk.bw.active, h);
+            k.launch((const void *)k_batch_step_graph, 1, 1, ah);
         else
-            k_batch_step<<<1, 1, 0, s>>>(wk.ctl, wk.bw.active);
+            k.launch((const void *)k_batch_step, 1, 1, a);
         return;
     }
     if (graph)
-        k_control_graph<<<1, 1, 0, s>>>(wk.ctl, h);
+        k.launch((const void *)k_control_graph, 1, 1, ah);
     else
-        k_control<<<1, 1, 0, s>>>(wk.ctl);
+        k.launch((const void *)k_control, 1, 1, a);
 }
 
-void launch_batch_weight_sum(const Work &wk, bool out, cudaStream_t s)
+void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k)
 {
-    if (wk.bw.count > 0)
-        k_batch_wsum<<<wk.bw.count, 256, 0, s>>>(wk.bw.count, wk.bw.n_off, wk.wm,
-                                                 out ? wk.bw.mw_out : wk.bw.mw_in, wk.ctl);
-}
-
-void launch_export_stepc(const Work &wk, double *gain, int32_t *row, cudaStream_t s)
-{
-    k_export_stepc<<<blocks_for(wk.n, 256), 256, 0, s>>>(wk.n, wk.rowidx, wk.best, gain, row, wk.ctl);
+    void *a[] = {(void *)&d, (void *)&gain, (void *)&row};
+    k.launch((const void *)k_export_stepc, util_grid(sh), kThreads, a);
 }
 
 }  // namespace awpm

@@ -33,7 +33,8 @@ constexpr size_t up(size_t x)
 
 // Layout of the scratch array (byte offsets, each 256-byte aligned).
 constexpr size_t kTilesMax = ((size_t)kMaxNnz + kTile - 1) / kTile + 1;
-constexpr size_t kOffCtl = 0;
+constexpr size_t kOffWork = 0;
+constexpr size_t kOffCtl = kOffWork + up(sizeof(Work));
 constexpr size_t kOffMc = kOffCtl + up(sizeof(Ctl));
 constexpr size_t kOffMr = kOffMc + up(sizeof(int32_t) * kMaxN);
 constexpr size_t kOffWm = kOffMr + up(sizeof(int32_t) * kMaxN);
@@ -137,13 +138,13 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     }
 
     Work wk;
+    std::memset(&wk, 0, sizeof(wk));
     wk.n = n;
     wk.nnz = nnz;
     wk.ntiles = (int32_t)(((int64_t)nnz + kTile - 1) / kTile);
+    wk.max_passes = 1;
     wk.lookup = AWPM_LOOKUP_BSEARCH;
     wk.htab = nullptr;
-    wk.search_u = default_search_u();
-    wk.search_bps = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, wk.search_u, false);
     wk.colptr = colptr;
     wk.rowidx = rowidx;
     wk.w = weight;
@@ -166,11 +167,27 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     // launch_init clears everything that must start at zero (control block,
     // row mates, column-start bits, column signatures, Step-C and Step-D
     // records) before use.
-    launch_init(wk, 1, num_sms, s);
-    launch_search(wk, num_sms, s);
-    launch_export_stepc(wk, stepc_gain, stepc_row, s);
-    if (cudaGetLastError() != cudaSuccess)
+    // the descriptor lives in the scratch array too; the kernels read it there
+    Work *d = (Work *)(base + kOffWork);
+    if (cudaMemcpyAsync(d, &wk, sizeof(Work), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
         return AWPM_ERR_CUDA;
+    }
+    Shape sh;
+    sh.num_sms = num_sms;
+    sh.pipe = default_search_pipe();
+    sh.search_bps = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, false, sh.pipe);
+    sh.lookup = AWPM_LOOKUP_BSEARCH;
+    sh.batch = false;
+    Sink k;
+    k.stream = s;
+    launch_init(d, sh, k);
+    launch_search(d, sh, k);
+    launch_export_stepc(d, sh, stepc_gain, stepc_row, k);
+    if (k.err != cudaSuccess) {
+        cudaGetLastError();
+        return AWPM_ERR_CUDA;
+    }
     Ctl h;
     if (cudaMemcpyAsync(&h, wk.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

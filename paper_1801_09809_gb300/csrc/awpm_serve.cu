@@ -1,0 +1,364 @@
+// Request server of a context: awpm_submit / awpm_poll / awpm_wait.
+//
+// Continuous batching of independent matching requests.  A scheduler thread
+// owns `slots` solve slots; each slot is an internal context with its own
+// stream, workspace and instantiated solve graph.  Requests queue in arrival
+// order; whenever a slot is free and the device bytes held by all slots plus
+// what the request needs stay within the context's budget, the head of the
+// queue (or, when the head does not fit, one of the next few requests that
+// does) is admitted: its inputs are staged, its descriptor written and its
+// graph launched on the slot's stream without waiting.  Requests therefore
+// run concurrently on the device, and a new one starts as soon as an earlier
+// one frees its slot; completion is detected by polling each slot's event.
+// Each request is solved exactly as by awpm_improve on its own, so its
+// result does not depend on what else is running.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "awpm.h"
+#include "awpm_ctx.h"
+
+using namespace awpm;
+
+namespace {
+
+constexpr int kDefaultSlots = 4;
+constexpr int kAdmitLookahead = 8;
+
+struct Item {
+    uint64_t ticket = 0;
+    awpm_problem p{};
+    int state = 0;  // 0 queued, 1 running, 2 done
+    int rc = AWPM_OK;
+    awpm_stats st{};
+    size_t need = 0;
+};
+
+}  // namespace
+
+struct awpm_server_impl {
+    awpm_ctx *owner = nullptr;
+    std::vector<awpm_ctx *> slots;
+    std::vector<cudaStream_t> streams;  // non-blocking, one per slot
+    std::vector<Item *> running;  // per slot
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Item *> queue;
+    std::unordered_map<uint64_t, Item *> items;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    size_t budget = 0;
+    std::thread th;
+};
+
+namespace {
+
+bool host_side(const void *p)
+{
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+}
+
+size_t held_total(const awpm_server_impl *s)
+{
+    size_t h = 0;
+    for (const awpm_ctx *c : s->slots)
+        h += ctx_bytes_held(c);
+    return h;
+}
+
+void finish_item(awpm_server_impl *s, Item *it, int rc)
+{
+    it->rc = rc;
+    it->state = 2;
+    s->cv_done.notify_all();
+}
+
+// Start `it` on free slot k (server lock held by the caller; released around
+// the CUDA calls).
+void start(awpm_server_impl *s, std::unique_lock<std::mutex> &lk, int k, Item *it)
+{
+    it->state = 1;
+    s->running[k] = it;
+    awpm_ctx *c = s->slots[k];
+    lk.unlock();
+    Request r;
+    r.n = it->p.n;
+    r.nnz = it->p.nnz;
+    r.colptr = it->p.colptr;
+    r.rowidx = it->p.rowidx;
+    r.weight = it->p.weight;
+    r.mate_in = it->p.mate_in;
+    r.mate_out = it->p.mate_out;
+    int rc;
+    {
+        std::lock_guard<std::mutex> cl(c->mu);
+        rc = ctx_enqueue(c, r);
+        if (rc != AWPM_OK) {
+            cudaStreamSynchronize(c->stream);
+            cudaGetLastError();
+            c->pend.active = false;
+        }
+    }
+    lk.lock();
+    if (rc != AWPM_OK) {
+        s->running[k] = nullptr;
+        finish_item(s, it, rc);
+    }
+}
+
+void scheduler(awpm_server_impl *s)
+{
+    cudaSetDevice(s->owner->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        bool progress = false;
+        // reap finished slots
+        for (size_t k = 0; k < s->slots.size(); ++k) {
+            Item *it = s->running[k];
+            if (!it)
+                continue;
+            awpm_ctx *c = s->slots[k];
+            const cudaError_t q = cudaEventQuery(c->ev_b);
+            if (q == cudaErrorNotReady)
+                continue;
+            if (q != cudaSuccess)
+                cudaGetLastError();
+            int rc;
+            {
+                std::lock_guard<std::mutex> cl(c->mu);
+                rc = ctx_finish(c, &it->st, nullptr);
+            }
+            s->running[k] = nullptr;
+            finish_item(s, it, rc);
+            progress = true;
+        }
+        // admit queued requests onto free slots within the budget
+        for (size_t k = 0; k < s->slots.size() && !s->queue.empty(); ++k) {
+            if (s->running[k])
+                continue;
+            const size_t held = held_total(s);
+            const size_t mine = ctx_bytes_held(s->slots[k]);
+            int pick = -1;
+            const int look = (int)s->queue.size() < kAdmitLookahead ? (int)s->queue.size()
+                                                                     : kAdmitLookahead;
+            for (int x = 0; x < look; ++x) {
+                Item *it = s->queue[x];
+                const size_t grow = it->need > mine ? it->need - mine : 0;
+                if (!s->budget || held + grow <= s->budget) {
+                    pick = x;
+                    break;
+                }
+                if (s->budget && it->need > s->budget) {
+                    // can never fit: fail it instead of blocking the queue
+                    s->queue.erase(s->queue.begin() + x);
+                    finish_item(s, it, AWPM_ERR_BUDGET);
+                    progress = true;
+                    break;
+                }
+            }
+            if (pick < 0)
+                continue;
+            Item *it = s->queue[pick];
+            s->queue.erase(s->queue.begin() + pick);
+            start(s, lk, (int)k, it);
+            progress = true;
+        }
+        bool busy = false;
+        for (Item *it : s->running)
+            busy |= it != nullptr;
+        if (s->stop && !busy)
+            break;
+        if (!busy && s->queue.empty()) {
+            s->cv_work.wait(lk);
+        } else if (!progress) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        }
+    }
+}
+
+awpm_server_impl *server_of(awpm_ctx *ctx, int *rc)
+{
+    *rc = AWPM_OK;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->server)
+        return ctx->server;
+    awpm_server_impl *s = new (std::nothrow) awpm_server_impl();
+    if (!s) {
+        *rc = AWPM_ERR_OOM;
+        return nullptr;
+    }
+    s->owner = ctx;
+    s->budget = ctx->opt.mem_budget_bytes;
+    const int nslots = ctx->opt.slots > 0 ? ctx->opt.slots : kDefaultSlots;
+    cudaSetDevice(ctx->device);
+    for (int k = 0; k < nslots; ++k) {
+        // slot streams do not synchronise with the legacy default stream:
+        // requests run beside whatever the caller's threads do
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (awpm_ctx *x : s->slots)
+                awpm_destroy(x);
+            for (cudaStream_t y : s->streams)
+                cudaStreamDestroy(y);
+            delete s;
+            *rc = AWPM_ERR_CUDA;
+            return nullptr;
+        }
+        s->streams.push_back(st);
+        awpm_options o = ctx->opt;
+        o.stream = st;
+        o.mem_budget_bytes = 0;  // the server enforces the budget over all slots
+        o.flags = 0;
+        o.slots = 0;
+        o.device = ctx->device;
+        awpm_ctx *c = nullptr;
+        int r = awpm_create(&c, &o);
+        if (r != AWPM_OK) {
+            for (awpm_ctx *x : s->slots)
+                awpm_destroy(x);
+            for (cudaStream_t y : s->streams)
+                cudaStreamDestroy(y);
+            delete s;
+            *rc = r;
+            return nullptr;
+        }
+        s->slots.push_back(c);
+    }
+    s->running.assign(s->slots.size(), nullptr);
+    s->th = std::thread(scheduler, s);
+    ctx->server = s;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+void awpm_server_shutdown(awpm_ctx *ctx)
+{
+    awpm_server_impl *s = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        s = ctx->server;
+        ctx->server = nullptr;
+    }
+    if (!s)
+        return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        // requests that never started are dropped: their arrays are released
+        for (Item *it : s->queue)
+            finish_item(s, it, AWPM_ERR_NOT_FOUND);
+        s->queue.clear();
+    }
+    s->cv_work.notify_all();
+    s->th.join();
+    for (awpm_ctx *c : s->slots)
+        awpm_destroy(c);
+    for (cudaStream_t st : s->streams)
+        cudaStreamDestroy(st);
+    for (auto &kv : s->items)
+        delete kv.second;
+    delete s;
+}
+
+int awpm_submit(awpm_ctx *ctx, const awpm_problem *p, uint64_t *ticket)
+{
+    if (!ctx || !p || !ticket || p->n < 0)
+        return AWPM_ERR_INVALID_ARG;
+    int rc;
+    awpm_server_impl *s = server_of(ctx, &rc);
+    if (!s)
+        return rc;
+    Item *it = new (std::nothrow) Item();
+    if (!it)
+        return AWPM_ERR_OOM;
+    it->p = *p;
+    int32_t nnz = p->nnz;
+    const bool host_in = host_side(p->rowidx);
+    if (nnz < 0 && p->colptr && host_side(p->colptr))
+        nnz = p->colptr[p->n];
+    it->need = ctx_bytes_needed(p->n, nnz > 0 ? nnz : 0, host_in, ctx->opt.lookup);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        it->ticket = s->next_ticket++;
+        s->items[it->ticket] = it;
+        s->queue.push_back(it);
+    }
+    s->cv_work.notify_all();
+    *ticket = it->ticket;
+    return AWPM_OK;
+}
+
+int awpm_poll(awpm_ctx *ctx, uint64_t ticket, int *done, awpm_stats *stats)
+{
+    if (!ctx || !done)
+        return AWPM_ERR_INVALID_ARG;
+    awpm_server_impl *s;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        s = ctx->server;
+    }
+    if (!s)
+        return AWPM_ERR_NOT_FOUND;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto f = s->items.find(ticket);
+    if (f == s->items.end())
+        return AWPM_ERR_NOT_FOUND;
+    Item *it = f->second;
+    if (it->state != 2) {
+        *done = 0;
+        return AWPM_OK;
+    }
+    *done = 1;
+    if (stats)
+        *stats = it->st;
+    const int rc = it->rc;
+    s->items.erase(f);
+    delete it;
+    return rc;
+}
+
+int awpm_wait(awpm_ctx *ctx, uint64_t ticket, awpm_stats *stats)
+{
+    if (!ctx)
+        return AWPM_ERR_INVALID_ARG;
+    awpm_server_impl *s;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        s = ctx->server;
+    }
+    if (!s)
+        return AWPM_ERR_NOT_FOUND;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto f = s->items.find(ticket);
+    if (f == s->items.end())
+        return AWPM_ERR_NOT_FOUND;
+    Item *it = f->second;
+    s->cv_done.wait(lk, [it] { return it->state == 2; });
+    if (stats)
+        *stats = it->st;
+    const int rc = it->rc;
+    s->items.erase(ticket);
+    delete it;
+    return rc;
+}
+
+}  // extern "C"

@@ -28,7 +28,8 @@ def built_lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("awpm_create", "awpm_destroy", "awpm_improve", "awpm_improve_ctx",
-                     "awpm_search", "awpm_strerror", "awpm_default_options"):
+                     "awpm_search", "awpm_strerror", "awpm_default_options", "awpm_submit",
+                     "awpm_poll", "awpm_improve_batch"):
         assert required in names
 
 
@@ -46,8 +47,10 @@ def test_binding_covers_the_header():
 def test_struct_layouts_match_header():
     """ctypes mirrors of awpm_options / awpm_stats have the C sizes."""
     from paper_1801_09809_gb300 import awpm
-    # awpm_options: 4 x int32 + pointer + size_t
-    assert ctypes.sizeof(awpm.Options) == 16 + 8 + 8
+    # awpm_options: 4 x int32 + pointer + size_t + 2 x int32
+    assert ctypes.sizeof(awpm.Options) == 16 + 8 + 8 + 8
+    # awpm_problem: 2 x int32 + 5 pointers
+    assert ctypes.sizeof(awpm.Problem) == 8 + 40
     # awpm_stats: 2 int32 + 5 int64 + 4 double + 2 int32
     assert ctypes.sizeof(awpm.Stats) == 8 + 40 + 32 + 8
 
