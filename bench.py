@@ -84,6 +84,15 @@ def peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+def search_kernel_hash():
+    """sha256 (16 hex digits) of the search kernel's source text, from its
+    template line to the Step D section."""
+    text = open(KERNEL_SRC).read()
+    a = text.index("template <int kLookup, bool kBatch, bool kPipe>")
+    b = text.index("// Step D (Algorithm 6)")
+    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
+
+
 def profile_traffic():
     """DRAM bytes per search launch from the committed ncu summary, or None
     when the kernel source changed since the capture."""
@@ -91,7 +100,7 @@ def profile_traffic():
         text = open(PROFILE).read()
     except OSError:
         return None
-    src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    src_hash = search_kernel_hash()
     vals = {}
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):
@@ -157,26 +166,40 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """Ranks from the torchrun environment; one process per GPU.  The
+    replicas share nothing on the data path: the process group only carries
+    the barriers and the max-over-ranks time."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return rank, world, local
 
 
 def barrier_max(world, x):
+    """Maximum of x over the ranks (the whole job ends with its slowest rank)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(units_per_rank, world, ms_max):
+    """Whole-job throughput of independent replicas: units of all ranks over
+    the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
 
 
 def barrier(world):
@@ -395,7 +418,7 @@ def main():
         barrier(world)
     ms = e0.elapsed_time(e1)
     ms_max = barrier_max(world, ms)
-    value = checks * world / (ms_max / 1e3)
+    value = replica_value(checks, world, ms_max)
 
     # timed region 2: the same solves with CUDA events around every search launch
     for _ in range(2):
@@ -458,7 +481,7 @@ def main():
                              ((4 * (n + 1) + 12 * nnz) / 1e6),
                        "hbm_gbs_search": achieved},
             "roofline": roofline,
-            "e2e": {"value": e2e_checks * world / (e2e_ms / 1e3), "unit": UNIT,
+            "e2e": {"value": replica_value(e2e_checks, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk.summary()}

@@ -976,6 +976,18 @@ static inline unsigned tile_grid(const Shape &sh)
     return (unsigned)(sh.num_sms * 8);
 }
 
+// The one-off initialisation kernels are chains of dependent loads per
+// column (or per tile); wider grids keep more of them in flight.
+static inline unsigned init_grid(const Shape &sh)
+{
+    return (unsigned)(sh.num_sms * 16);
+}
+
+static inline unsigned init_tile_grid(const Shape &sh)
+{
+    return (unsigned)(sh.num_sms * 32);
+}
+
 void Sink::launch(const void *func, unsigned grid, unsigned block, void **args)
 {
     if (err != cudaSuccess)
@@ -1001,16 +1013,16 @@ void launch_init(const Work *d, const Shape &sh, Sink &k)
 {
     void *a[] = {(void *)&d};
     k.launch((const void *)k_reset, util_grid(sh), kThreads, a);
-    k.launch((const void *)k_check_colptr, util_grid(sh), kThreads, a);
-    k.launch((const void *)k_mark_starts, util_grid(sh), kThreads, a);
-    k.launch((const void *)k_entries, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_check_colptr, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_mark_starts, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_entries, init_tile_grid(sh), kThreads, a);
     if (sh.batch)
-        k.launch((const void *)k_batch_cols, util_grid(sh), kThreads, a);
-    k.launch((const void *)k_init_mates, util_grid(sh), kThreads, a);
+        k.launch((const void *)k_batch_cols, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_init_mates, init_grid(sh), kThreads, a);
     if (sh.batch)
-        k.launch((const void *)k_batch_check, tile_grid(sh), kThreads, a);
+        k.launch((const void *)k_batch_check, init_tile_grid(sh), kThreads, a);
     if (sh.lookup == AWPM_LOOKUP_HASH)
-        k.launch((const void *)k_hash_build, tile_grid(sh), kThreads, a);
+        k.launch((const void *)k_hash_build, init_tile_grid(sh), kThreads, a);
 }
 
 void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k)
