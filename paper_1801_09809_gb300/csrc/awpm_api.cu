@@ -138,15 +138,25 @@ int check_sink(const Sink &k)
     return AWPM_OK;
 }
 
-Shape shape_of(const awpm_ctx *c, bool batch, int lookup)
+Shape shape_of(const awpm_ctx *c, bool batch, int lookup, bool pipe)
 {
     Shape sh;
     sh.num_sms = c->num_sms;
     sh.batch = batch;
     sh.lookup = lookup;
-    sh.search_bps = c->search_bps[batch ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0];
-    sh.pipe = c->search_pipe;
+    sh.pipe = pipe;
+    sh.search_bps = c->search_bps[batch ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0][pipe ? 1 : 0];
     return sh;
+}
+
+int ilog2(int64_t x)
+{
+    int l = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++l;
+    }
+    return l;
 }
 
 // The solve graph of one launch shape: initialisation, WHILE{pass}, final
@@ -194,7 +204,6 @@ int build_graph(awpm_ctx *c, const Shape &sh, cudaGraphExec_t *out)
         goto done;
     }
     sb.graph = cp.conditional.phGraph_out[0];
-    launch_reset_best(d, sh, sb);
     launch_search(d, sh, sb);
     launch_select_and_flip(d, sh, sb);
     launch_control(d, sh, true, h, sb);
@@ -254,7 +263,6 @@ int run_timed(awpm_ctx *c, const Shape &sh, int max_passes, int *passes_enqueued
                 break;
         }
         AWPM_TRY(ensure_timing_events(c, (size_t)t + 1));
-        launch_reset_best(d, sh, k);
         CUDA_TRY(cudaEventRecord(c->tev[2 * t], s));
         launch_search(d, sh, k);
         CUDA_TRY(cudaEventRecord(c->tev[2 * t + 1], s));
@@ -295,7 +303,8 @@ namespace awpm {
 size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup)
 {
     const size_t N = (size_t)n, Z = (size_t)nnz, T = Z / kTile + 1;
-    size_t b = N * (4 + 4 + 8 + sizeof(RowRec) + 8 + 8 + sizeof(Rec) + sizeof(Sel)) + 4 * T +
+    size_t b = N * (4 + 4 + 8 + sizeof(RowRec) + 8 + 8 + sizeof(Rec) + sizeof(Sel) + 4) + N / 8 +
+               4 * T +
                4 * (Z / 32 + 1) + sizeof(Ctl) + 8 * kWsumBlocks;
     if (lookup == AWPM_LOOKUP_HASH)
         b += 16 * Z;
@@ -324,10 +333,11 @@ int setup_ctx(awpm_ctx *c, const awpm_options *opt)
     CUDA_TRY(cudaSetDevice(dev));
     CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     c->search_pipe = default_search_pipe();
-    for (int b = 0; b < 2; ++b) {
-        c->search_bps[b][0] = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, b == 1, c->search_pipe);
-        c->search_bps[b][1] = search_blocks_per_sm(AWPM_LOOKUP_HASH, b == 1, c->search_pipe);
-    }
+    for (int b = 0; b < 2; ++b)
+        for (int p = 0; p < 2; ++p) {
+            c->search_bps[b][0][p] = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, b == 1, p == 1);
+            c->search_bps[b][1][p] = search_blocks_per_sm(AWPM_LOOKUP_HASH, b == 1, p == 1);
+        }
     if (c->opt.stream) {
         c->stream = (cudaStream_t)c->opt.stream;
         c->own_stream = false;
@@ -355,16 +365,17 @@ void teardown_ctx(awpm_ctx *c)
         cudaStreamSynchronize(c->stream);
     for (int b = 0; b < 2; ++b)
         for (int h = 0; h < 2; ++h)
-            if (c->g_exec[b][h]) {
-                cudaGraphExecDestroy(c->g_exec[b][h]);
-                c->g_exec[b][h] = nullptr;
-            }
+            for (int p = 0; p < 2; ++p)
+                if (c->g_exec[b][h][p]) {
+                    cudaGraphExecDestroy(c->g_exec[b][h][p]);
+                    c->g_exec[b][h][p] = nullptr;
+                }
     DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->wmr,
                       &c->colsig,  &c->best,     &c->dsel,     &c->tile_col, &c->starts,
                       &c->ctl,     &c->wpart,    &c->htab,     &c->b_noff,   &c->b_colmat,
                       &c->b_tilemat, &c->b_i32,  &c->b_u64,    &c->b_f64,    &c->s_colptr,
                       &c->s_rowidx, &c->s_w,     &c->s_mate,   &c->s_out,    &c->s_gain,
-                      &c->s_row,   &c->d_work};
+                      &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_work)
@@ -399,8 +410,7 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
         (r.count > 0 && !r.n_off))
         return AWPM_ERR_INVALID_ARG;
     CUDA_TRY(cudaSetDevice(c->device));
-    const int lookup = c->opt.lookup == AWPM_LOOKUP_HASH ? AWPM_LOOKUP_HASH : AWPM_LOOKUP_BSEARCH;
-    pd.lookup = lookup;
+    pd.lookup = c->opt.lookup == AWPM_LOOKUP_HASH ? AWPM_LOOKUP_HASH : AWPM_LOOKUP_BSEARCH;
     pd.search_only = r.search_only;
     if (n == 0) {
         pd.active = true;
@@ -430,6 +440,23 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     }
     if (nnz < 0 || (nnz > 0 && (!r.rowidx || !r.weight)))
         return AWPM_ERR_INVALID_ARG;
+    const bool timed = (c->opt.flags & AWPM_FLAG_TIME_SEARCH) != 0;
+    // launch configuration: given, or the autotuner's (AWPM_LOOKUP_AUTO)
+    int lookup = pd.lookup;
+    bool pipe = c->search_pipe;
+    if (c->opt.lookup == AWPM_LOOKUP_AUTO && !r.search_only && !timed) {
+        const uint64_t key = ((uint64_t)(r.count > 0) << 62) | ((uint64_t)ilog2(n) << 32) |
+                             (uint64_t)ilog2(nnz > 0 ? nnz : 1);
+        TuneEntry &te = c->tune[key];
+        const int cfg = te.chosen >= 0 ? te.chosen : te.trials;
+        lookup = kTune[cfg].lookup;
+        pipe = kTune[cfg].pipe;
+        if (te.chosen < 0) {
+            pd.tune_cfg = cfg;
+            pd.tune_key = key;
+        }
+    }
+    pd.lookup = lookup;
     const int32_t ntiles = (int32_t)(((int64_t)nnz + kTile - 1) / kTile);
     const int32_t max_passes = c->opt.max_iters > 0 ? c->opt.max_iters : AWPM_PASS_CAP;
     const int32_t count = r.count;
@@ -442,6 +469,8 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     AWPM_TRY(ensure(c, c->colsig, sizeof(unsigned long long) * n));
     AWPM_TRY(ensure(c, c->best, sizeof(Rec) * n));
     AWPM_TRY(ensure(c, c->dsel, sizeof(Sel) * n));
+    AWPM_TRY(ensure(c, c->winbits, sizeof(uint32_t) * ((size_t)n / 32 + 1)));
+    AWPM_TRY(ensure(c, c->wkey, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->tile_col, sizeof(int32_t) * ((size_t)ntiles + 1)));
     AWPM_TRY(ensure(c, c->starts, sizeof(uint32_t) * (((size_t)nnz + 31) / 32 + 1)));
     AWPM_TRY(ensure(c, c->ctl, sizeof(Ctl)));
@@ -449,6 +478,15 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     if (lookup == AWPM_LOOKUP_HASH)
         AWPM_TRY(ensure(c, c->htab, sizeof(unsigned long long) * 2 * (size_t)nnz));
 
+    // the solve graph of this launch shape, built once (before the timed span)
+    cudaGraphExec_t gexec = nullptr;
+    if (!r.search_only && !timed) {
+        cudaGraphExec_t &g =
+            c->g_exec[count > 0 ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0][pipe ? 1 : 0];
+        if (!g)
+            AWPM_TRY(build_graph(c, shape_of(c, count > 0, lookup, pipe), &g));
+        gexec = g;
+    }
     CUDA_TRY(cudaEventRecord(c->ev_a, c->stream));
     Work &wk = *c->h_work;
     std::memset(&wk, 0, sizeof(Work));
@@ -470,6 +508,8 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     wk.htab = lookup == AWPM_LOOKUP_HASH ? (unsigned long long *)c->htab.p : nullptr;
     wk.best = (Rec *)c->best.p;
     wk.dsel = (Sel *)c->dsel.p;
+    wk.winbits = (uint32_t *)c->winbits.p;
+    wk.wkey = (int32_t *)c->wkey.p;
     wk.tile_col = (int32_t *)c->tile_col.p;
     wk.starts = (uint32_t *)c->starts.p;
     wk.ctl = (Ctl *)c->ctl.p;
@@ -507,8 +547,7 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     CUDA_TRY(cudaMemcpyAsync(c->d_work.p, c->h_work, sizeof(Work), cudaMemcpyHostToDevice,
                              c->stream));
     const Work *d = (const Work *)c->d_work.p;
-    const Shape sh = shape_of(c, count > 0, lookup);
-    const bool timed = (c->opt.flags & AWPM_FLAG_TIME_SEARCH) != 0;
+    const Shape sh = shape_of(c, count > 0, lookup, pipe);
 
     if (r.search_only) {
         Sink k;
@@ -536,10 +575,7 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     } else if (timed) {
         AWPM_TRY(run_timed(c, sh, max_passes, &pd.passes_enqueued));
     } else {
-        cudaGraphExec_t &g = c->g_exec[count > 0 ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0];
-        if (!g)
-            AWPM_TRY(build_graph(c, sh, &g));
-        CUDA_TRY(cudaGraphLaunch(g, c->stream));
+        CUDA_TRY(cudaGraphLaunch(gexec, c->stream));
     }
     if (!r.search_only)
         CUDA_TRY(cudaMemcpyAsync(r.mate_out, wk.mc, sizeof(int32_t) * n,
@@ -605,6 +641,20 @@ int ctx_finish(awpm_ctx *c, awpm_stats *st, awpm_stats *per_matrix)
     }
     float ms_total = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms_total, c->ev_a, c->ev_b));
+    if (pd.tune_cfg >= 0) {
+        TuneEntry &te = c->tune[pd.tune_key];
+        if (te.chosen < 0 && pd.tune_cfg == te.trials) {
+            te.ms[te.trials++] = ms_total;
+            if (te.trials == kTuneConfigs) {
+                int best = 0;
+                for (int k = 1; k < kTuneConfigs; ++k)
+                    if (te.ms[k] < te.ms[best])
+                        best = k;
+                te.chosen = best;
+            }
+        }
+        pd.tune_cfg = -1;
+    }
     S.iterations = h.iterations;
     S.converged = h.converged;
     S.cycles_applied = (int64_t)h.cycles;

@@ -6,6 +6,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -35,6 +36,24 @@ struct Request {
     int32_t *row_out = nullptr;
 };
 
+// Launch configurations the autotuner tries (AWPM_LOOKUP_AUTO): closing-edge
+// lookup and whether the search kernel prefetches the next tile.
+struct TuneConfig {
+    int lookup;
+    bool pipe;
+};
+constexpr int kTuneConfigs = 3;
+constexpr TuneConfig kTune[kTuneConfigs] = {
+    {AWPM_LOOKUP_BSEARCH, true}, {AWPM_LOOKUP_BSEARCH, false}, {AWPM_LOOKUP_HASH, true}};
+
+// Per problem class (batched or not, log2 of n and of nnz): the time of each
+// configuration's trial solve and the configuration chosen once all ran.
+struct TuneEntry {
+    int trials = 0;
+    float ms[kTuneConfigs] = {};
+    int chosen = -1;
+};
+
 // What finish() needs to turn the device results into statistics.
 struct Pending {
     bool active = false;
@@ -42,6 +61,8 @@ struct Pending {
     bool search_only = false, timed = false, trivial = false;
     int passes_enqueued = 0;
     std::vector<int32_t> n_off;  // host copy of the batch offsets
+    int tune_cfg = -1;           // autotuner trial of this solve, or -1
+    uint64_t tune_key = 0;
 };
 
 int setup_ctx(struct ::awpm_ctx *c, const awpm_options *opt);
@@ -67,10 +88,11 @@ struct awpm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t held = 0;
-    int search_bps[2][2] = {{1, 1}, {1, 1}};  // [batch][hash]
-    bool search_pipe = true;
+    int search_bps[2][2][2] = {};  // [batch][hash][pipe]
+    bool search_pipe = true;      // default when the lookup is given explicitly
     // per-solve device workspace
     awpm::DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
+    awpm::DevBuf winbits, wkey;
     awpm::DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
     // staging of host-resident arrays
     awpm::DevBuf s_colptr, s_rowidx, s_w, s_mate, s_out, s_gain, s_row;
@@ -83,8 +105,9 @@ struct awpm_ctx {
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     std::vector<cudaEvent_t> tev;     // timing pairs of the timed loop
     std::vector<cudaEvent_t> flagev;  // ring of the timed loop
-    // one instantiated graph per [batch][hash]
-    cudaGraphExec_t g_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    // one instantiated graph per [batch][hash][pipe]
+    cudaGraphExec_t g_exec[2][2][2] = {};
+    std::map<uint64_t, awpm::TuneEntry> tune;  // autotuner state per problem class
     awpm::Pending pend;
     // the request server of this context (awpm_submit), created on first use
     struct awpm_server_impl *server = nullptr;

@@ -29,10 +29,10 @@ struct alignas(16) Rec {
 };
 
 // Per-row view of the column matched to row i (m_i): where its rows sit in
-// the CSC arrays and a 64-bit signature of those rows (bit sig_bit(r) set for
-// every stored row r).  A clear bit proves that the closing entry (m_j, m_i)
-// is absent without touching the column; the record is rewritten whenever
-// row i changes mate.
+// the CSC arrays and a 64-bit signature of those rows (the bits sig_mask(r)
+// set for every stored row r).  A clear bit proves that the closing entry
+// (m_j, m_i) is absent without touching the column; the record is rewritten
+// whenever row i changes mate.
 struct alignas(16) RowRec {
     int32_t s;
     int32_t e;
@@ -109,6 +109,8 @@ struct Work {
     unsigned long long *htab;    // per-column hash tables (2 slots per nonzero), or null
     Rec *best;          // Step-C records
     Sel *dsel;          // Step-D selections
+    uint32_t *winbits;  // bit j: column j holds a Step-C winner this pass
+    int32_t *wkey;      // key column of winner j (set by Step D), -1 if dropped
     int32_t *tile_col;  // column holding the first nonzero of each tile
     uint32_t *starts;   // bit p set when a column starts at nonzero p
     Ctl *ctl;
@@ -143,7 +145,6 @@ struct Sink {
 // Launch sequences; `d` is the device copy of the Work.
 void launch_init(const Work *d, const Shape &sh, Sink &k);
 void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k);
-void launch_reset_best(const Work *d, const Shape &sh, Sink &k);
 void launch_search(const Work *d, const Shape &sh, Sink &k);
 void launch_select_and_flip(const Work *d, const Shape &sh, Sink &k);
 void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,

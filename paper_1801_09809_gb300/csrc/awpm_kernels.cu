@@ -27,8 +27,15 @@ namespace awpm {
 // into an error bit instead of a hang).
 constexpr int kCasRetryCap = 1 << 20;
 
-// Closing-edge ranges longer than this go to the warp-cooperative search.
+// Closing-edge ranges longer than this go to the warp-cooperative search,
+// and so do all of a warp's ranges when at most kCoopFew lanes need one.
 constexpr int32_t kCoopMin = 32;
+#ifndef AWPM_COOP_FEW
+#define AWPM_COOP_FEW 3
+#endif
+constexpr int kCoopFew = AWPM_COOP_FEW;
+// Quiet NaN: wm[j] before the entry pass finds the matched entry of column j.
+constexpr unsigned long long kNaNBits = 0x7ff8000000000000ull;
 
 constexpr int kThreads = 256;
 
@@ -55,24 +62,6 @@ __device__ __forceinline__ bool gate(const Ctl *ctl)
 {
     return *(volatile const unsigned *)&ctl->err == 0u &&
            *(volatile const int32_t *)&ctl->active != 0;
-}
-
-// Lower bound of row r among the sorted rows rowidx[s..e); position or -1.
-__device__ __forceinline__ int32_t find_row(const int32_t *__restrict__ rowidx, int32_t s,
-                                            int32_t e, int32_t r)
-{
-    int32_t lo = s, len = e - s;
-    while (len > 0) {
-        int32_t half = len >> 1;
-        int32_t mid = lo + half;
-        if (__ldg(rowidx + mid) < r) {
-            lo = mid + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return (lo < e && __ldg(rowidx + lo) == r) ? lo : -1;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
@@ -123,10 +112,20 @@ __device__ double block_sum_f64(double v)
     return v;
 }
 
-// Bit of row r in a column signature (multiplicative hash, top 6 bits).
-__device__ __forceinline__ unsigned sig_bit(int32_t r)
+// Bits of row r in a column signature, a 64-bit Bloom filter of the
+// column's rows with AWPM_SIG_HASHES bit positions per row, all taken from
+// one multiplicative hash (bits 26..31, then 20..25).  A row whose bits are
+// not all set in the signature is not stored in the column.
+#ifndef AWPM_SIG_HASHES
+#define AWPM_SIG_HASHES 2
+#endif
+__device__ __forceinline__ unsigned long long sig_mask(int32_t r)
 {
-    return ((uint32_t)r * 0x9E3779B1u) >> 26;
+    const uint32_t h = (uint32_t)r * 0x9E3779B1u;
+    unsigned long long m = 1ull << (h >> 26);
+    if (AWPM_SIG_HASHES > 1)
+        m |= 1ull << ((h >> 20) & 63u);
+    return m;
 }
 
 // Column of the lane's nonzero: c0 (column of the tile's first nonzero) plus
@@ -303,10 +302,13 @@ __global__ void k_reset(const Work *__restrict__ W)
         w.best[j] = Rec{0.0, 0, 0};
         w.dsel[j] = Sel{0.0, 0, 0};
         w.colsig[j] = 0ull;
+        w.wm[j] = __longlong_as_double(kNaNBits);  // "no matched entry seen"
     }
     const int64_t words = ((int64_t)w.nnz + 31) / 32 + 1;
     for (int64_t x = gtid(); x < words; x += gstride())
         w.starts[x] = 0u;
+    for (int64_t x = gtid(); x <= w.n / 32; x += gstride())
+        w.winbits[x] = 0u;
     if (w.lookup == AWPM_LOOKUP_HASH && w.htab)
         for (int64_t x = gtid(); x < 2 * (int64_t)w.nnz; x += gstride())
             w.htab[x] = kSlotEmpty;
@@ -319,7 +321,8 @@ __global__ void k_reset(const Work *__restrict__ W)
     }
 }
 
-// colptr[0] = 0, non-decreasing, colptr[n] = nnz.
+// colptr[0] = 0, non-decreasing, colptr[n] = nnz.  An empty column cannot
+// hold a matched entry, so it already rules out a perfect matching.
 __global__ void k_check_colptr(const Work *__restrict__ W)
 {
     const Work &w = *W;
@@ -329,6 +332,8 @@ __global__ void k_check_colptr(const Work *__restrict__ W)
                          (j == w.n && c != w.nnz);
         if (bad)
             raise_err(w.ctl, kErrInvalid);
+        else if (j < w.n && w.colptr[j + 1] == c)
+            raise_err(w.ctl, kErrNotPerfect);
     }
 }
 
@@ -336,7 +341,7 @@ __global__ void k_check_colptr(const Work *__restrict__ W)
 __global__ void k_mark_starts(const Work *__restrict__ W)
 {
     const Work &w = *W;
-    if (w.ctl->err)
+    if (w.ctl->err & kErrInvalid)
         return;
     for (int64_t j = gtid(); j < w.n; j += gstride()) {
         const int32_t s = w.colptr[j], e = w.colptr[j + 1];
@@ -349,48 +354,83 @@ __global__ void k_mark_starts(const Work *__restrict__ W)
 }
 
 // One pass over the entries: row range, sortedness inside columns, finite
-// weights, and the column signatures (OR of 1 << sig_bit(row) over each
-// column; lanes of one column are OR-ed in the warp, whole columns stored,
-// columns cut by a tile boundary merged with atomics).
+// weights, the column signatures (OR of sig_mask(row) over each column;
+// lanes of one column are OR-ed in the warp, whole columns stored, columns cut
+// by a tile boundary merged with atomics) and the matched weight of every
+// column: the lane holding (mate_in[j], j) stores its weight as wm[j].  Each
+// warp takes two tiles per round and issues both tiles' loads before using
+// either, so twice the bytes are in flight.  Column numbers come from the
+// start bitmap, exact once no column is empty (empty columns were reported by
+// the column-pointer check and always stay below n).
 __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W)
 {
     const Work &w = *W;
     if (w.ctl->err & kErrInvalid)
         return;
+    constexpr int kU = 2;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = gstride() >> 5;
     const int32_t n = w.n, nnz = w.nnz;
+    const int32_t *__restrict__ rowidx = w.rowidx;
     unsigned bits = 0;
-    for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
-        const int32_t base = (int32_t)(t * kTile);
-        const int32_t p = base + lane;
-        const bool valid = p < nnz;
-        const int32_t c0 = w.tile_col[t];
-        const uint32_t mask = w.starts[t];
-        const int32_t r = valid ? __ldcs(w.rowidx + p) : 0;
-        if (valid) {
-            if (r < 0 || r >= n)
-                bits |= kErrInvalid;
-            if (!isfinite(__ldcs(w.w + p)))
-                bits |= kErrNonfinite;
-            if (p > 0 && !((mask >> lane) & 1u) && w.rowidx[p - 1] >= r)
-                bits |= kErrUnsorted;
-        }
-        const int32_t j = valid ? lane_column(c0, mask, lane) : -1 - lane;
-        unsigned long long v = (valid && r >= 0 && r < n) ? (1ull << sig_bit(r)) : 0ull;
+    for (int64_t t0 = gtid() >> 5; t0 < w.ntiles; t0 += kU * nwarps) {
+        int32_t c0[kU], r[kU], prev[kU], mate[kU], j[kU];
+        uint32_t mask[kU];
+        double x[kU];
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const unsigned long long ov = __shfl_down_sync(FULL_MASK, v, off);
-            const int32_t oj = __shfl_down_sync(FULL_MASK, j, off);
-            if (lane + off < 32 && oj == j)
-                v |= ov;
+        for (int u = 0; u < kU; ++u) {
+            const int64_t t = t0 + u * nwarps;
+            const int32_t p = (int32_t)(t * kTile) + lane;
+            const bool tv = t < w.ntiles;
+            const bool valid = tv && p < nnz;
+            c0[u] = tv ? __ldg(w.tile_col + t) : 0;
+            mask[u] = tv ? __ldg(w.starts + t) : 1u;
+            r[u] = valid ? __ldcs(rowidx + p) : 0;
+            x[u] = valid ? __ldcs(w.w + p) : 0.0;
+            prev[u] = (valid && lane == 0 && p > 0) ? __ldg(rowidx + p - 1) : 0;
         }
-        const bool head = valid && (lane == 0 || ((mask >> lane) & 1u));
-        if (head && j < n) {
-            if (segment_complete(mask, lane, base, nnz, w.starts, t))
-                w.colsig[j] = v;
-            else if (v)
-                atomicOr(w.colsig + j, v);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t t = t0 + u * nwarps;
+            const int32_t p = (int32_t)(t * kTile) + lane;
+            const bool valid = t < w.ntiles && p < nnz;
+            j[u] = valid ? lane_column(c0[u], mask[u], lane) : -1 - lane;
+            mate[u] = valid ? __ldg(w.mate_in + j[u]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t t = t0 + u * nwarps;
+            const int32_t base = (int32_t)(t * kTile);
+            const int32_t p = base + lane;
+            const bool valid = t < w.ntiles && p < nnz;
+            const int32_t up = __shfl_up_sync(FULL_MASK, r[u], 1);
+            const int32_t before = lane == 0 ? prev[u] : up;
+            const bool in_range = r[u] >= 0 && r[u] < n;
+            if (valid) {
+                if (!in_range)
+                    bits |= kErrInvalid;
+                if (!isfinite(x[u]))
+                    bits |= kErrNonfinite;
+                if (p > 0 && !((mask[u] >> lane) & 1u) && before >= r[u])
+                    bits |= kErrUnsorted;
+                if (mate[u] == r[u])
+                    w.wm[j[u]] = x[u];
+            }
+            unsigned long long v = (valid && in_range) ? sig_mask(r[u]) : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long ov = __shfl_down_sync(FULL_MASK, v, off);
+                const int32_t oj = __shfl_down_sync(FULL_MASK, j[u], off);
+                if (lane + off < 32 && oj == j[u])
+                    v |= ov;
+            }
+            const bool head = valid && (lane == 0 || ((mask[u] >> lane) & 1u));
+            if (head && j[u] < n) {
+                if (segment_complete(mask[u], lane, base, nnz, w.starts, t))
+                    w.colsig[j[u]] = v;
+                else if (v)
+                    atomicOr(w.colsig + j[u], v);
+            }
         }
     }
     bits = __reduce_or_sync(FULL_MASK, bits);
@@ -398,9 +438,9 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
         raise_err(w.ctl, bits);
 }
 
-// mc = mate_in, mr = its inverse, wm[j] = w(mate_in[j], j), and the row
-// record and matched weight of every row; checks that mate_in is a
-// permutation over stored entries.
+// mc = mate_in, mr = its inverse, and the row record and matched weight of
+// every row; checks that mate_in is a permutation over stored entries (the
+// entry pass left wm[j] = NaN where (mate_in[j], j) is not stored).
 __global__ void k_init_mates(const Work *__restrict__ W)
 {
     const Work &w = *W;
@@ -415,17 +455,14 @@ __global__ void k_init_mates(const Work *__restrict__ W)
         }
         if (atomicCAS(&w.mr[r], -1, (int32_t)j) != -1)
             raise_err(w.ctl, kErrNotPerfect);
-        const int32_t s = w.colptr[j], e = w.colptr[j + 1];
-        const int32_t q = find_row(w.rowidx, s, e, r);
-        if (q < 0) {
+        const double x = w.wm[j];
+        if (isnan(x)) {
             raise_err(w.ctl, kErrNotPerfect);
             continue;
         }
-        const double x = w.w[q];
-        w.wm[j] = x;
         RowRec rec;
-        rec.s = s;
-        rec.e = e;
+        rec.s = w.colptr[j];
+        rec.e = w.colptr[j + 1];
         rec.sig = w.colsig[j];
         w.rr[r] = rec;
         w.wmr[r] = x;
@@ -576,16 +613,6 @@ __global__ void k_batch_wsum(const Work *__restrict__ W, int out)
 // Steps A + B + C (Algorithms 3, 4, 5): fused edge-parallel cycle search
 // ---------------------------------------------------------------------------
 
-// A new pass starts with no Step-C record.
-__global__ void k_reset_best(const Work *__restrict__ W)
-{
-    const Work &w = *W;
-    if (!gate(w.ctl))
-        return;
-    for (int64_t j = gtid(); j < w.n; j += gstride())
-        w.best[j] = Rec{0.0, 0, 0};
-}
-
 // One warp per tile of kTile consecutive nonzeros (lane = one nonzero).
 // The lane's column comes from the tile's first column and its word of the
 // column-start bitmap (one popcount).  Lane with nonzero p = (i, j): if
@@ -618,6 +645,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
     const double *__restrict__ wmr = W->wmr;
     const unsigned long long *__restrict__ htab = W->htab;
     Rec *__restrict__ best = W->best;
+    uint32_t *winbits = W->winbits;
     Ctl *ctl = W->ctl;
     const int32_t *__restrict__ tilemat = W->bw.tilemat;
     const int32_t *__restrict__ colmat = W->bw.colmat;
@@ -674,18 +702,19 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
         }
         const int32_t i = valid ? (kPipe ? i_now : __ldcs(rowidx + p)) : 0;
         const int32_t j = valid ? lane_column(c0, mask, lane) : -1 - lane;
+        RowRec rec;
+        rec.s = rec.e = 0;
+        rec.sig = 0ull;
         int32_t mj = valid ? ld_i32_last(mc + j, pol) : 0x7fffffff;
         if (kBatch && mixed && valid && __ldg(mdone + __ldg(colmat + j)))
             mj = 0x7fffffff;  // finished matrix: no candidate
         const bool cand = valid && i > mj;
-        RowRec rec;
-        rec.s = rec.e = 0;
-        rec.sig = 0ull;
         if (cand) {
             ++n_cand;
             rec = ld_rowrec(rr + i, pol);
         }
-        const bool pass = cand && ((rec.sig >> sig_bit(mj)) & 1ull);
+        const unsigned long long smj = sig_mask(mj);
+        const bool pass = cand && (rec.sig & smj) == smj;
         int32_t lo = rec.s;
         int32_t len = pass ? rec.e - rec.s : 0;
         int32_t q = -1;
@@ -706,8 +735,13 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
                     pos = hbase;
             }
         } else {
-            // long columns: the warp searches them together, one request at a time
+            // long columns, or every column when few lanes need a search:
+            // the warp searches them together, one request at a time (a
+            // column of up to 32 rows is one coalesced read and a ballot)
             unsigned longm = __ballot_sync(FULL_MASK, len > kCoopMin);
+            const unsigned need = __ballot_sync(FULL_MASK, len > 0);
+            if (__popc(need) <= kCoopFew)
+                longm = need;
             while (longm) {
                 const int src = __ffs(longm) - 1;
                 longm &= longm - 1;
@@ -776,6 +810,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
                 best[j] = r;
             else
                 rec_combine(best + j, r, ctl);
+            atomicOr(winbits + (j >> 5), 1u << (j & 31));
         }
     }
     block_add_u64(n_cand, &ctl->candidates);
@@ -787,70 +822,94 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
 // Step D (Algorithm 6): conflicts, per-key selection, flip
 // ---------------------------------------------------------------------------
 
-// For every Step-C winner rooted at j with second matched edge at column
-// k = m_i: drop it if column k is itself the root of a Step-C winner,
-// otherwise compete for key k (maximum gain, then lowest root j).
+// For every Step-C winner rooted at j (a set bit of the winner bitmap) with
+// second matched edge at column k = m_i: drop it if column k is itself the
+// root of a Step-C winner, otherwise compete for key k (maximum gain, then
+// lowest root j).  The winner's key (or -1) is kept for the flip.
 __global__ void k_select(const Work *__restrict__ W)
 {
     const Work &w = *W;
     if (!gate(w.ctl))
         return;
-    for (int64_t j = gtid(); j < w.n; j += gstride()) {
-        const Rec r = w.best[j];
-        if (!(r.g > 0.0))
-            continue;
-        const int32_t i = __ldg(w.rowidx + r.p);
-        const int32_t k = w.mr[i];
-        if (w.best[k].g > 0.0)
-            continue;
-        Sel s;
-        s.g = r.g;
-        s.j = (int32_t)j;
-        s.pad = 0;
-        sel_combine(w.dsel + k, s, w.ctl);
+    const int64_t words = (int64_t)w.n / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride()) {
+        uint32_t bits = w.winbits[x];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int32_t j = (int32_t)(x * 32 + b);
+            const Rec r = w.best[j];
+            const int32_t i = __ldg(w.rowidx + r.p);
+            const int32_t k = w.mr[i];
+            if ((w.winbits[k >> 5] >> (k & 31)) & 1u) {
+                w.wkey[j] = -1;
+                continue;
+            }
+            w.wkey[j] = k;
+            Sel s;
+            s.g = r.g;
+            s.j = j;
+            s.pad = 0;
+            sel_combine(w.dsel + k, s, w.ctl);
+        }
     }
 }
 
 // Flip every selected cycle: column j takes row i, key column k takes m_j;
 // the row records of rows i and m_j follow their new mates.  The selected
-// cycles are vertex-disjoint, so each thread owns its four vertices.
+// cycles are vertex-disjoint, so each thread owns its four vertices.  Each
+// thread also clears the Step-C records and winner bits it visited, which
+// leaves them empty for the next pass.
 __global__ void k_flip(const Work *__restrict__ W)
 {
     const Work &w = *W;
     unsigned long long flips = 0;
     if (gate(w.ctl)) {
-        for (int64_t k = gtid(); k < w.n; k += gstride()) {
-            const Sel s = w.dsel[k];
-            if (!(s.g > 0.0))
+        const int64_t words = (int64_t)w.n / 32 + 1;
+        for (int64_t x = gtid(); x < words; x += gstride()) {
+            uint32_t bits = w.winbits[x];
+            if (!bits)
                 continue;
-            w.dsel[k] = Sel{0.0, 0, 0};
-            const int32_t j = s.j;
-            const Rec r = w.best[j];
-            const int32_t i = w.rowidx[r.p];
-            const int32_t mj = w.mc[j];
-            const double wij = w.w[r.p];
-            const double wq = w.w[r.q];
-            w.mc[j] = i;
-            w.mr[i] = j;
-            w.mc[k] = mj;
-            w.mr[mj] = (int32_t)k;
-            w.wm[j] = wij;
-            w.wm[k] = wq;
-            RowRec a;
-            a.s = w.colptr[j];
-            a.e = w.colptr[j + 1];
-            a.sig = w.colsig[j];
-            w.rr[i] = a;
-            w.wmr[i] = wij;
-            RowRec b;
-            b.s = w.colptr[k];
-            b.e = w.colptr[k + 1];
-            b.sig = w.colsig[k];
-            w.rr[mj] = b;
-            w.wmr[mj] = wq;
-            ++flips;
-            if (w.bw.count > 0)
-                atomicAdd(w.bw.mflips + w.bw.colmat[k], 1ull);
+            w.winbits[x] = 0u;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int32_t j = (int32_t)(x * 32 + b);
+                const Rec r = w.best[j];
+                w.best[j] = Rec{0.0, 0, 0};
+                const int32_t k = w.wkey[j];
+                if (k < 0)
+                    continue;
+                const Sel s = w.dsel[k];
+                if (!(s.g > 0.0) || s.j != j)
+                    continue;  // another root won key k
+                w.dsel[k] = Sel{0.0, 0, 0};
+                const int32_t i = w.rowidx[r.p];
+                const int32_t mj = w.mc[j];
+                const double wij = w.w[r.p];
+                const double wq = w.w[r.q];
+                w.mc[j] = i;
+                w.mr[i] = j;
+                w.mc[k] = mj;
+                w.mr[mj] = k;
+                w.wm[j] = wij;
+                w.wm[k] = wq;
+                RowRec a;
+                a.s = w.colptr[j];
+                a.e = w.colptr[j + 1];
+                a.sig = w.colsig[j];
+                w.rr[i] = a;
+                w.wmr[i] = wij;
+                RowRec c;
+                c.s = w.colptr[k];
+                c.e = w.colptr[k + 1];
+                c.sig = w.colsig[k];
+                w.rr[mj] = c;
+                w.wmr[mj] = wq;
+                ++flips;
+                if (w.bw.count > 0)
+                    atomicAdd(w.bw.mflips + w.bw.colmat[k], 1ull);
+            }
         }
     }
     block_add_u64(flips, &w.ctl->pass_flips);
@@ -1034,12 +1093,6 @@ void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k)
     k.launch((const void *)k_wsum_final, 1, kWsumBlocks, ao);
     if (sh.batch)
         k.launch((const void *)k_batch_wsum, util_grid(sh), kThreads, ao);
-}
-
-void launch_reset_best(const Work *d, const Shape &sh, Sink &k)
-{
-    void *a[] = {(void *)&d};
-    k.launch((const void *)k_reset_best, util_grid(sh), kThreads, a);
 }
 
 template <int kLookup, bool kBatch, bool kPipe>

@@ -5,7 +5,7 @@
 // handed the whole GPU to its own memory pool, or code running where an
 // allocation (which may synchronise the device) is not allowed.  This entry
 // point therefore allocates nothing.  Its scratch lives in one file-scope
-// __device__ array of fixed size (kScratchBytes, about 17 MB), which every
+// __device__ array of fixed size (kScratchBytes, about 18 MB), which every
 // GPU that loads the library keeps until the process exits.  The caller
 // passes every input and output in device memory.
 #include <cuda_runtime.h>
@@ -42,7 +42,9 @@ constexpr size_t kOffRr = kOffWm + up(sizeof(double) * kMaxN);
 constexpr size_t kOffWmr = kOffRr + up(sizeof(RowRec) * kMaxN);
 constexpr size_t kOffSig = kOffWmr + up(sizeof(double) * kMaxN);
 constexpr size_t kOffBest = kOffSig + up(sizeof(unsigned long long) * kMaxN);
-constexpr size_t kOffTile = kOffBest + up(sizeof(Rec) * kMaxN);
+constexpr size_t kOffWin = kOffBest + up(sizeof(Rec) * kMaxN);
+constexpr size_t kOffWkey = kOffWin + up(sizeof(uint32_t) * (kMaxN / 32 + 1));
+constexpr size_t kOffTile = kOffWkey + up(sizeof(int32_t) * kMaxN);
 constexpr size_t kOffStarts = kOffTile + up(sizeof(int32_t) * kTilesMax);
 constexpr size_t kOffWpart = kOffStarts + up(sizeof(uint32_t) * (kMaxNnz / 32 + 1));
 constexpr size_t kScratchBytes = kOffWpart + up(sizeof(double) * kWsumBlocks);
@@ -160,6 +162,8 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     // the search never selects (Step D): its selection records share the
     // Step-C area, which launch_init clears either way
     wk.dsel = (Sel *)(base + kOffBest);
+    wk.winbits = (uint32_t *)(base + kOffWin);
+    wk.wkey = (int32_t *)(base + kOffWkey);
     wk.tile_col = (int32_t *)(base + kOffTile);
     wk.starts = (uint32_t *)(base + kOffStarts);
     wk.wpart = (double *)(base + kOffWpart);

@@ -316,3 +316,27 @@ def test_lookup_strategies(torch, orc, lookup):
             assert st["lookup_used"] == lookup
     finally:
         awpm.awpm_destroy(c)
+
+
+def test_autotuner_trials_are_exact(torch, orc):
+    """lookup AUTO: the first solves of a problem class try each launch
+    configuration (each a full solve), then one is kept; every result equals
+    the oracle's."""
+    c = awpm.awpm_create(device=0)  # lookup AUTO
+    try:
+        g = gen.rmat(1 << 13, 16, 151)
+        ref, rst, _ = orc.improve(g)
+        used = []
+        for _ in range(6):
+            got, st = run_gpu(c, g, torch=torch)
+            assert_same_as_oracle(g, got, st, ref, rst, "autotuned")
+            used.append(st["lookup_used"])
+        assert set(used[:3]) == {awpm.LOOKUP_BSEARCH, awpm.LOOKUP_HASH}
+        assert len(set(used[3:])) == 1
+        # a different size class starts its own trials
+        g2 = gen.stencil_2d(40, 152)
+        ref2, rst2, _ = orc.improve(g2)
+        got2, st2 = run_gpu(c, g2, torch=torch)
+        assert_same_as_oracle(g2, got2, st2, ref2, rst2, "autotuned 2")
+    finally:
+        awpm.awpm_destroy(c)
