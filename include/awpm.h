@@ -15,7 +15,7 @@
  * Data conventions (all entry points):
  *   - n: number of rows = number of columns, 0 <= n < 2^31.
  *   - colptr[n+1] int32, rowidx[nnz] int32, weight[nnz] double: the matrix in
- *     compressed sparse column form, nnz = colptr[n] < 2^31, colptr[0] = 0,
+ *     compressed sparse column form, nnz = colptr[n] <= 2^31 - 64, colptr[0] = 0,
  *     colptr non-decreasing, rows strictly increasing inside each column,
  *     every weight finite.  The library never modifies them.
  *   - mate_in[n] int32: the matching, mate_in[j] = row matched to column j.
@@ -66,7 +66,9 @@ extern "C" {
 /* Closing-edge lookup strategy of the cycle search (Step B). */
 #define AWPM_LOOKUP_AUTO 0    /* the library picks (per matrix)                         */
 #define AWPM_LOOKUP_BSEARCH 1 /* binary search in the sorted rows of column m_i         */
-#define AWPM_LOOKUP_HASH 2    /* per-column open-addressing table built once per solve  */
+#define AWPM_LOOKUP_HASH 2    /* per-column open-addressing table built once per solve
+                                 (nnz < 2^30; larger problems use the binary search,
+                                 as awpm_stats.lookup_used reports)                    */
 
 /* awpm_options.flags */
 #define AWPM_FLAG_TIME_SEARCH 1u /* time every cycle-search launch with CUDA events

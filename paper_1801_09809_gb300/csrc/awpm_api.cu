@@ -56,6 +56,10 @@ namespace {
             return rc_;        \
     } while (0)
 
+// Largest nnz: positions up to nnz + 31 (a tile's last lane) stay in int32.
+constexpr int32_t kMaxNnz = 0x7fffffff - 63;
+// Largest nnz served by the hash lookup (slot 2 * position in int32).
+constexpr int32_t kMaxHashNnz = (1 << 30) - 1;
 constexpr int kLookahead = 2;
 constexpr int kRing = 4;
 
@@ -306,8 +310,10 @@ size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup)
     size_t b = N * (4 + 4 + 8 + sizeof(RowRec) + 8 + 8 + sizeof(Rec) + sizeof(Sel) + 4) + N / 8 +
                4 * T +
                4 * (Z / 32 + 1) + sizeof(Ctl) + 8 * kWsumBlocks;
-    if (lookup == AWPM_LOOKUP_HASH)
+    if (lookup != AWPM_LOOKUP_BSEARCH)  // hash tables (AUTO may pick them)
         b += 16 * Z;
+    if (lookup != AWPM_LOOKUP_HASH)  // Bloom filters of the binary search
+        b += Z + 4;
     if (host_inputs)
         b += 4 * (N + 1) + 12 * Z + 8 * N;
     return b + b / 8;
@@ -375,7 +381,7 @@ void teardown_ctx(awpm_ctx *c)
                       &c->ctl,     &c->wpart,    &c->htab,     &c->b_noff,   &c->b_colmat,
                       &c->b_tilemat, &c->b_i32,  &c->b_u64,    &c->b_f64,    &c->s_colptr,
                       &c->s_rowidx, &c->s_w,     &c->s_mate,   &c->s_out,    &c->s_gain,
-                      &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey};
+                      &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey,     &c->bloom};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_work)
@@ -438,7 +444,8 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
             nnz = r.colptr[n];
         }
     }
-    if (nnz < 0 || (nnz > 0 && (!r.rowidx || !r.weight)))
+    // tile arithmetic is int32: positions up to nnz + 31 must fit
+    if (nnz < 0 || nnz > kMaxNnz || (nnz > 0 && (!r.rowidx || !r.weight)))
         return AWPM_ERR_INVALID_ARG;
     const bool timed = (c->opt.flags & AWPM_FLAG_TIME_SEARCH) != 0;
     // launch configuration: given, or the autotuner's (AWPM_LOOKUP_AUTO)
@@ -456,6 +463,9 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
             pd.tune_key = key;
         }
     }
+    // hash slots are addressed as 2 * position in int32
+    if (lookup == AWPM_LOOKUP_HASH && nnz > kMaxHashNnz)
+        lookup = AWPM_LOOKUP_BSEARCH;
     pd.lookup = lookup;
     const int32_t ntiles = (int32_t)(((int64_t)nnz + kTile - 1) / kTile);
     const int32_t max_passes = c->opt.max_iters > 0 ? c->opt.max_iters : AWPM_PASS_CAP;
@@ -477,6 +487,8 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     AWPM_TRY(ensure(c, c->wpart, sizeof(double) * kWsumBlocks));
     if (lookup == AWPM_LOOKUP_HASH)
         AWPM_TRY(ensure(c, c->htab, sizeof(unsigned long long) * 2 * (size_t)nnz));
+    else
+        AWPM_TRY(ensure(c, c->bloom, sizeof(uint32_t) * ((size_t)nnz / 4 + 1)));
 
     // the solve graph of this launch shape, built once (before the timed span)
     cudaGraphExec_t gexec = nullptr;
@@ -506,6 +518,7 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     wk.wmr = (double *)c->wmr.p;
     wk.colsig = (unsigned long long *)c->colsig.p;
     wk.htab = lookup == AWPM_LOOKUP_HASH ? (unsigned long long *)c->htab.p : nullptr;
+    wk.bloom = lookup == AWPM_LOOKUP_HASH ? nullptr : (uint32_t *)c->bloom.p;
     wk.best = (Rec *)c->best.p;
     wk.dsel = (Sel *)c->dsel.p;
     wk.winbits = (uint32_t *)c->winbits.p;

@@ -92,7 +92,7 @@ struct awpm_ctx {
     bool search_pipe = true;      // default when the lookup is given explicitly
     // per-solve device workspace
     awpm::DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
-    awpm::DevBuf winbits, wkey;
+    awpm::DevBuf winbits, wkey, bloom;
     awpm::DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
     // staging of host-resident arrays
     awpm::DevBuf s_colptr, s_rowidx, s_w, s_mate, s_out, s_gain, s_row;

@@ -107,6 +107,7 @@ struct Work {
     double *wmr;        // per row i: wm[mr[i]] = w(i, mr[i])
     unsigned long long *colsig;  // per column: signature of its rows
     unsigned long long *htab;    // per-column hash tables (2 slots per nonzero), or null
+    uint32_t *bloom;    // blocked Bloom filters of the long columns (a word per 4 nonzeros), or null
     Rec *best;          // Step-C records
     Sel *dsel;          // Step-D selections
     uint32_t *winbits;  // bit j: column j holds a Step-C winner this pass

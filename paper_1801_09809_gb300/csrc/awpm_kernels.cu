@@ -173,11 +173,54 @@ __device__ __forceinline__ int32_t slot_start(int32_t r, int32_t base, int32_t s
     return base + (int32_t)__umulhi(row_mix(r), (uint32_t)size);
 }
 
+// ---- blocked Bloom filters of long columns (binary-search lookup) -------------
+// A column with more than kBloomMin rows, stored at positions [s, e), owns the
+// words [s/4, (e-1)/4] of the bloom array: one 32-bit word per 4 nonzeros (a
+// word at a boundary may be shared with the neighbouring column, which only
+// adds false positives).  Each row sets three bits of one word, word and bits
+// picked by a hash of the row; a row with a clear bit is not in the column.
+// Long columns are where the 64-bit signature fills up, so this filter keeps
+// most of their absent closing entries away from the search.
+
+constexpr int32_t kBloomMin = 32;
+
+__device__ __forceinline__ void bloom_key(int32_t r, int32_t s, int32_t e, uint32_t &word,
+                                          uint32_t &bits)
+{
+    const uint32_t h = row_mix(r);
+    const uint32_t w0 = (uint32_t)s >> 2;
+    const uint32_t nw = (((uint32_t)e - 1u) >> 2) - w0 + 1u;
+    word = w0 + __umulhi(h, nw);
+    const uint32_t h2 = h * 0x9E3779B1u;
+    bits = (1u << (h2 >> 27)) | (1u << ((h2 >> 22) & 31u)) | (1u << ((h2 >> 17) & 31u));
+}
+
+// ---- gains as integers ----------------------------------------------------------
+// FP64 instructions are scarce on this GPU, so gains are compared through
+// their IEEE bit patterns.  For values in [+0, +inf] the order of the bit
+// patterns read as signed 64-bit integers is the numeric order, and equal
+// patterns are equal values; every stored or compared gain is either +0.0
+// ("none") or a positive gain.
+
+__device__ __forceinline__ long long gbits(double g)
+{
+    return __double_as_longlong(g);
+}
+
+// g > 0.0 exactly as IEEE compares it: sign clear, not zero, not NaN.
+__device__ __forceinline__ bool gain_positive(double g)
+{
+    const long long b = gbits(g);
+    return b > 0ll && b <= 0x7ff0000000000000ll;
+}
+
 // ---- lock-free arg-max records ----------------------------------------------
 
+// (g, p) beats (cg, cp): larger gain, then lower position (gains >= +0).
 __device__ __forceinline__ bool rec_better(double g, int32_t p, double cg, int32_t cp)
 {
-    return g > cg || (g == cg && p < cp);
+    const long long a = gbits(g), b = gbits(cg);
+    return a > b || (a == b && p < cp);
 }
 
 // Maximum of (g, lowest p) into a Step-C record.
@@ -196,9 +239,11 @@ __device__ void rec_combine(Rec *addr, Rec mine, Ctl *ctl)
     raise_err(ctl, kErrInternal);
 }
 
+// (g, j) beats (cg, cj): larger gain, then lower root (gains >= +0).
 __device__ __forceinline__ bool sel_better(double g, int32_t j, double cg, int32_t cj)
 {
-    return g > cg || (g == cg && j < cj);
+    const long long a = gbits(g), b = gbits(cg);
+    return a > b || (a == b && j < cj);
 }
 
 // Maximum of (g, lowest root j) into a Step-D selection.
@@ -312,6 +357,9 @@ __global__ void k_reset(const Work *__restrict__ W)
     if (w.lookup == AWPM_LOOKUP_HASH && w.htab)
         for (int64_t x = gtid(); x < 2 * (int64_t)w.nnz; x += gstride())
             w.htab[x] = kSlotEmpty;
+    if (w.bloom)
+        for (int64_t x = gtid(); x <= (int64_t)w.nnz / 4; x += gstride())
+            w.bloom[x] = 0u;
     for (int64_t b = gtid(); b < w.bw.count; b += gstride()) {
         w.bw.mdone[b] = 0;
         w.bw.miter[b] = 0;
@@ -357,7 +405,8 @@ __global__ void k_mark_starts(const Work *__restrict__ W)
 // weights, the column signatures (OR of sig_mask(row) over each column;
 // lanes of one column are OR-ed in the warp, whole columns stored, columns cut
 // by a tile boundary merged with atomics) and the matched weight of every
-// column: the lane holding (mate_in[j], j) stores its weight as wm[j].  Each
+// column: the lane holding (mate_in[j], j) stores its weight as wm[j]; with
+// the binary-search lookup also the Bloom filters of the long columns.  Each
 // warp takes two tiles per round and issues both tiles' loads before using
 // either, so twice the bytes are in flight.  Column numbers come from the
 // start bitmap, exact once no column is empty (empty columns were reported by
@@ -374,7 +423,7 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
     const int32_t *__restrict__ rowidx = w.rowidx;
     unsigned bits = 0;
     for (int64_t t0 = gtid() >> 5; t0 < w.ntiles; t0 += kU * nwarps) {
-        int32_t c0[kU], r[kU], prev[kU], mate[kU], j[kU];
+        int32_t c0[kU], r[kU], prev[kU], mate[kU], j[kU], cs[kU], ce[kU];
         uint32_t mask[kU];
         double x[kU];
 #pragma unroll
@@ -396,6 +445,9 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
             const bool valid = t < w.ntiles && p < nnz;
             j[u] = valid ? lane_column(c0[u], mask[u], lane) : -1 - lane;
             mate[u] = valid ? __ldg(w.mate_in + j[u]) : -1;
+            const bool bl = valid && w.bloom;
+            cs[u] = bl ? __ldg(w.colptr + j[u]) : 0;
+            ce[u] = bl ? __ldg(w.colptr + j[u] + 1) : 0;
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
@@ -409,19 +461,24 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
             if (valid) {
                 if (!in_range)
                     bits |= kErrInvalid;
-                if (!isfinite(x[u]))
+                if ((__double2hiint(x[u]) & 0x7ff00000) == 0x7ff00000)  // inf or NaN
                     bits |= kErrNonfinite;
                 if (p > 0 && !((mask[u] >> lane) & 1u) && before >= r[u])
                     bits |= kErrUnsorted;
                 if (mate[u] == r[u])
                     w.wm[j[u]] = x[u];
+                if (ce[u] - cs[u] > kBloomMin && in_range) {
+                    uint32_t word, b;
+                    bloom_key(r[u], cs[u], ce[u], word, b);
+                    atomicOr(w.bloom + word, b);
+                }
             }
             unsigned long long v = (valid && in_range) ? sig_mask(r[u]) : 0ull;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const unsigned long long ov = __shfl_down_sync(FULL_MASK, v, off);
-                const int32_t oj = __shfl_down_sync(FULL_MASK, j[u], off);
-                if (lane + off < 32 && oj == j[u])
+                // lane + off is in the same column: no column starts in between
+                if (lane + off < 32 && ((mask[u] >> (lane + 1)) & ((1u << off) - 1u)) == 0u)
                     v |= ov;
             }
             const bool head = valid && (lane == 0 || ((mask[u] >> lane) & 1u));
@@ -456,7 +513,7 @@ __global__ void k_init_mates(const Work *__restrict__ W)
         if (atomicCAS(&w.mr[r], -1, (int32_t)j) != -1)
             raise_err(w.ctl, kErrNotPerfect);
         const double x = w.wm[j];
-        if (isnan(x)) {
+        if (gbits(x) == (long long)kNaNBits) {
             raise_err(w.ctl, kErrNotPerfect);
             continue;
         }
@@ -644,6 +701,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
     const RowRec *__restrict__ rr = W->rr;
     const double *__restrict__ wmr = W->wmr;
     const unsigned long long *__restrict__ htab = W->htab;
+    const uint32_t *__restrict__ bloom = W->bloom;
     Rec *__restrict__ best = W->best;
     uint32_t *winbits = W->winbits;
     Ctl *ctl = W->ctl;
@@ -717,6 +775,13 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
         const bool pass = cand && (rec.sig & smj) == smj;
         int32_t lo = rec.s;
         int32_t len = pass ? rec.e - rec.s : 0;
+        if (kLookup == AWPM_LOOKUP_BSEARCH && bloom && len > kBloomMin) {
+            // long column: its Bloom filter rules most absent rows out first
+            uint32_t word, b;
+            bloom_key(mj, lo, lo + len, word, b);
+            if ((__ldg(bloom + word) & b) != b)
+                len = 0;
+        }
         int32_t q = -1;
         const double wmi = pass ? __ldg(wmr + i) : 0.0;
         if (kLookup == AWPM_LOOKUP_HASH) {
@@ -771,39 +836,44 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
                 }
             }
         }
-        double g = 0.0;
+        // the gain in FP64; from here on it is handled as its bit pattern gb
+        // (0 = no positive cycle), and q >= 0 marks a lane with one
+        long long gb = 0;
         if (q >= 0) {
             ++n_found;
             const double wij = __ldcs(wv + p);
             const double wq = __ldg(wv + q);
             const double gg = ((wij + wq) - wmi) - __ldg(wm + j);
-            if (gg > 0.0) {
+            if (gain_positive(gg)) {
                 ++n_pos;
-                g = gg;
+                gb = gbits(gg);
             } else {
                 q = -1;
             }
         }
-        if (!__any_sync(FULL_MASK, g > 0.0))
+        if (!__any_sync(FULL_MASK, q >= 0))
             continue;
-        // segmented arg-max over lanes of the same column (suffix direction)
+        // segmented arg-max over lanes of the same column (suffix direction);
+        // lanes lane and lane + off share a column when no column starts in
+        // between
         int32_t bp = valid ? p : 0x7fffffff;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const double og = __shfl_down_sync(FULL_MASK, g, off);
+            const long long og = __shfl_down_sync(FULL_MASK, gb, off);
             const int32_t op = __shfl_down_sync(FULL_MASK, bp, off);
             const int32_t oq = __shfl_down_sync(FULL_MASK, q, off);
-            const int32_t oj = __shfl_down_sync(FULL_MASK, j, off);
-            if (lane + off < 32 && oj == j && og > 0.0 && rec_better(og, op, g, bp)) {
-                g = og;
+            const bool same =
+                lane + off < 32 && ((mask >> (lane + 1)) & ((1u << off) - 1u)) == 0u;
+            if (same && oq >= 0 && (og > gb || (og == gb && op < bp))) {
+                gb = og;
                 bp = op;
                 q = oq;
             }
         }
         const bool head = valid && (lane == 0 || ((mask >> lane) & 1u));
-        if (head && g > 0.0) {
+        if (head && q >= 0) {
             Rec r;
-            r.g = g;
+            r.g = __longlong_as_double(gb);
             r.p = bp;
             r.q = q;
             if (segment_complete(mask, lane, base, nnz, starts, t))
@@ -881,7 +951,7 @@ __global__ void k_flip(const Work *__restrict__ W)
                 if (k < 0)
                     continue;
                 const Sel s = w.dsel[k];
-                if (!(s.g > 0.0) || s.j != j)
+                if (gbits(s.g) <= 0ll || s.j != j)
                     continue;  // another root won key k
                 w.dsel[k] = Sel{0.0, 0, 0};
                 const int32_t i = w.rowidx[r.p];
@@ -1015,7 +1085,7 @@ __global__ void k_export_stepc(const Work *__restrict__ W, double *gain, int32_t
         return;
     for (int64_t j = gtid(); j < w.n; j += gstride()) {
         const Rec r = w.best[j];
-        const bool has = r.g > 0.0;
+        const bool has = gbits(r.g) > 0ll;
         gain[j] = has ? r.g : 0.0;
         row[j] = has ? w.rowidx[r.p] : -1;
     }
