@@ -142,7 +142,7 @@ int check_sink(const Sink &k)
     return AWPM_OK;
 }
 
-Shape shape_of(const awpm_ctx *c, bool batch, int lookup, bool pipe)
+Shape shape_of(const awpm_ctx *c, bool batch, int lookup, bool pipe, int32_t ntiles)
 {
     Shape sh;
     sh.num_sms = c->num_sms;
@@ -150,6 +150,7 @@ Shape shape_of(const awpm_ctx *c, bool batch, int lookup, bool pipe)
     sh.lookup = lookup;
     sh.pipe = pipe;
     sh.search_bps = c->search_bps[batch ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0][pipe ? 1 : 0];
+    sh.search_waves = search_waves(sh.num_sms, sh.search_bps, ntiles);
     return sh;
 }
 
@@ -372,10 +373,11 @@ void teardown_ctx(awpm_ctx *c)
     for (int b = 0; b < 2; ++b)
         for (int h = 0; h < 2; ++h)
             for (int p = 0; p < 2; ++p)
-                if (c->g_exec[b][h][p]) {
-                    cudaGraphExecDestroy(c->g_exec[b][h][p]);
-                    c->g_exec[b][h][p] = nullptr;
-                }
+                for (int v = 0; v < 2; ++v)
+                    if (c->g_exec[b][h][p][v]) {
+                        cudaGraphExecDestroy(c->g_exec[b][h][p][v]);
+                        c->g_exec[b][h][p][v] = nullptr;
+                    }
     DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->wmr,
                       &c->colsig,  &c->best,     &c->dsel,     &c->tile_col, &c->starts,
                       &c->ctl,     &c->wpart,    &c->htab,     &c->b_noff,   &c->b_colmat,
@@ -491,12 +493,13 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
         AWPM_TRY(ensure(c, c->bloom, sizeof(uint32_t) * ((size_t)nnz / 4 + 1)));
 
     // the solve graph of this launch shape, built once (before the timed span)
+    const Shape sh = shape_of(c, count > 0, lookup, pipe, ntiles);
     cudaGraphExec_t gexec = nullptr;
     if (!r.search_only && !timed) {
-        cudaGraphExec_t &g =
-            c->g_exec[count > 0 ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0][pipe ? 1 : 0];
+        cudaGraphExec_t &g = c->g_exec[count > 0 ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0]
+                                      [pipe ? 1 : 0][sh.search_waves - 1];
         if (!g)
-            AWPM_TRY(build_graph(c, shape_of(c, count > 0, lookup, pipe), &g));
+            AWPM_TRY(build_graph(c, sh, &g));
         gexec = g;
     }
     CUDA_TRY(cudaEventRecord(c->ev_a, c->stream));
@@ -560,7 +563,6 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     CUDA_TRY(cudaMemcpyAsync(c->d_work.p, c->h_work, sizeof(Work), cudaMemcpyHostToDevice,
                              c->stream));
     const Work *d = (const Work *)c->d_work.p;
-    const Shape sh = shape_of(c, count > 0, lookup, pipe);
 
     if (r.search_only) {
         Sink k;

@@ -105,8 +105,8 @@ struct awpm_ctx {
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     std::vector<cudaEvent_t> tev;     // timing pairs of the timed loop
     std::vector<cudaEvent_t> flagev;  // ring of the timed loop
-    // one instantiated graph per [batch][hash][pipe]
-    cudaGraphExec_t g_exec[2][2][2] = {};
+    // one instantiated graph per [batch][hash][pipe][search waves - 1]
+    cudaGraphExec_t g_exec[2][2][2][2] = {};
     std::map<uint64_t, awpm::TuneEntry> tune;  // autotuner state per problem class
     awpm::Pending pend;
     // the request server of this context (awpm_submit), created on first use

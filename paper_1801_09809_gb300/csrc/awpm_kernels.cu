@@ -112,20 +112,23 @@ __device__ double block_sum_f64(double v)
     return v;
 }
 
-// Bits of row r in a column signature, a 64-bit Bloom filter of the
-// column's rows with AWPM_SIG_HASHES bit positions per row, all taken from
-// one multiplicative hash (bits 26..31, then 20..25).  A row whose bits are
-// not all set in the signature is not stored in the column.
-#ifndef AWPM_SIG_HASHES
-#define AWPM_SIG_HASHES 2
-#endif
+// Column signatures: a partitioned Bloom filter of the column's rows in 64
+// bits, one bit per row in each 32-bit half, both positions taken from one
+// multiplicative hash of the row (bits 27..31 select the bit of the low
+// half, bits 22..26 that of the high half).  A row with either bit clear is
+// not stored in the column.  With 32-bit halves the test needs no 64-bit
+// shifts.
 __device__ __forceinline__ unsigned long long sig_mask(int32_t r)
 {
     const uint32_t h = (uint32_t)r * 0x9E3779B1u;
-    unsigned long long m = 1ull << (h >> 26);
-    if (AWPM_SIG_HASHES > 1)
-        m |= 1ull << ((h >> 20) & 63u);
-    return m;
+    return ((unsigned long long)(1u << ((h >> 22) & 31u)) << 32) | (1u << (h >> 27));
+}
+
+__device__ __forceinline__ bool sig_has(unsigned long long sig, int32_t r)
+{
+    const uint32_t h = (uint32_t)r * 0x9E3779B1u;
+    return (((uint32_t)sig >> (h >> 27)) & ((uint32_t)(sig >> 32) >> ((h >> 22) & 31u)) & 1u) !=
+           0u;
 }
 
 // Column of the lane's nonzero: c0 (column of the tile's first nonzero) plus
@@ -474,12 +477,20 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
                 }
             }
             unsigned long long v = (valid && in_range) ? sig_mask(r[u]) : 0ull;
+            if (mask[u] <= 1u) {
+                // the whole tile lies in one column: one warp-wide OR
+                const unsigned lo = __reduce_or_sync(FULL_MASK, (unsigned)v);
+                const unsigned hi = __reduce_or_sync(FULL_MASK, (unsigned)(v >> 32));
+                v = ((unsigned long long)hi << 32) | lo;
+            } else {
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const unsigned long long ov = __shfl_down_sync(FULL_MASK, v, off);
-                // lane + off is in the same column: no column starts in between
-                if (lane + off < 32 && ((mask[u] >> (lane + 1)) & ((1u << off) - 1u)) == 0u)
-                    v |= ov;
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned long long ov = __shfl_down_sync(FULL_MASK, v, off);
+                    // lane + off is in the same column: no column starts in between
+                    if (lane + off < 32 &&
+                        ((mask[u] >> (lane + 1)) & ((1u << off) - 1u)) == 0u)
+                        v |= ov;
+                }
             }
             const bool head = valid && (lane == 0 || ((mask[u] >> lane) & 1u));
             if (head && j[u] < n) {
@@ -497,32 +508,59 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
 
 // mc = mate_in, mr = its inverse, and the row record and matched weight of
 // every row; checks that mate_in is a permutation over stored entries (the
-// entry pass left wm[j] = NaN where (mate_in[j], j) is not stored).
+// entry pass left wm[j] = NaN where (mate_in[j], j) is not stored).  Each
+// thread takes four columns per round and issues their loads together: the
+// scattered writes by row and the inverse's compare-and-swap are latency
+// bound, so the rounds overlap four of them.
 __global__ void k_init_mates(const Work *__restrict__ W)
 {
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    for (int64_t j = gtid(); j < w.n; j += gstride()) {
-        const int32_t r = w.mate_in[j];
-        w.mc[j] = r;
-        if (r < 0 || r >= w.n) {
-            raise_err(w.ctl, kErrNotPerfect);
-            continue;
+    constexpr int kU = 4;
+    const int64_t stride = gstride();
+    const int32_t n = w.n;
+    for (int64_t j0 = gtid(); j0 < n; j0 += kU * stride) {
+        int32_t r[kU], s[kU], e[kU], old[kU];
+        double x[kU];
+        unsigned long long sig[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t j = j0 + u * stride;
+            const bool ok = j < n;
+            r[u] = ok ? w.mate_in[j] : 0;
+            x[u] = ok ? w.wm[j] : 0.0;
+            s[u] = ok ? w.colptr[j] : 0;
+            e[u] = ok ? w.colptr[j + 1] : 0;
+            sig[u] = ok ? w.colsig[j] : 0ull;
         }
-        if (atomicCAS(&w.mr[r], -1, (int32_t)j) != -1)
-            raise_err(w.ctl, kErrNotPerfect);
-        const double x = w.wm[j];
-        if (gbits(x) == (long long)kNaNBits) {
-            raise_err(w.ctl, kErrNotPerfect);
-            continue;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t j = j0 + u * stride;
+            old[u] = -1;
+            if (j >= n)
+                continue;
+            w.mc[j] = r[u];
+            if (r[u] < 0 || r[u] >= n) {
+                raise_err(w.ctl, kErrNotPerfect);
+                continue;
+            }
+            old[u] = atomicCAS(&w.mr[r[u]], -1, (int32_t)j);
+            if (gbits(x[u]) == (long long)kNaNBits) {
+                raise_err(w.ctl, kErrNotPerfect);
+                continue;
+            }
+            RowRec rec;
+            rec.s = s[u];
+            rec.e = e[u];
+            rec.sig = sig[u];
+            w.rr[r[u]] = rec;
+            w.wmr[r[u]] = x[u];
         }
-        RowRec rec;
-        rec.s = w.colptr[j];
-        rec.e = w.colptr[j + 1];
-        rec.sig = w.colsig[j];
-        w.rr[r] = rec;
-        w.wmr[r] = x;
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (old[u] != -1)
+                raise_err(w.ctl, kErrNotPerfect);
     }
 }
 
@@ -712,7 +750,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = gstride() >> 5;
     const unsigned long long pol = policy_evict_last();
-    unsigned long long n_cand = 0, n_found = 0, n_pos = 0;
+    // per-thread counts fit 32 bits (one nonzero per tile a warp visits)
+    uint32_t n_cand = 0, n_found = 0, n_pos = 0;
 
     // kPipe: the next tile's first column, start bits and row indices are
     // loaded while the current tile is processed, so the latency of the
@@ -771,8 +810,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
             ++n_cand;
             rec = ld_rowrec(rr + i, pol);
         }
-        const unsigned long long smj = sig_mask(mj);
-        const bool pass = cand && (rec.sig & smj) == smj;
+        const bool pass = cand && sig_has(rec.sig, mj);
         int32_t lo = rec.s;
         int32_t len = pass ? rec.e - rec.s : 0;
         if (kLookup == AWPM_LOOKUP_BSEARCH && bloom && len > kBloomMin) {
@@ -883,9 +921,9 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
             atomicOr(winbits + (j >> 5), 1u << (j & 31));
         }
     }
-    block_add_u64(n_cand, &ctl->candidates);
-    block_add_u64(n_found, &ctl->found);
-    block_add_u64(n_pos, &ctl->positive);
+    block_add_u64((unsigned long long)n_cand, &ctl->candidates);
+    block_add_u64((unsigned long long)n_found, &ctl->found);
+    block_add_u64((unsigned long long)n_pos, &ctl->positive);
 }
 
 // ---------------------------------------------------------------------------
@@ -1213,11 +1251,18 @@ bool default_search_pipe()
 
 void launch_search(const Work *d, const Shape &sh, Sink &k)
 {
-    const unsigned grid = (unsigned)(sh.num_sms * (sh.search_bps > 0 ? sh.search_bps : 1));
+    const unsigned grid = (unsigned)(sh.num_sms * (sh.search_bps > 0 ? sh.search_bps : 1) *
+                                     (sh.search_waves > 1 ? sh.search_waves : 1));
     void *a[] = {(void *)&d};
     const void *f = sh.pipe ? search_fn<true>(sh.lookup, sh.batch)
                             : search_fn<false>(sh.lookup, sh.batch);
     k.launch(f, grid, kThreads, a);
+}
+
+int search_waves(int num_sms, int search_bps, int32_t ntiles)
+{
+    const int64_t warps = (int64_t)num_sms * (search_bps > 0 ? search_bps : 1) * (kThreads / 32);
+    return (int64_t)ntiles >= 64 * warps ? 2 : 1;
 }
 
 void launch_select_and_flip(const Work *d, const Shape &sh, Sink &k)

@@ -183,6 +183,7 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     sh.search_bps = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, false, sh.pipe);
     sh.lookup = AWPM_LOOKUP_BSEARCH;
     sh.batch = false;
+    sh.search_waves = search_waves(num_sms, sh.search_bps, wk.ntiles);
     Sink k;
     k.stream = s;
     launch_init(d, sh, k);

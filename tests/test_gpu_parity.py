@@ -223,12 +223,34 @@ def test_skewed_columns(ctx, orc, torch):
     check(ctx, orc, gen.from_dense(W, S, p), torch, what="dense row+col, ties")
 
 
+def test_long_columns_bloom(ctx, orc, torch):
+    """Columns longer than 32 rows carry Bloom filters in front of the binary
+    search: long columns next to each other (filter words shared at their
+    boundaries), closing entries mostly absent (sparse) or mostly present
+    (dense, integer weights with ties)."""
+    rng = np.random.default_rng(171)
+    n = 6000
+    deg = np.where(rng.random(n) < 0.5, rng.integers(33, 400, size=n), rng.integers(1, 9, size=n))
+    rows = [rng.choice(n, size=int(d), replace=False) for d in deg]
+    cols = [np.full(int(d), c) for c, d in enumerate(deg)]
+    mate = rng.permutation(n)
+    rows.append(mate)
+    cols.append(np.arange(n))
+    colptr, rowidx = gen._csc_from_coo(n, np.concatenate(rows), np.concatenate(cols))
+    w = gen.log_weights_lognormal(colptr, rng)
+    g = gen.Graph(n, colptr, rowidx, w, mate.astype(np.int32), "long_columns")
+    assert np.mean(np.diff(g.colptr) > 32) > 0.4
+    check(ctx, orc, g, torch)
+    check(ctx, orc, gen.random_small(400, 0.3, 172, integer_weights=True), torch,
+          what="dense, integer ties")
+
+
 @pytest.mark.parametrize("kind,expect", [
     ("dup_mate", "NOT_PERFECT"), ("mate_out_of_range", "NOT_PERFECT"),
     ("mate_not_stored", "NOT_PERFECT"), ("inf_weight", "NONFINITE"), ("nan_weight", "NONFINITE"),
     ("row_out_of_range", "INVALID_ARG"), ("bad_colptr", "INVALID_ARG"),
     ("unsorted", "UNSORTED_OR_DUP"), ("duplicate_row", "UNSORTED_OR_DUP"),
-    ("unsorted_and_nonfinite", "UNSORTED_OR_DUP"),
+    ("unsorted_and_nonfinite", "UNSORTED_OR_DUP"), ("empty_column", "NOT_PERFECT"),
 ])
 def test_validation_errors(ctx, orc, torch, kind, expect):
     g = gen.random_small(30, 0.3, 101)
@@ -262,6 +284,13 @@ def test_validation_errors(ctx, orc, torch, kind, expect):
     elif kind == "unsorted_and_nonfinite":
         b.rowidx[a0], b.rowidx[a0 + 1] = g.rowidx[a0 + 1], g.rowidx[a0]
         b.weight[0] = np.nan
+    elif kind == "empty_column":
+        c = 11
+        s0, e0 = int(g.colptr[c]), int(g.colptr[c + 1])
+        b.rowidx = np.delete(g.rowidx, np.arange(s0, e0))
+        b.weight = np.delete(g.weight, np.arange(s0, e0))
+        b.colptr = g.colptr.copy()
+        b.colptr[c + 1:] -= e0 - s0
     assert orc.validate(b) == expect
     for host in (False, True):
         with pytest.raises(awpm.AwpmError) as ei:
