@@ -708,23 +708,131 @@ __global__ void k_batch_wsum(const Work *__restrict__ W, int out)
 // Steps A + B + C (Algorithms 3, 4, 5): fused edge-parallel cycle search
 // ---------------------------------------------------------------------------
 
+// Closing-entry lookups of one warp, queued across tiles (a ring of 64
+// entries, struct of arrays in shared memory): a lane whose candidate passed
+// the signature test leaves its request here, and the warp resolves 32
+// requests at a time, one per lane, instead of searching with the one or two
+// lanes of a tile that need it.
+constexpr int kQueue = 64;
+struct LookupQueue {
+    int32_t j[kQueue];    // root column
+    int32_t p[kQueue];    // position of (i, j)
+    int32_t i[kQueue];    // row i
+    int32_t mj[kQueue];   // m_j, the row looked up in column m_i
+    int32_t lo[kQueue];   // column m_i's rows: rowidx[lo, lo + len)
+    int32_t len[kQueue];
+};
+
+// Resolve the queued requests head .. head + k - 1 (k <= 32, lane x takes
+// request head + x): Bloom probe for long columns, then the column search
+// (per lane up to kCoopMin rows, warp-cooperative above) or the hash probe;
+// a closing entry found gives the gain in the fixed order
+// ((w_ij + w_q) - w(i, m_i)) - w(m_j, j), and a positive gain goes into the
+// root's Step-C record (maximum gain, then lowest position; Algorithm 5).
+// Called by the whole warp.
+template <int kLookup>
+__device__ __forceinline__ void resolve_lookups(
+    const LookupQueue &qu, int head, int k, int lane, const int32_t *__restrict__ rowidx,
+    const double *__restrict__ wv, const double *__restrict__ wm, const double *__restrict__ wmr,
+    const unsigned long long *__restrict__ htab, const uint32_t *__restrict__ bloom,
+    Rec *__restrict__ best, uint32_t *winbits, Ctl *ctl, uint32_t &n_found, uint32_t &n_pos)
+{
+    const int x = (head + lane) & (kQueue - 1);
+    const bool act = lane < k;
+    const int32_t mj = act ? qu.mj[x] : 0;
+    int32_t lo = act ? qu.lo[x] : 0;
+    int32_t len = act ? qu.len[x] : 0;
+    int32_t q = -1;
+    if (kLookup == AWPM_LOOKUP_HASH) {
+        const int32_t hbase = 2 * lo;
+        const int32_t hsize = 2 * len;
+        int32_t pos = hsize > 0 ? slot_start(mj, hbase, hsize) : 0;
+        for (int32_t left = hsize; left > 0; --left) {
+            const unsigned long long v = __ldg(htab + pos);
+            if ((int32_t)(uint32_t)v == mj) {
+                q = (int32_t)(v >> 32);
+                break;
+            }
+            if (v == kSlotEmpty)
+                break;
+            if (++pos == hbase + hsize)
+                pos = hbase;
+        }
+    } else {
+        if (bloom && len > kBloomMin) {
+            // long column: its Bloom filter rules most absent rows out first
+            uint32_t word, b;
+            bloom_key(mj, lo, lo + len, word, b);
+            if ((__ldg(bloom + word) & b) != b)
+                len = 0;
+        }
+        // long columns: the warp searches them together, one request at a time
+        unsigned longm = __ballot_sync(FULL_MASK, len > kCoopMin);
+        while (longm) {
+            const int src = __ffs(longm) - 1;
+            longm &= longm - 1;
+            const int32_t ss = __shfl_sync(FULL_MASK, lo, src);
+            const int32_t sl = __shfl_sync(FULL_MASK, len, src);
+            const int32_t sk = __shfl_sync(FULL_MASK, mj, src);
+            const int32_t f = coop_find(rowidx, ss, sl, sk, lane);
+            if (lane == src) {
+                q = f;
+                len = 0;
+            }
+        }
+        // short columns: binary search per lane (early exit on a hit)
+        while (len > 0) {
+            const int32_t half = len >> 1;
+            const int32_t mid = lo + half;
+            const int32_t v = __ldg(rowidx + mid);
+            if (v == mj) {
+                q = mid;
+                break;
+            }
+            if (v < mj) {
+                lo = mid + 1;
+                len -= half + 1;
+            } else {
+                len = half;
+            }
+        }
+    }
+    if (q >= 0) {
+        ++n_found;
+        const int32_t j = qu.j[x];
+        const int32_t p = qu.p[x];
+        const int32_t i = qu.i[x];
+        const double wij = __ldg(wv + p);
+        const double wq = __ldg(wv + q);
+        const double wmi = __ldg(wmr + i);
+        const double gg = ((wij + wq) - wmi) - __ldg(wm + j);
+        if (gain_positive(gg)) {
+            ++n_pos;
+            Rec r;
+            r.g = gg;
+            r.p = p;
+            r.q = q;
+            rec_combine(best + j, r, ctl);
+            atomicOr(winbits + (j >> 5), 1u << (j & 31));
+        }
+    }
+}
+
 // One warp per tile of kTile consecutive nonzeros (lane = one nonzero).
 // The lane's column comes from the tile's first column and its word of the
 // column-start bitmap (one popcount).  Lane with nonzero p = (i, j): if
 // i > m_j it is an A-request (Algorithm 3); the closing entry (m_j, m_i) is
 // looked up in column m_i (Algorithm 4): the row record of i gives that
 // column's range and signature, so a clear signature bit settles "absent" at
-// once; otherwise the column is searched (binary search, warp-cooperative for
-// long columns, or the column's hash table).  The gain is evaluated in the
-// fixed order ((w_ij + w_q) - w(i,m_i)) - w(m_j,j).  Per column the warp
-// keeps the maximum positive gain with the lowest row (Algorithm 5); columns
-// cut by a tile boundary are merged across warps by a 128-bit
-// compare-and-swap.  `best` must be zero on entry: only positive records are
+// once; otherwise the request is queued and resolved with 31 others (see
+// resolve_lookups).  Step-C records (Algorithm 5) are combined by a 128-bit
+// compare-and-swap; `best` must be zero on entry: only positive records are
 // written.  In a batched solve, tiles of finished matrices are skipped.
 template <int kLookup, bool kBatch, bool kPipe>
 __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__ W)
 {
     __shared__ int s_go;
+    __shared__ LookupQueue s_queue[kThreads / 32];
     if (threadIdx.x == 0)
         s_go = gate(W->ctl) ? 1 : 0;
     __syncthreads();
@@ -746,12 +854,15 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
     const int32_t *__restrict__ tilemat = W->bw.tilemat;
     const int32_t *__restrict__ colmat = W->bw.colmat;
     const int32_t *__restrict__ mdone = W->bw.mdone;
+    LookupQueue &qu = s_queue[threadIdx.x >> 5];
 
     const int lane = threadIdx.x & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
     const int64_t nwarps = gstride() >> 5;
     const unsigned long long pol = policy_evict_last();
     // per-thread counts fit 32 bits (one nonzero per tile a warp visits)
     uint32_t n_cand = 0, n_found = 0, n_pos = 0;
+    int qhead = 0, qn = 0;  // the warp's queue (warp-uniform)
 
     // kPipe: the next tile's first column, start bits and row indices are
     // loaded while the current tile is processed, so the latency of the
@@ -765,161 +876,78 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
         const int32_t pp = (int32_t)(t * kTile) + lane;
         pf_i = pp < nnz ? __ldcs(rowidx + pp) : 0;
     }
-    for (; t < ntiles; t += nwarps) {
-        const int32_t base = (int32_t)(t * kTile);
-        const int32_t p = base + lane;
-        bool valid = p < nnz;
-        bool mixed = false;
-        int32_t c0, i_now = 0;
-        uint32_t mask;
-        if (kPipe) {
-            c0 = pf_c0;
-            mask = pf_mask;
-            i_now = pf_i;
-            const int64_t tn = t + nwarps;
-            if (tn < ntiles) {
-                pf_c0 = __ldg(tile_col + tn);
-                pf_mask = __ldg(starts + tn);
-                const int32_t pn = (int32_t)(tn * kTile) + lane;
-                pf_i = pn < nnz ? __ldcs(rowidx + pn) : 0;
-            }
-        } else {
-            c0 = __ldg(tile_col + t);
-            mask = __ldg(starts + t);
-        }
-        if (kBatch) {
-            // a tile of one finished matrix has nothing left to do
-            const int32_t tm = __ldg(tilemat + t);
-            if (tm & kTileSingle) {
-                if (__ldg(mdone + (tm & ~kTileSingle)))
-                    valid = false;
+    for (;;) {
+        const bool more = t < ntiles;
+        if (more) {
+            const int32_t base = (int32_t)(t * kTile);
+            const int32_t p = base + lane;
+            bool valid = p < nnz;
+            bool mixed = false;
+            int32_t c0, i_now = 0;
+            uint32_t mask;
+            if (kPipe) {
+                c0 = pf_c0;
+                mask = pf_mask;
+                i_now = pf_i;
+                const int64_t tn = t + nwarps;
+                if (tn < ntiles) {
+                    pf_c0 = __ldg(tile_col + tn);
+                    pf_mask = __ldg(starts + tn);
+                    const int32_t pn = (int32_t)(tn * kTile) + lane;
+                    pf_i = pn < nnz ? __ldcs(rowidx + pn) : 0;
+                }
             } else {
-                mixed = true;
+                c0 = __ldg(tile_col + t);
+                mask = __ldg(starts + t);
             }
-        }
-        const int32_t i = valid ? (kPipe ? i_now : __ldcs(rowidx + p)) : 0;
-        const int32_t j = valid ? lane_column(c0, mask, lane) : -1 - lane;
-        RowRec rec;
-        rec.s = rec.e = 0;
-        rec.sig = 0ull;
-        int32_t mj = valid ? ld_i32_last(mc + j, pol) : 0x7fffffff;
-        if (kBatch && mixed && valid && __ldg(mdone + __ldg(colmat + j)))
-            mj = 0x7fffffff;  // finished matrix: no candidate
-        const bool cand = valid && i > mj;
-        if (cand) {
-            ++n_cand;
-            rec = ld_rowrec(rr + i, pol);
-        }
-        const bool pass = cand && sig_has(rec.sig, mj);
-        int32_t lo = rec.s;
-        int32_t len = pass ? rec.e - rec.s : 0;
-        if (kLookup == AWPM_LOOKUP_BSEARCH && bloom && len > kBloomMin) {
-            // long column: its Bloom filter rules most absent rows out first
-            uint32_t word, b;
-            bloom_key(mj, lo, lo + len, word, b);
-            if ((__ldg(bloom + word) & b) != b)
-                len = 0;
-        }
-        int32_t q = -1;
-        const double wmi = pass ? __ldg(wmr + i) : 0.0;
-        if (kLookup == AWPM_LOOKUP_HASH) {
-            const int32_t hbase = 2 * lo;
-            const int32_t hsize = 2 * len;
-            int32_t pos = hsize > 0 ? slot_start(mj, hbase, hsize) : 0;
-            for (int32_t left = hsize; left > 0; --left) {
-                const unsigned long long v = __ldg(htab + pos);
-                if ((int32_t)(uint32_t)v == mj) {
-                    q = (int32_t)(v >> 32);
-                    break;
-                }
-                if (v == kSlotEmpty)
-                    break;
-                if (++pos == hbase + hsize)
-                    pos = hbase;
-            }
-        } else {
-            // long columns, or every column when few lanes need a search:
-            // the warp searches them together, one request at a time (a
-            // column of up to 32 rows is one coalesced read and a ballot)
-            unsigned longm = __ballot_sync(FULL_MASK, len > kCoopMin);
-            const unsigned need = __ballot_sync(FULL_MASK, len > 0);
-            if (__popc(need) <= kCoopFew)
-                longm = need;
-            while (longm) {
-                const int src = __ffs(longm) - 1;
-                longm &= longm - 1;
-                const int32_t ss = __shfl_sync(FULL_MASK, lo, src);
-                const int32_t sl = __shfl_sync(FULL_MASK, len, src);
-                const int32_t sk = __shfl_sync(FULL_MASK, mj, src);
-                const int32_t f = coop_find(rowidx, ss, sl, sk, lane);
-                if (lane == src) {
-                    q = f;
-                    len = 0;
-                }
-            }
-            // short columns: binary search per lane (early exit on a hit)
-            while (len > 0) {
-                const int32_t half = len >> 1;
-                const int32_t mid = lo + half;
-                const int32_t v = __ldg(rowidx + mid);
-                if (v == mj) {
-                    q = mid;
-                    break;
-                }
-                if (v < mj) {
-                    lo = mid + 1;
-                    len -= half + 1;
+            if (kBatch) {
+                // a tile of one finished matrix has nothing left to do
+                const int32_t tm = __ldg(tilemat + t);
+                if (tm & kTileSingle) {
+                    if (__ldg(mdone + (tm & ~kTileSingle)))
+                        valid = false;
                 } else {
-                    len = half;
+                    mixed = true;
                 }
             }
-        }
-        // the gain in FP64; from here on it is handled as its bit pattern gb
-        // (0 = no positive cycle), and q >= 0 marks a lane with one
-        long long gb = 0;
-        if (q >= 0) {
-            ++n_found;
-            const double wij = __ldcs(wv + p);
-            const double wq = __ldg(wv + q);
-            const double gg = ((wij + wq) - wmi) - __ldg(wm + j);
-            if (gain_positive(gg)) {
-                ++n_pos;
-                gb = gbits(gg);
-            } else {
-                q = -1;
+            const int32_t i = valid ? (kPipe ? i_now : __ldcs(rowidx + p)) : 0;
+            const int32_t j = valid ? lane_column(c0, mask, lane) : -1 - lane;
+            int32_t mj = valid ? ld_i32_last(mc + j, pol) : 0x7fffffff;
+            if (kBatch && mixed && valid && __ldg(mdone + __ldg(colmat + j)))
+                mj = 0x7fffffff;  // finished matrix: no candidate
+            const bool cand = valid && i > mj;
+            RowRec rec;
+            rec.s = rec.e = 0;
+            rec.sig = 0ull;
+            if (cand) {
+                ++n_cand;
+                rec = ld_rowrec(rr + i, pol);
             }
-        }
-        if (!__any_sync(FULL_MASK, q >= 0))
-            continue;
-        // segmented arg-max over lanes of the same column (suffix direction);
-        // lanes lane and lane + off share a column when no column starts in
-        // between
-        int32_t bp = valid ? p : 0x7fffffff;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const long long og = __shfl_down_sync(FULL_MASK, gb, off);
-            const int32_t op = __shfl_down_sync(FULL_MASK, bp, off);
-            const int32_t oq = __shfl_down_sync(FULL_MASK, q, off);
-            const bool same =
-                lane + off < 32 && ((mask >> (lane + 1)) & ((1u << off) - 1u)) == 0u;
-            if (same && oq >= 0 && (og > gb || (og == gb && op < bp))) {
-                gb = og;
-                bp = op;
-                q = oq;
+            const bool pass = cand && sig_has(rec.sig, mj);
+            const unsigned need = __ballot_sync(FULL_MASK, pass);
+            if (pass) {
+                const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
+                qu.j[x] = j;
+                qu.p[x] = p;
+                qu.i[x] = i;
+                qu.mj[x] = mj;
+                qu.lo[x] = rec.s;
+                qu.len[x] = rec.e - rec.s;
             }
+            qn += __popc(need);
+            t += nwarps;
         }
-        const bool head = valid && (lane == 0 || ((mask >> lane) & 1u));
-        if (head && q >= 0) {
-            Rec r;
-            r.g = __longlong_as_double(gb);
-            r.p = bp;
-            r.q = q;
-            if (segment_complete(mask, lane, base, nnz, starts, t))
-                best[j] = r;
-            else
-                rec_combine(best + j, r, ctl);
-            atomicOr(winbits + (j >> 5), 1u << (j & 31));
+        if (qn >= 32 || (!more && qn > 0)) {
+            __syncwarp();
+            const int k = qn < 32 ? qn : 32;
+            resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, wmr, htab, bloom, best,
+                                     winbits, ctl, n_found, n_pos);
+            __syncwarp();
+            qhead = (qhead + k) & (kQueue - 1);
+            qn -= k;
         }
+        if (!more && qn == 0)
+            break;
     }
     block_add_u64((unsigned long long)n_cand, &ctl->candidates);
     block_add_u64((unsigned long long)n_found, &ctl->found);
