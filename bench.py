@@ -90,7 +90,7 @@ def search_kernel_hash():
     """sha256 (16 hex digits) of the search kernel's source text, from its
     template line to the Step D section."""
     text = open(KERNEL_SRC).read()
-    a = text.index("template <int kLookup, bool kBatch, bool kPipe>")
+    a = text.index("template <int kLookup, bool kBatch, bool kPair>")
     b = text.index("// Step D (Algorithm 6)")
     return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 

@@ -828,7 +828,7 @@ __device__ __forceinline__ void resolve_lookups(
 // resolve_lookups).  Step-C records (Algorithm 5) are combined by a 128-bit
 // compare-and-swap; `best` must be zero on entry: only positive records are
 // written.  In a batched solve, tiles of finished matrices are skipped.
-template <int kLookup, bool kBatch, bool kPipe>
+template <int kLookup, bool kBatch, bool kPair>
 __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__ W)
 {
     __shared__ int s_go;
@@ -864,89 +864,112 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
     uint32_t n_cand = 0, n_found = 0, n_pos = 0;
     int qhead = 0, qn = 0;  // the warp's queue (warp-uniform)
 
-    // kPipe: the next tile's first column, start bits and row indices are
-    // loaded while the current tile is processed, so the latency of the
-    // streamed row indices overlaps the current tile's gathers
+    auto flush = [&](int k) {
+        __syncwarp();
+        resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, wmr, htab, bloom, best,
+                                 winbits, ctl, n_found, n_pos);
+        __syncwarp();
+        qhead = (qhead + k) & (kQueue - 1);
+        qn -= k;
+    };
+    // Each round a warp takes kU tiles (t, t + nwarps, ...) and issues their
+    // loads side by side, so the dependent chains (m_j, then the row record)
+    // of the kU tiles overlap; the tiles of the next round have their first
+    // column, start bits and row indices loaded (prefetched) meanwhile.
+    constexpr int kU = kPair ? 2 : 1;
     int64_t t = s_go ? (gtid() >> 5) : (int64_t)ntiles;
-    int32_t pf_c0 = 0, pf_i = 0;
-    uint32_t pf_mask = 0u;
-    if (kPipe && t < ntiles) {
-        pf_c0 = __ldg(tile_col + t);
-        pf_mask = __ldg(starts + t);
-        const int32_t pp = (int32_t)(t * kTile) + lane;
-        pf_i = pp < nnz ? __ldcs(rowidx + pp) : 0;
+    int32_t pf_c0[kU], pf_i[kU];
+    uint32_t pf_mask[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        const int64_t tu = t + u * nwarps;
+        pf_c0[u] = 0;
+        pf_i[u] = 0;
+        pf_mask[u] = 1u;
+        if (tu < ntiles) {
+            pf_c0[u] = __ldg(tile_col + tu);
+            pf_mask[u] = __ldg(starts + tu);
+            const int32_t pp = (int32_t)(tu * kTile) + lane;
+            pf_i[u] = pp < nnz ? __ldcs(rowidx + pp) : 0;
+        }
     }
     for (;;) {
         const bool more = t < ntiles;
         if (more) {
-            const int32_t base = (int32_t)(t * kTile);
-            const int32_t p = base + lane;
-            bool valid = p < nnz;
-            bool mixed = false;
-            int32_t c0, i_now = 0;
-            uint32_t mask;
-            if (kPipe) {
-                c0 = pf_c0;
-                mask = pf_mask;
-                i_now = pf_i;
-                const int64_t tn = t + nwarps;
+            int32_t c0[kU], iv[kU], jv[kU], mjv[kU], pv[kU];
+            uint32_t mask[kU];
+            bool valid[kU], mixed[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t tu = t + u * nwarps;
+                pv[u] = (int32_t)(tu * kTile) + lane;
+                valid[u] = tu < ntiles && pv[u] < nnz;
+                mixed[u] = false;
+                c0[u] = pf_c0[u];
+                mask[u] = pf_mask[u];
+                iv[u] = pf_i[u];
+                if (kBatch && tu < ntiles) {
+                    const int32_t tm = __ldg(tilemat + tu);
+                    if (tm & kTileSingle) {
+                        if (__ldg(mdone + (tm & ~kTileSingle)))
+                            valid[u] = false;
+                    } else {
+                        mixed[u] = true;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t tn = t + (kU + u) * nwarps;
                 if (tn < ntiles) {
-                    pf_c0 = __ldg(tile_col + tn);
-                    pf_mask = __ldg(starts + tn);
+                    pf_c0[u] = __ldg(tile_col + tn);
+                    pf_mask[u] = __ldg(starts + tn);
                     const int32_t pn = (int32_t)(tn * kTile) + lane;
-                    pf_i = pn < nnz ? __ldcs(rowidx + pn) : 0;
-                }
-            } else {
-                c0 = __ldg(tile_col + t);
-                mask = __ldg(starts + t);
-            }
-            if (kBatch) {
-                // a tile of one finished matrix has nothing left to do
-                const int32_t tm = __ldg(tilemat + t);
-                if (tm & kTileSingle) {
-                    if (__ldg(mdone + (tm & ~kTileSingle)))
-                        valid = false;
-                } else {
-                    mixed = true;
+                    pf_i[u] = pn < nnz ? __ldcs(rowidx + pn) : 0;
                 }
             }
-            const int32_t i = valid ? (kPipe ? i_now : __ldcs(rowidx + p)) : 0;
-            const int32_t j = valid ? lane_column(c0, mask, lane) : -1 - lane;
-            int32_t mj = valid ? ld_i32_last(mc + j, pol) : 0x7fffffff;
-            if (kBatch && mixed && valid && __ldg(mdone + __ldg(colmat + j)))
-                mj = 0x7fffffff;  // finished matrix: no candidate
-            const bool cand = valid && i > mj;
-            RowRec rec;
-            rec.s = rec.e = 0;
-            rec.sig = 0ull;
-            if (cand) {
-                ++n_cand;
-                rec = ld_rowrec(rr + i, pol);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                iv[u] = valid[u] ? iv[u] : 0;
+                jv[u] = valid[u] ? lane_column(c0[u], mask[u], lane) : -1 - lane;
+                mjv[u] = valid[u] ? ld_i32_last(mc + jv[u], pol) : 0x7fffffff;
             }
-            const bool pass = cand && sig_has(rec.sig, mj);
-            const unsigned need = __ballot_sync(FULL_MASK, pass);
-            if (pass) {
-                const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
-                qu.j[x] = j;
-                qu.p[x] = p;
-                qu.i[x] = i;
-                qu.mj[x] = mj;
-                qu.lo[x] = rec.s;
-                qu.len[x] = rec.e - rec.s;
+            RowRec rec[kU];
+            bool cand[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                if (kBatch && mixed[u] && valid[u] && __ldg(mdone + __ldg(colmat + jv[u])))
+                    mjv[u] = 0x7fffffff;  // finished matrix: no candidate
+                cand[u] = valid[u] && iv[u] > mjv[u];
+                rec[u].s = rec[u].e = 0;
+                rec[u].sig = 0ull;
+                if (cand[u]) {
+                    ++n_cand;
+                    rec[u] = ld_rowrec(rr + iv[u], pol);
+                }
             }
-            qn += __popc(need);
-            t += nwarps;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const bool pass = cand[u] && sig_has(rec[u].sig, mjv[u]);
+                const unsigned need = __ballot_sync(FULL_MASK, pass);
+                if (pass) {
+                    const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
+                    qu.j[x] = jv[u];
+                    qu.p[x] = pv[u];
+                    qu.i[x] = iv[u];
+                    qu.mj[x] = mjv[u];
+                    qu.lo[x] = rec[u].s;
+                    qu.len[x] = rec[u].e - rec[u].s;
+                }
+                qn += __popc(need);
+                if (qn >= 32)
+                    flush(32);
+            }
+            t += kU * nwarps;
         }
-        if (qn >= 32 || (!more && qn > 0)) {
-            __syncwarp();
-            const int k = qn < 32 ? qn : 32;
-            resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, wmr, htab, bloom, best,
-                                     winbits, ctl, n_found, n_pos);
-            __syncwarp();
-            qhead = (qhead + k) & (kQueue - 1);
-            qn -= k;
-        }
-        if (!more && qn == 0)
+        if (!more && qn > 0)
+            flush(qn);
+        if (!more)
             break;
     }
     block_add_u64((unsigned long long)n_cand, &ctl->candidates);
@@ -1231,11 +1254,11 @@ void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k)
         k.launch((const void *)k_batch_wsum, util_grid(sh), kThreads, ao);
 }
 
-template <int kLookup, bool kBatch, bool kPipe>
+template <int kLookup, bool kBatch, bool kPair>
 static int bps_of()
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<kLookup, kBatch, kPipe>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<kLookup, kBatch, kPair>,
                                                       kThreads, 0) != cudaSuccess) {
         cudaGetLastError();
         b = 1;
@@ -1243,19 +1266,19 @@ static int bps_of()
     return b < 1 ? 1 : b;
 }
 
-template <bool kPipe>
+template <bool kPair>
 static const void *search_fn(int lookup, bool batch)
 {
     if (lookup == AWPM_LOOKUP_HASH)
-        return batch ? (const void *)k_search<AWPM_LOOKUP_HASH, true, kPipe>
-                     : (const void *)k_search<AWPM_LOOKUP_HASH, false, kPipe>;
-    return batch ? (const void *)k_search<AWPM_LOOKUP_BSEARCH, true, kPipe>
-                 : (const void *)k_search<AWPM_LOOKUP_BSEARCH, false, kPipe>;
+        return batch ? (const void *)k_search<AWPM_LOOKUP_HASH, true, kPair>
+                     : (const void *)k_search<AWPM_LOOKUP_HASH, false, kPair>;
+    return batch ? (const void *)k_search<AWPM_LOOKUP_BSEARCH, true, kPair>
+                 : (const void *)k_search<AWPM_LOOKUP_BSEARCH, false, kPair>;
 }
 
-int search_blocks_per_sm(int lookup, bool batch, bool pipe)
+int search_blocks_per_sm(int lookup, bool batch, bool pair)
 {
-    if (pipe) {
+    if (pair) {
         if (lookup == AWPM_LOOKUP_HASH)
             return batch ? bps_of<AWPM_LOOKUP_HASH, true, true>()
                          : bps_of<AWPM_LOOKUP_HASH, false, true>();
@@ -1269,9 +1292,9 @@ int search_blocks_per_sm(int lookup, bool batch, bool pipe)
                  : bps_of<AWPM_LOOKUP_BSEARCH, false, false>();
 }
 
-bool default_search_pipe()
+bool default_search_pair()
 {
-    const char *v = getenv("AWPM_SEARCH_PIPE");
+    const char *v = getenv("AWPM_SEARCH_PAIR");
     if (v && (v[0] == '0' || v[0] == '1') && v[1] == 0)
         return v[0] == '1';
     return true;
@@ -1282,7 +1305,7 @@ void launch_search(const Work *d, const Shape &sh, Sink &k)
     const unsigned grid = (unsigned)(sh.num_sms * (sh.search_bps > 0 ? sh.search_bps : 1) *
                                      (sh.search_waves > 1 ? sh.search_waves : 1));
     void *a[] = {(void *)&d};
-    const void *f = sh.pipe ? search_fn<true>(sh.lookup, sh.batch)
+    const void *f = sh.pair ? search_fn<true>(sh.lookup, sh.batch)
                             : search_fn<false>(sh.lookup, sh.batch);
     k.launch(f, grid, kThreads, a);
 }
