@@ -215,6 +215,45 @@ def pin_local_optimality_midsize(orc):
     opt = float(np.sum(np.asarray(A[r, c]).ravel())) - shift * g.n
     assert st["weight_out"] <= opt + 1e-9 * abs(opt)
     assert st["weight_out"] > st["weight_in"]
+    # the quality report: gap to the optimum for these (log, <= 0) weights,
+    # and the ratio w(M) / w(M*) for the positive weights exp(w) on the same
+    # pattern (Option A), where a ratio is meaningful
+    ga = g.copy()
+    ga.weight = np.exp(g.weight)
+    outa, sta, _ = orc.improve(ga)
+    B = csc_matrix((ga.weight, ga.rowidx, ga.colptr), shape=(g.n, g.n))
+    ra, ca = min_weight_full_bipartite_matching(B, maximize=True)
+    opta = float(np.sum(np.asarray(B[ra, ca]).ravel()))
+    ratio = sta["weight_out"] / opta
+    assert 0.0 < ratio <= 1.0 + 1e-12
+    print(f"\nquality n={g.n}: log weights gap {opt - st['weight_out']:.6g} "
+          f"(w {st['weight_out']:.6g}, optimum {opt:.6g}); exp weights ratio {ratio:.6f}")
+    return {"gap_log": opt - st["weight_out"], "ratio_exp": ratio}
+
+
+def pin_rank_simulation(orc):
+    """The paper's distributed pass simulated literally on virtual process
+    grids of 1, 4 and 9 processes (explicit A/B/C request queues, replicated
+    matching, broadcast flips; Section 5.3, Algorithms 2-6) gives the
+    oracle's matching after every pass, ties included."""
+    import rank_sim
+    for s in range(12):
+        n = 20 + 15 * s
+        g = gen.random_small(n, 0.06 + 0.01 * (s % 4), 4100 + s, integer_weights=(s % 3 == 0))
+        for side in (1, 2, 3):
+            grid = rank_sim.Grid(g, g.mate, side)
+            cur = g.mate.copy()
+            for it in range(200):
+                flips = grid.one_pass()
+                ref, _, counts = orc.one_pass(g, cur)
+                got = grid.matching()
+                assert got.tolist() == ref.tolist(), (s, side, it)
+                assert flips == counts[3], (s, side, it)
+                cur = ref
+                if flips == 0:
+                    break
+            out, st, _ = orc.improve(g)
+            assert cur.tolist() == out.tolist() and it + 1 == st["iterations"], (s, side)
 
 
 def pin_validation(orc):
@@ -275,5 +314,5 @@ def pin_paper_maxiters(orc):
 
 
 PINS = [pin_hand_cases, pin_2x2_closed_form, pin_block_diagonal, pin_six_cycle,
-        pin_bruteforce_small, pin_one_pass_bruteforce, pin_local_optimality_midsize,
-        pin_validation, pin_resume, pin_paper_maxiters]
+        pin_bruteforce_small, pin_one_pass_bruteforce, pin_rank_simulation,
+        pin_local_optimality_midsize, pin_validation, pin_resume, pin_paper_maxiters]
