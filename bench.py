@@ -90,7 +90,7 @@ def search_kernel_hash():
     """sha256 (16 hex digits) of the search kernel's source text, from its
     template line to the Step D section."""
     text = open(KERNEL_SRC).read()
-    a = text.index("template <int kLookup, bool kBatch, bool kPair>")
+    a = text.index("template <int kLookup, bool kBatch, bool kWide>")
     b = text.index("// Step D (Algorithm 6)")
     return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 
@@ -242,6 +242,25 @@ def cpu_baseline(g, desc_sample="one full solve of the same graph (oracle)"):
     dt = time.perf_counter() - t0
     return {"value": st["edge_checks"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{desc_sample}: {st['iterations']} passes, {dt:.1f} s, single thread"}
+
+
+def cpu_baseline_parallel(g):
+    """The multi-threaded restatement of the oracle (OpenMP, all host cores;
+    its results equal the oracle's), one full solve of the same graph: the
+    paper's shared-memory setting.  None when it cannot be built here."""
+    import oracle
+    try:
+        par = oracle.OraclePar()
+    except (OSError, subprocess.CalledProcessError):
+        return None
+    par.improve(g, max_iters=1)  # touch the pages once
+    t0 = time.perf_counter()
+    _, st = par.improve(g)
+    dt = time.perf_counter() - t0
+    return {"value": st["edge_checks"] / dt, "unit": UNIT, "cores": par.threads(),
+            "kind": "oracle, OpenMP restatement",
+            "sample": f"one full solve of the same graph: {st['iterations']} passes, "
+                      f"{dt:.2f} s, {par.threads()} threads"}
 
 
 def run_reference(args, rank, world):
@@ -567,6 +586,7 @@ def main():
         line["served"] = bench_served(awpm, torch, dev, args.serve_requests, args.serve_pool)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(g) if world == 1 else None
+        line["cpu_baseline_parallel"] = cpu_baseline_parallel(g) if world == 1 else None
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -37,6 +37,7 @@ def build(force: bool = False) -> str:
     return SO
 
 
+
 class _Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("cycles_applied", ctypes.c_int64), ("edge_checks", ctypes.c_int64),
@@ -163,3 +164,50 @@ def get() -> Oracle:
     if _default is None:
         _default = Oracle()
     return _default
+
+
+PAR_SRC = os.path.join(HERE, "awpm_oracle_par.c")
+PAR_SO = os.path.join(HERE, "_awpm_oracle_par.so")
+
+
+def build_par(force: bool = False) -> str:
+    """The multi-threaded restatement (OpenMP); raises if gcc cannot build it."""
+    if force or not os.path.exists(PAR_SO) or os.path.getmtime(PAR_SO) < os.path.getmtime(PAR_SRC):
+        tmp = PAR_SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, "-fopenmp", "-o", tmp, PAR_SRC, "-lm"])
+        os.replace(tmp, PAR_SO)
+    return PAR_SO
+
+
+class OraclePar:
+    """ctypes front end of the multi-threaded restatement: the CPU timing
+    baseline on all host cores; its results must equal the oracle's."""
+
+    def __init__(self, path: str | None = None):
+        self.lib = ctypes.CDLL(path or build_par())
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        self.lib.oracle_par_improve.restype = ctypes.c_int
+        self.lib.oracle_par_improve.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p, i32p,
+                                                ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.POINTER(_Stats)]
+        self.lib.oracle_par_threads.restype = ctypes.c_int
+        self.lib.oracle_par_threads.argtypes = []
+
+    def threads(self) -> int:
+        return int(self.lib.oracle_par_threads())
+
+    def improve(self, g, mate=None, max_iters: int = 0, threads: int = 0):
+        """(mate_out, stats dict) of the whole phase with `threads` threads
+        (0: all)."""
+        cp, ri, w = _arrs(g)
+        m = np.ascontiguousarray(g.mate if mate is None else mate, dtype=np.int32)
+        out = np.empty(max(g.n, 1), dtype=np.int32)
+        st = _Stats()
+        rc = self.lib.oracle_par_improve(g.n, _p(cp, ctypes.c_int32), _p(ri, ctypes.c_int32),
+                                         _p(w, ctypes.c_double), _p(m, ctypes.c_int32),
+                                         _p(out, ctypes.c_int32), max_iters, threads,
+                                         ctypes.byref(st))
+        if rc != 0:
+            raise OracleError(rc)
+        return out[:g.n], {k: getattr(st, k) for k, _ in _Stats._fields_}

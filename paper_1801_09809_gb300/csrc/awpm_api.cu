@@ -142,14 +142,14 @@ int check_sink(const Sink &k)
     return AWPM_OK;
 }
 
-Shape shape_of(const awpm_ctx *c, bool batch, int lookup, bool pair, int32_t ntiles)
+Shape shape_of(const awpm_ctx *c, bool batch, int lookup, bool wide, int32_t ntiles)
 {
     Shape sh;
     sh.num_sms = c->num_sms;
     sh.batch = batch;
     sh.lookup = lookup;
-    sh.pair = pair;
-    sh.search_bps = c->search_bps[batch ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0][pair ? 1 : 0];
+    sh.wide = wide;
+    sh.search_bps = c->search_bps[batch ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0][wide ? 1 : 0];
     sh.search_waves = search_waves(sh.num_sms, sh.search_bps, ntiles);
     return sh;
 }
@@ -339,7 +339,7 @@ int setup_ctx(awpm_ctx *c, const awpm_options *opt)
     c->device = dev;
     CUDA_TRY(cudaSetDevice(dev));
     CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    c->search_pair = default_search_pair();
+    c->search_wide = default_search_wide();
     for (int b = 0; b < 2; ++b)
         for (int p = 0; p < 2; ++p) {
             c->search_bps[b][0][p] = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, b == 1, p == 1);
@@ -452,14 +452,14 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     const bool timed = (c->opt.flags & AWPM_FLAG_TIME_SEARCH) != 0;
     // launch configuration: given, or the autotuner's (AWPM_LOOKUP_AUTO)
     int lookup = pd.lookup;
-    bool pair = c->search_pair;
+    bool wide = c->search_wide;
     if (c->opt.lookup == AWPM_LOOKUP_AUTO && !r.search_only && !timed) {
         const uint64_t key = ((uint64_t)(r.count > 0) << 62) | ((uint64_t)ilog2(n) << 32) |
                              (uint64_t)ilog2(nnz > 0 ? nnz : 1);
         TuneEntry &te = c->tune[key];
         const int cfg = te.chosen >= 0 ? te.chosen : te.trials;
         lookup = kTune[cfg].lookup;
-        pair = kTune[cfg].pair;
+        wide = kTune[cfg].wide;
         if (te.chosen < 0) {
             pd.tune_cfg = cfg;
             pd.tune_key = key;
@@ -493,11 +493,11 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
         AWPM_TRY(ensure(c, c->bloom, sizeof(uint32_t) * ((size_t)nnz / 4 + 1)));
 
     // the solve graph of this launch shape, built once (before the timed span)
-    const Shape sh = shape_of(c, count > 0, lookup, pair, ntiles);
+    const Shape sh = shape_of(c, count > 0, lookup, wide, ntiles);
     cudaGraphExec_t gexec = nullptr;
     if (!r.search_only && !timed) {
         cudaGraphExec_t &g = c->g_exec[count > 0 ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0]
-                                      [pair ? 1 : 0][sh.search_waves - 1];
+                                      [wide ? 1 : 0][sh.search_waves - 1];
         if (!g)
             AWPM_TRY(build_graph(c, sh, &g));
         gexec = g;

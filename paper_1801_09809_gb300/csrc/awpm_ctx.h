@@ -37,10 +37,10 @@ struct Request {
 };
 
 // Launch configurations the autotuner tries (AWPM_LOOKUP_AUTO): closing-edge
-// lookup and whether the search kernel takes two tiles per warp round.
+// lookup and whether the search kernel takes four tiles per warp round.
 struct TuneConfig {
     int lookup;
-    bool pair;
+    bool wide;
 };
 constexpr int kTuneConfigs = 3;
 constexpr TuneConfig kTune[kTuneConfigs] = {
@@ -88,8 +88,8 @@ struct awpm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t held = 0;
-    int search_bps[2][2][2] = {};  // [batch][hash][pair]
-    bool search_pair = true;      // default when the lookup is given explicitly
+    int search_bps[2][2][2] = {};  // [batch][hash][wide]
+    bool search_wide = true;      // default when the lookup is given explicitly
     // per-solve device workspace
     awpm::DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
     awpm::DevBuf winbits, wkey, bloom;
@@ -105,7 +105,7 @@ struct awpm_ctx {
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     std::vector<cudaEvent_t> tev;     // timing pairs of the timed loop
     std::vector<cudaEvent_t> flagev;  // ring of the timed loop
-    // one instantiated graph per [batch][hash][pair][search waves - 1]
+    // one instantiated graph per [batch][hash][wide][search waves - 1]
     cudaGraphExec_t g_exec[2][2][2][2] = {};
     std::map<uint64_t, awpm::TuneEntry> tune;  // autotuner state per problem class
     awpm::Pending pend;

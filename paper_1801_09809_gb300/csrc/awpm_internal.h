@@ -125,7 +125,7 @@ struct Shape {
     int search_bps;     // resident blocks per SM of the chosen search kernel
     int lookup;         // AWPM_LOOKUP_BSEARCH or AWPM_LOOKUP_HASH
     bool batch;
-    bool pair;          // search kernel takes two tiles per warp round (else one)
+    bool wide;          // search kernel takes four tiles per warp round (else one)
     int search_waves;   // search grid = search_waves full waves of resident blocks
 };
 
@@ -153,13 +153,13 @@ void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditi
                     Sink &k);
 void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k);
 // Resident blocks per SM of the search kernel for a lookup strategy.
-int search_blocks_per_sm(int lookup, bool batch, bool pair);
+int search_blocks_per_sm(int lookup, bool batch, bool wide);
 // Waves of the search grid for a problem of ntiles tiles: 2 once every warp
 // of a single wave would take at least 64 tiles (more blocks than resident
 // slots shorten the tail of uneven warps), else 1.
 int search_waves(int num_sms, int search_bps, int32_t ntiles);
-// Whether the search kernel takes two tiles per warp round (default on; the
-// environment variable AWPM_SEARCH_PAIR=0/1 overrides it, a tuning knob).
-bool default_search_pair();
+// Whether the search kernel takes four tiles per warp round (default on; the
+// environment variable AWPM_SEARCH_WIDE=0/1 overrides it, a tuning knob).
+bool default_search_wide();
 
 }  // namespace awpm

@@ -828,8 +828,8 @@ __device__ __forceinline__ void resolve_lookups(
 // resolve_lookups).  Step-C records (Algorithm 5) are combined by a 128-bit
 // compare-and-swap; `best` must be zero on entry: only positive records are
 // written.  In a batched solve, tiles of finished matrices are skipped.
-template <int kLookup, bool kBatch, bool kPair>
-__global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__ W)
+template <int kLookup, bool kBatch, bool kWide>
+__global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *__restrict__ W)
 {
     __shared__ int s_go;
     __shared__ LookupQueue s_queue[kThreads / 32];
@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_search(const Work *__restrict__
     // loads side by side, so the dependent chains (m_j, then the row record)
     // of the kU tiles overlap; the tiles of the next round have their first
     // column, start bits and row indices loaded (prefetched) meanwhile.
-    constexpr int kU = kPair ? 2 : 1;
+    constexpr int kU = kWide ? 4 : 1;
     int64_t t = s_go ? (gtid() >> 5) : (int64_t)ntiles;
     int32_t pf_c0[kU], pf_i[kU];
     uint32_t pf_mask[kU];
@@ -1254,11 +1254,11 @@ void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k)
         k.launch((const void *)k_batch_wsum, util_grid(sh), kThreads, ao);
 }
 
-template <int kLookup, bool kBatch, bool kPair>
+template <int kLookup, bool kBatch, bool kWide>
 static int bps_of()
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<kLookup, kBatch, kPair>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<kLookup, kBatch, kWide>,
                                                       kThreads, 0) != cudaSuccess) {
         cudaGetLastError();
         b = 1;
@@ -1266,19 +1266,19 @@ static int bps_of()
     return b < 1 ? 1 : b;
 }
 
-template <bool kPair>
+template <bool kWide>
 static const void *search_fn(int lookup, bool batch)
 {
     if (lookup == AWPM_LOOKUP_HASH)
-        return batch ? (const void *)k_search<AWPM_LOOKUP_HASH, true, kPair>
-                     : (const void *)k_search<AWPM_LOOKUP_HASH, false, kPair>;
-    return batch ? (const void *)k_search<AWPM_LOOKUP_BSEARCH, true, kPair>
-                 : (const void *)k_search<AWPM_LOOKUP_BSEARCH, false, kPair>;
+        return batch ? (const void *)k_search<AWPM_LOOKUP_HASH, true, kWide>
+                     : (const void *)k_search<AWPM_LOOKUP_HASH, false, kWide>;
+    return batch ? (const void *)k_search<AWPM_LOOKUP_BSEARCH, true, kWide>
+                 : (const void *)k_search<AWPM_LOOKUP_BSEARCH, false, kWide>;
 }
 
-int search_blocks_per_sm(int lookup, bool batch, bool pair)
+int search_blocks_per_sm(int lookup, bool batch, bool wide)
 {
-    if (pair) {
+    if (wide) {
         if (lookup == AWPM_LOOKUP_HASH)
             return batch ? bps_of<AWPM_LOOKUP_HASH, true, true>()
                          : bps_of<AWPM_LOOKUP_HASH, false, true>();
@@ -1292,9 +1292,9 @@ int search_blocks_per_sm(int lookup, bool batch, bool pair)
                  : bps_of<AWPM_LOOKUP_BSEARCH, false, false>();
 }
 
-bool default_search_pair()
+bool default_search_wide()
 {
-    const char *v = getenv("AWPM_SEARCH_PAIR");
+    const char *v = getenv("AWPM_SEARCH_WIDE");
     if (v && (v[0] == '0' || v[0] == '1') && v[1] == 0)
         return v[0] == '1';
     return true;
@@ -1305,7 +1305,7 @@ void launch_search(const Work *d, const Shape &sh, Sink &k)
     const unsigned grid = (unsigned)(sh.num_sms * (sh.search_bps > 0 ? sh.search_bps : 1) *
                                      (sh.search_waves > 1 ? sh.search_waves : 1));
     void *a[] = {(void *)&d};
-    const void *f = sh.pair ? search_fn<true>(sh.lookup, sh.batch)
+    const void *f = sh.wide ? search_fn<true>(sh.lookup, sh.batch)
                             : search_fn<false>(sh.lookup, sh.batch);
     k.launch(f, grid, kThreads, a);
 }

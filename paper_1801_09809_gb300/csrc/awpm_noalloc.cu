@@ -179,8 +179,8 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     }
     Shape sh;
     sh.num_sms = num_sms;
-    sh.pair = default_search_pair();
-    sh.search_bps = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, false, sh.pair);
+    sh.wide = default_search_wide();
+    sh.search_bps = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, false, sh.wide);
     sh.lookup = AWPM_LOOKUP_BSEARCH;
     sh.batch = false;
     sh.search_waves = search_waves(num_sms, sh.search_bps, wk.ntiles);
