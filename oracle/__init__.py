@@ -46,6 +46,11 @@ class _Stats(ctypes.Structure):
                 ("weight_out", ctypes.c_double)]
 
 
+class _GreedyStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("cardinality", ctypes.c_int32),
+                ("weight", ctypes.c_double)]
+
+
 def _p(a, t):
     if a is None:
         return None
@@ -85,6 +90,9 @@ class Oracle:
                                      ctypes.c_int32]
         L.oracle_step_c.restype = ctypes.c_int
         L.oracle_step_c.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p, f64p, i32p, i64p]
+        L.oracle_greedy.restype = ctypes.c_int
+        L.oracle_greedy.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p,
+                                    ctypes.POINTER(_GreedyStats)]
 
     # -- API -----------------------------------------------------------------
     def validate(self, g, mate=None) -> str:
@@ -115,6 +123,20 @@ class Oracle:
             k = min(st.iterations, trace_cap)
             trace = (tw[:k].copy(), tf[:k].copy())
         return out[:g.n].copy(), stats, trace
+
+    def greedy(self, g):
+        """Heavy-weight greedy maximal matching: (mate_out with -1 for
+        unmatched columns, stats dict {rounds, cardinality, weight})."""
+        cp, ri, w = _arrs(g)
+        out = np.empty(max(g.n, 1), dtype=np.int32)
+        st = _GreedyStats()
+        rc = self.lib.oracle_greedy(g.n, _p(cp, ctypes.c_int32), _p(ri, ctypes.c_int32),
+                                    _p(w, ctypes.c_double), _p(out, ctypes.c_int32),
+                                    ctypes.byref(st))
+        if rc != 0:
+            raise OracleError(rc)
+        return out[:g.n], {"rounds": st.rounds, "cardinality": st.cardinality,
+                           "weight": st.weight}
 
     def step_c(self, g, mate=None):
         """Step-C winners of one pass from ``mate``: (gain[n], row[n], counts[4])."""

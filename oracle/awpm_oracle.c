@@ -88,10 +88,11 @@ static int64_t find_entry(const int32_t *colptr, const int32_t *rowidx, int32_t 
  * (UNSORTED_OR_DUP), non-finite weights (NONFINITE), matching not a perfect
  * matching over stored entries (NOT_PERFECT).
  */
-int oracle_validate(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
-                    const int32_t *mate)
+/* The checks on the matrix alone (no matching), in the same priority order. */
+static int validate_matrix(int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                           const double *w)
 {
-    if (n < 0 || (n > 0 && (!colptr || !mate)))
+    if (n < 0 || (n > 0 && !colptr))
         return OR_INVALID_ARG;
     if (n == 0)
         return OR_OK;
@@ -113,6 +114,17 @@ int oracle_validate(int32_t n, const int32_t *colptr, const int32_t *rowidx, con
     for (int64_t p = 0; p < nnz; ++p)
         if (!isfinite(w[p]))
             return OR_NONFINITE;
+    return OR_OK;
+}
+
+int oracle_validate(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+                    const int32_t *mate)
+{
+    if (n < 0 || (n > 0 && (!colptr || !mate)))
+        return OR_INVALID_ARG;
+    int rc0 = validate_matrix(n, colptr, rowidx, w);
+    if (rc0 != OR_OK || n == 0)
+        return rc0;
     char *seen = (char *)calloc((size_t)n, 1);
     if (!seen)
         return OR_OOM;
@@ -371,4 +383,114 @@ int oracle_step_c(int32_t n, const int32_t *colptr, const int32_t *rowidx, const
     free(mr);
     free(wm);
     return f < 0 ? OR_OOM : OR_OK;
+}
+
+/*
+ * Heavy-weight greedy maximal matching: the maximal matching that starts the
+ * paper's pipeline (Section 5.1), with its heavy-weight preference ("we
+ * select edges with heavy weights when greedily selecting edges").
+ *
+ * Reading: greedy takes the stored entries from heaviest to lightest (equal
+ * weights: lower row first, then lower column) and keeps every entry whose
+ * row and column are both still unmatched.  It is computed here in rounds, as
+ * a parallel machine computes it: in each round every unmatched column names
+ * its first entry in that order among the entries with an unmatched row,
+ * every unmatched row names its first entry among the entries with an
+ * unmatched column, and the entries named by both their row and their column
+ * are matched.  The first remaining entry overall is always named twice, so
+ * every round but the last matches at least one entry; the last round
+ * matches none and the matching is maximal.  `rounds` counts all rounds,
+ * the last one included.
+ *
+ * mate_out[j]: the row matched to column j, or -1.
+ */
+typedef struct {
+    int32_t rounds;
+    int32_t cardinality;   /* matched columns */
+    double weight;         /* sum of the matched weights, ascending column order */
+} oracle_greedy_stats;
+
+int oracle_greedy(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+                  int32_t *mate_out, oracle_greedy_stats *st)
+{
+    int rc = validate_matrix(n, colptr, rowidx, w);
+    if (rc != OR_OK)
+        return rc;
+    if (!mate_out && n > 0)
+        return OR_INVALID_ARG;
+    int32_t nn = n > 0 ? n : 1;
+    int32_t *mc = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);   /* row of column */
+    int32_t *mr = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);   /* column of row */
+    int64_t *cbest = (int64_t *)malloc(sizeof(int64_t) * (size_t)nn); /* position, or -1 */
+    int32_t *rbest = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn); /* column, or -1 */
+    double *rbw = (double *)malloc(sizeof(double) * (size_t)nn);      /* its weight */
+    if (!mc || !mr || !cbest || !rbest || !rbw) {
+        free(mc); free(mr); free(cbest); free(rbest); free(rbw);
+        return OR_OOM;
+    }
+    for (int32_t x = 0; x < n; ++x) {
+        mc[x] = -1;
+        mr[x] = -1;
+    }
+    oracle_greedy_stats s;
+    memset(&s, 0, sizeof(s));
+    for (;;) {
+        s.rounds += 1;
+        /* every unmatched column: its first entry with an unmatched row
+         * (rows ascend in a column, so a strictly heavier weight wins) */
+        for (int32_t j = 0; j < n; ++j) {
+            cbest[j] = -1;
+            if (mc[j] >= 0)
+                continue;
+            for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+                if (mr[rowidx[p]] >= 0)
+                    continue;
+                if (cbest[j] < 0 || w[p] > w[cbest[j]])
+                    cbest[j] = p;
+            }
+        }
+        /* every unmatched row: its first entry with an unmatched column
+         * (columns are visited in ascending order) */
+        for (int32_t i = 0; i < n; ++i)
+            rbest[i] = -1;
+        for (int32_t j = 0; j < n; ++j) {
+            if (mc[j] >= 0)
+                continue;
+            for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+                int32_t i = rowidx[p];
+                if (mr[i] >= 0)
+                    continue;
+                if (rbest[i] < 0 || w[p] > rbw[i]) {
+                    rbest[i] = j;
+                    rbw[i] = w[p];
+                }
+            }
+        }
+        /* entries named by both ends are matched */
+        int32_t matched = 0;
+        for (int32_t j = 0; j < n; ++j) {
+            if (cbest[j] < 0)
+                continue;
+            int32_t i = rowidx[cbest[j]];
+            if (rbest[i] == j) {
+                mc[j] = i;
+                mr[i] = j;
+                ++matched;
+            }
+        }
+        s.cardinality += matched;
+        if (matched == 0)
+            break;
+    }
+    double total = 0.0;
+    for (int32_t j = 0; j < n; ++j) {
+        mate_out[j] = mc[j];
+        if (mc[j] >= 0)
+            total += w[find_entry(colptr, rowidx, mc[j], j)];
+    }
+    s.weight = total;
+    if (st)
+        *st = s;
+    free(mc); free(mr); free(cbest); free(rbest); free(rbw);
+    return OR_OK;
 }

@@ -145,3 +145,38 @@ def no_positive_4cycle_vectorized(g, mate):
     found = keys[pos] == qk
     gain = ((wij[found] + g.weight[pos[found]]) - wm[k[found]]) - wm[j[found]]
     return not np.any(gain > 0)
+
+
+def greedy_sequential(g):
+    """Textbook greedy: stored entries from heaviest to lightest (equal
+    weights: lower row, then lower column), each kept when its row and its
+    column are both free.  Returns mate[j] (row or -1)."""
+    col = np.repeat(np.arange(g.n), np.diff(g.colptr))
+    order = sorted(range(len(g.rowidx)),
+                   key=lambda p: (-float(g.weight[p]), int(g.rowidx[p]), int(col[p])))
+    mate = np.full(g.n, -1, dtype=np.int64)
+    row_used = np.zeros(g.n, dtype=bool)
+    for p in order:
+        i, j = int(g.rowidx[p]), int(col[p])
+        if mate[j] < 0 and not row_used[i]:
+            mate[j] = i
+            row_used[i] = True
+    return mate
+
+
+def is_maximal_matching(g, mate):
+    """A matching over stored entries that no stored entry between a free
+    row and a free column could extend."""
+    rows = [int(r) for r in mate if r >= 0]
+    if len(rows) != len(set(rows)):
+        return False
+    free_row = np.ones(g.n, dtype=bool)
+    free_row[rows] = False
+    for j in range(g.n):
+        seg = g.rowidx[g.colptr[j]:g.colptr[j + 1]]
+        if mate[j] >= 0:
+            if mate[j] not in seg:
+                return False
+        elif np.any(free_row[seg]):
+            return False
+    return True

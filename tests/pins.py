@@ -256,6 +256,47 @@ def pin_rank_simulation(orc):
             assert cur.tolist() == out.tolist() and it + 1 == st["iterations"], (s, side)
 
 
+def pin_greedy_matching(orc):
+    """Heavy-weight greedy maximal matching (Section 5.1): the round-based
+    matching equals the textbook sequential greedy over the entries sorted by
+    weight (ties by row, then column), is maximal, and its statistics add up;
+    integer weights (ties), signed zeros and empty columns included."""
+    cases = []
+    for s in range(30):
+        n = 5 + 13 * s
+        cases.append(gen.random_small(n, 0.05 + 0.04 * (s % 4), 5100 + s,
+                                      integer_weights=(s % 2 == 0)))
+    cases.append(gen.stencil_2d(12, 5200))
+    cases.append(full2(3.0, 2.0, 2.0, 1.0))
+    cases.append(full2(1.0, 3.0, 3.0, 1.0))
+    z = full2(0.0, -0.0, -0.0, 0.0)
+    cases.append(z)
+    # empty columns: drop every entry of two columns
+    e = gen.random_small(40, 0.2, 5300)
+    keep = np.ones(e.nnz, dtype=bool)
+    for c in (3, 17):
+        keep[e.colptr[c]:e.colptr[c + 1]] = False
+    counts = np.diff(e.colptr) - np.add.reduceat(~keep, e.colptr[:-1])
+    e.rowidx, e.weight = e.rowidx[keep], e.weight[keep]
+    e.colptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    cases.append(e)
+    for g in cases:
+        got, st = orc.greedy(g)
+        ref = brute.greedy_sequential(g)
+        assert got.tolist() == ref.tolist(), g.name
+        assert brute.is_maximal_matching(g, got), g.name
+        assert st["cardinality"] == int(np.sum(got >= 0))
+        assert st["rounds"] >= 1 + (1 if st["cardinality"] else 0)
+        wsum = sum(float(g.weight[g.colptr[j] + int(np.nonzero(
+            g.rowidx[g.colptr[j]:g.colptr[j + 1]] == got[j])[0][0])])
+            for j in range(g.n) if got[j] >= 0)
+        assert abs(st["weight"] - wsum) <= 1e-12 * max(1.0, abs(wsum))
+    # 2x2 by hand: the heaviest entry first
+    assert orc.greedy(full2(3.0, 2.0, 2.0, 1.0))[0].tolist() == [0, 1]
+    assert orc.greedy(full2(1.0, 3.0, 3.0, 1.0))[0].tolist() == [1, 0]
+    assert orc.greedy(full2(1.0, 3.0, 2.0, 1.0))[0].tolist() == [1, 0]
+
+
 def pin_validation(orc):
     """Input checks: error classes for malformed inputs."""
     g = gen.random_small(5, 0.6, 3)
@@ -315,4 +356,5 @@ def pin_paper_maxiters(orc):
 
 PINS = [pin_hand_cases, pin_2x2_closed_form, pin_block_diagonal, pin_six_cycle,
         pin_bruteforce_small, pin_one_pass_bruteforce, pin_rank_simulation,
-        pin_local_optimality_midsize, pin_validation, pin_resume, pin_paper_maxiters]
+        pin_local_optimality_midsize, pin_validation, pin_resume, pin_paper_maxiters,
+        pin_greedy_matching]

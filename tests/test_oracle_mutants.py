@@ -41,6 +41,13 @@ MUTANTS = [
     ("stops one pass early", "if (f == 0) {", "if (f <= 1) {"),
     ("duplicate mates accepted", "if (r < 0 || r >= n || seen[r] ||", "if (r < 0 || r >= n ||"),
     ("non-finite weights accepted", "if (!isfinite(w[p]))", "if (0)"),
+    ("greedy column keeps the lightest", "if (cbest[j] < 0 || w[p] > w[cbest[j]])",
+     "if (cbest[j] < 0 || w[p] < w[cbest[j]])"),
+    ("greedy column tie to the highest row", "if (cbest[j] < 0 || w[p] > w[cbest[j]])",
+     "if (cbest[j] < 0 || w[p] >= w[cbest[j]])"),
+    ("greedy row tie to the highest column", "if (rbest[i] < 0 || w[p] > rbw[i]) {",
+     "if (rbest[i] < 0 || w[p] >= rbw[i]) {"),
+    ("greedy ignores the row's choice", "if (rbest[i] == j) {", "if (mr[i] < 0) {"),
 ]
 
 RUNNER = textwrap.dedent("""
