@@ -217,6 +217,36 @@ int awpm_poll(awpm_ctx *ctx, uint64_t ticket, int *done, awpm_stats *stats);
 int awpm_wait(awpm_ctx *ctx, uint64_t ticket, awpm_stats *stats);
 
 /*
+ * Heavy-weight greedy maximal matching (Section 5.1: the maximal matching
+ * that starts the paper's pipeline, choosing heavy edges first).  No
+ * matching is given: the result is the matching greedy builds when it takes
+ * the stored entries from heaviest to lightest (equal weights: lower row
+ * first, then lower column) and keeps each entry whose row and column are
+ * both free.  It is computed in rounds: every free column and every free row
+ * names its first free entry in that order, and the entries named by both
+ * ends are matched; a round that matches nothing ends the loop, and the
+ * matching is then maximal.  When it is perfect (cardinality = n) it can be
+ * given to awpm_improve as mate_in.
+ *   colptr, rowidx, weight: the matrix as for awpm_improve (host or device).
+ *   mate_out[n] (host or device): the row matched to column j, or -1.
+ *   stats (may be NULL): rounds (all of them, the last one included),
+ *     cardinality, the sum of the matched weights, elapsed milliseconds.
+ * Errors as awpm_improve: AWPM_ERR_INVALID_ARG, _UNSORTED_OR_DUP, _NONFINITE;
+ * AWPM_ERR_NOT_PERFECT when a column has no entry (no perfect matching can
+ * exist then).
+ */
+typedef struct {
+    int32_t rounds;
+    int32_t cardinality;
+    double weight;
+    double ms_total;
+    int64_t reserved[2];
+} awpm_greedy_stats;
+
+int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                const double *weight, int32_t *mate_out, awpm_greedy_stats *stats);
+
+/*
  * One cycle search from a given matching without flipping anything: Steps
  * A-C of a single pass (Algorithms 3-5).  For every column j,
  * stepc_gain[j] / stepc_row[j] receive the Step-C winner rooted at j (its gain

@@ -49,6 +49,15 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class GreedyStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("cardinality", ctypes.c_int32),
+                ("weight", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("reserved", ctypes.c_int64 * 2)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class AwpmError(RuntimeError):
     def __init__(self, code: int, detail: str = ""):
         self.code = code
@@ -80,6 +89,8 @@ SIGNATURES = [
     ("awpm_wait", ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(Stats)]),
     ("awpm_search_noalloc", ctypes.c_int, [ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                            ctypes.POINTER(Stats)]),
+    ("awpm_greedy", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP,
+                                   ctypes.POINTER(GreedyStats)]),
 ]
 NOALLOC_MAX_N = 262144
 NOALLOC_MAX_NNZ = 4194304
@@ -198,6 +209,15 @@ def awpm_search(ctx: Context, n, colptr, rowidx, weight, mate, stepc_gain, stepc
     _check(lib().awpm_search(ctx.handle, int(n), _ptr(colptr, "int32"), _ptr(rowidx, "int32"),
                              _ptr(weight, "float64"), _ptr(mate, "int32"),
                              _ptr(stepc_gain, "float64"), _ptr(stepc_row, "int32"),
+                             ctypes.byref(st)))
+    return st.as_dict()
+
+
+def awpm_greedy(ctx: Context, n, colptr, rowidx, weight, mate_out) -> dict:
+    """Heavy-weight greedy maximal matching into mate_out (-1: unmatched)."""
+    st = GreedyStats()
+    _check(lib().awpm_greedy(ctx.handle, int(n), _ptr(colptr, "int32"), _ptr(rowidx, "int32"),
+                             _ptr(weight, "float64"), _ptr(mate_out, "int32"),
                              ctypes.byref(st)))
     return st.as_dict()
 

@@ -235,6 +235,74 @@ done:
     return rc;
 }
 
+// Graph of the greedy maximal matching: state reset and input checks, a
+// conditional WHILE node over the rounds, the matched-weight sum.
+int build_greedy_graph(awpm_ctx *c, const Shape &sh, cudaGraphExec_t *out)
+{
+    const Work *d = (const Work *)c->d_work.p;
+    cudaGraph_t top = nullptr, g_init = nullptr, g_final = nullptr;
+    cudaGraphNode_t n_init, n_cond, n_final;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    int rc = AWPM_OK;
+    cudaError_t e;
+    Sink si, sf, sb;
+    if ((e = cudaGraphCreate(&g_init, 0)) != cudaSuccess ||
+        (e = cudaGraphCreate(&g_final, 0)) != cudaSuccess ||
+        (e = cudaGraphCreate(&top, 0)) != cudaSuccess) {
+        note_cuda_error(e, "cudaGraphCreate", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    si.graph = g_init;
+    launch_greedy_init(d, sh, si);
+    sf.graph = g_final;
+    launch_weight_sum(d, sh, true, sf);
+    if (si.err != cudaSuccess || sf.err != cudaSuccess) {
+        note_cuda_error(si.err != cudaSuccess ? si.err : sf.err, "kernel nodes", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    if ((e = cudaGraphAddChildGraphNode(&n_init, top, nullptr, 0, g_init)) != cudaSuccess ||
+        (e = cudaGraphConditionalHandleCreate(&h, top, 1, cudaGraphCondAssignDefault)) !=
+            cudaSuccess) {
+        note_cuda_error(e, "graph assembly", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&n_cond, top, &n_init, nullptr, 1, &cp)) != cudaSuccess) {
+        note_cuda_error(e, "conditional node", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    sb.graph = cp.conditional.phGraph_out[0];
+    launch_greedy_round(d, sh, true, h, sb);
+    if (sb.err != cudaSuccess) {
+        note_cuda_error(sb.err, "round body nodes", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    if ((e = cudaGraphAddChildGraphNode(&n_final, top, &n_cond, 1, g_final)) != cudaSuccess ||
+        (e = cudaGraphInstantiate(out, top, 0)) != cudaSuccess) {
+        note_cuda_error(e, "graph instantiation", __LINE__);
+        *out = nullptr;
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+done:
+    if (top)
+        cudaGraphDestroy(top);
+    if (g_init)
+        cudaGraphDestroy(g_init);
+    if (g_final)
+        cudaGraphDestroy(g_final);
+    cudaGetLastError();
+    return rc;
+}
+
 int ensure_timing_events(awpm_ctx *c, size_t pairs)
 {
     while (c->tev.size() < 2 * pairs) {
@@ -378,12 +446,18 @@ void teardown_ctx(awpm_ctx *c)
                         cudaGraphExecDestroy(c->g_exec[b][h][p][v]);
                         c->g_exec[b][h][p][v] = nullptr;
                     }
+    for (int v = 0; v < 2; ++v)
+        if (c->g_greedy[v]) {
+            cudaGraphExecDestroy(c->g_greedy[v]);
+            c->g_greedy[v] = nullptr;
+        }
     DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->wmr,
                       &c->colsig,  &c->best,     &c->dsel,     &c->tile_col, &c->starts,
                       &c->ctl,     &c->wpart,    &c->htab,     &c->b_noff,   &c->b_colmat,
                       &c->b_tilemat, &c->b_i32,  &c->b_u64,    &c->b_f64,    &c->s_colptr,
                       &c->s_rowidx, &c->s_w,     &c->s_mate,   &c->s_out,    &c->s_gain,
-                      &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey,     &c->bloom};
+                      &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey,     &c->bloom,    &c->gckey,
+                      &c->gcpos,   &c->grkey,    &c->grcol};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_work)
@@ -887,6 +961,100 @@ int awpm_improve_batch(awpm_ctx *ctx, int32_t count, const int32_t *n_off, const
     r.count = count;
     r.n_off = n_off;
     return solve_sync(ctx, r, total, per_matrix);
+}
+
+int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                const double *weight, int32_t *mate_out, awpm_greedy_stats *stats)
+{
+    if (!ctx || n < 0 || (n > 0 && (!colptr || !mate_out)))
+        return AWPM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    awpm_ctx *c = ctx;
+    awpm_greedy_stats S;
+    std::memset(&S, 0, sizeof(S));
+    if (n == 0) {
+        S.rounds = 1;  // one round, which matches nothing
+        if (stats)
+            *stats = S;
+        return AWPM_OK;
+    }
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int l_colptr = where(c, colptr), l_rowidx = where(c, rowidx), l_w = where(c, weight),
+              l_out = where(c, mate_out);
+    if (l_colptr < 0 || l_rowidx < 0 || l_w < 0 || l_out < 0)
+        return AWPM_ERR_INVALID_ARG;
+    int32_t nnz = 0;
+    if (l_colptr == 1) {
+        CUDA_TRY(cudaMemcpyAsync(c->h_ctl, colptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        std::memcpy(&nnz, c->h_ctl, sizeof(int32_t));
+    } else {
+        nnz = colptr[n];
+    }
+    if (nnz < 0 || nnz > kMaxNnz || (nnz > 0 && (!rowidx || !weight)))
+        return AWPM_ERR_INVALID_ARG;
+    const int32_t ntiles = (int32_t)(((int64_t)nnz + kTile - 1) / kTile);
+    AWPM_TRY(ensure(c, c->mc, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->mr, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->wm, sizeof(double) * n));
+    AWPM_TRY(ensure(c, c->gckey, sizeof(long long) * n));
+    AWPM_TRY(ensure(c, c->gcpos, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->grkey, sizeof(long long) * n));
+    AWPM_TRY(ensure(c, c->grcol, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->tile_col, sizeof(int32_t) * ((size_t)ntiles + 1)));
+    AWPM_TRY(ensure(c, c->starts, sizeof(uint32_t) * (((size_t)nnz + 31) / 32 + 1)));
+    AWPM_TRY(ensure(c, c->ctl, sizeof(Ctl)));
+    AWPM_TRY(ensure(c, c->wpart, sizeof(double) * kWsumBlocks));
+    const Shape sh = shape_of(c, false, AWPM_LOOKUP_BSEARCH, true, ntiles);
+    cudaGraphExec_t &g = c->g_greedy[sh.search_waves - 1];
+    if (!g)
+        AWPM_TRY(build_greedy_graph(c, sh, &g));
+    CUDA_TRY(cudaEventRecord(c->ev_a, c->stream));
+    Work &wk = *c->h_work;
+    std::memset(&wk, 0, sizeof(Work));
+    wk.n = n;
+    wk.nnz = nnz;
+    wk.ntiles = ntiles;
+    // at most n rounds match something, then one matches nothing
+    wk.max_passes = n < 0x7fffffff ? n + 1 : n;
+    wk.lookup = AWPM_LOOKUP_BSEARCH;
+    AWPM_TRY(stage_in(c, c->s_colptr, colptr, (size_t)n + 1, l_colptr, &wk.colptr));
+    AWPM_TRY(stage_in(c, c->s_rowidx, rowidx, (size_t)nnz, l_rowidx, &wk.rowidx));
+    AWPM_TRY(stage_in(c, c->s_w, weight, (size_t)nnz, l_w, &wk.w));
+    wk.mc = (int32_t *)c->mc.p;
+    wk.mr = (int32_t *)c->mr.p;
+    wk.wm = (double *)c->wm.p;
+    wk.tile_col = (int32_t *)c->tile_col.p;
+    wk.starts = (uint32_t *)c->starts.p;
+    wk.ctl = (Ctl *)c->ctl.p;
+    wk.wpart = (double *)c->wpart.p;
+    wk.gckey = (long long *)c->gckey.p;
+    wk.gcpos = (int32_t *)c->gcpos.p;
+    wk.grkey = (long long *)c->grkey.p;
+    wk.grcol = (int32_t *)c->grcol.p;
+    CUDA_TRY(cudaMemcpyAsync(c->d_work.p, c->h_work, sizeof(Work), cudaMemcpyHostToDevice,
+                             c->stream));
+    CUDA_TRY(cudaGraphLaunch(g, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(mate_out, wk.mc, sizeof(int32_t) * n,
+                             l_out == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->h_ctl, wk.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaEventRecord(c->ev_b, c->stream));
+    CUDA_TRY(cudaEventSynchronize(c->ev_b));
+    const Ctl &h = *c->h_ctl;
+    const int rc = code_of(h.err);
+    if (rc != AWPM_OK)
+        return rc;
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev_a, c->ev_b));
+    S.rounds = h.iterations;
+    S.cardinality = (int32_t)h.cycles;
+    S.weight = h.weight_out;
+    S.ms_total = ms;
+    if (stats)
+        *stats = S;
+    return AWPM_OK;
 }
 
 int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,

@@ -93,6 +93,7 @@ struct awpm_ctx {
     // per-solve device workspace
     awpm::DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
     awpm::DevBuf winbits, wkey, bloom;
+    awpm::DevBuf gckey, gcpos, grkey, grcol;  // greedy matching records
     awpm::DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
     // staging of host-resident arrays
     awpm::DevBuf s_colptr, s_rowidx, s_w, s_mate, s_out, s_gain, s_row;
@@ -107,6 +108,7 @@ struct awpm_ctx {
     std::vector<cudaEvent_t> flagev;  // ring of the timed loop
     // one instantiated graph per [batch][hash][wide][search waves - 1]
     cudaGraphExec_t g_exec[2][2][2][2] = {};
+    cudaGraphExec_t g_greedy[2] = {};  // greedy matching, [search waves - 1] of the shape
     std::map<uint64_t, awpm::TuneEntry> tune;  // autotuner state per problem class
     awpm::Pending pend;
     // the request server of this context (awpm_submit), created on first use

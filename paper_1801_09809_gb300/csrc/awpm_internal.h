@@ -117,6 +117,12 @@ struct Work {
     Ctl *ctl;
     double *wpart;      // partial sums of the weight reduction
     BatchWork bw;       // batched solve (bw.count > 0), else zero
+    // greedy maximal matching: per column the best free entry (order key,
+    // then position), per row the best free entry (order key, then column)
+    long long *gckey;
+    int32_t *gcpos;
+    long long *grkey;
+    int32_t *grcol;
 };
 
 // Launch shape of a context: fixed grids sized by the GPU, not the problem.
@@ -152,6 +158,11 @@ void launch_select_and_flip(const Work *d, const Shape &sh, Sink &k);
 void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,
                     Sink &k);
 void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k);
+// Greedy maximal matching: state reset and input checks; one round (the
+// control kernel ends the loop after a round that matched nothing).
+void launch_greedy_init(const Work *d, const Shape &sh, Sink &k);
+void launch_greedy_round(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,
+                         Sink &k);
 // Resident blocks per SM of the search kernel for a lookup strategy.
 int search_blocks_per_sm(int lookup, bool batch, bool wide);
 // Waves of the search grid for a problem of ntiles tiles: 2 once every warp

@@ -1181,6 +1181,198 @@ __global__ void k_export_stepc(const Work *__restrict__ W, double *gain, int32_t
 }
 
 // ---------------------------------------------------------------------------
+// Heavy-weight greedy maximal matching (Section 5.1)
+// ---------------------------------------------------------------------------
+// The matching that greedy builds when it takes the stored entries from
+// heaviest to lightest (equal weights: lower row, then lower column) and
+// keeps each entry whose row and column are both free.  Computed in rounds:
+// every free column names its first free entry in that order (largest
+// weight, then lowest row), every free row names its first free entry
+// (largest weight, then lowest column), and the entries named by both ends
+// are matched.  Weights are compared through order keys: 64-bit integers
+// ordered like the doubles, so the maxima and minima are plain 64-bit
+// atomics.
+
+constexpr long long kKeyNone = (long long)0x8000000000000000ull;
+
+// Integer ordered like the weight (-0 taken as +0; finite weights only).
+__device__ __forceinline__ long long order_key(double x)
+{
+    long long b = __double_as_longlong(x);
+    if (b == kKeyNone)
+        b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+// Clear the matching, the per-round records and the control block.
+__global__ void k_gm_reset(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (gtid() == 0) {
+        Ctl *c = w.ctl;
+        c->err = 0u;
+        c->active = 1;
+        c->iterations = 0;
+        c->converged = 0;
+        c->max_passes = w.max_passes;
+        c->pass_flips = 0ull;
+        c->cycles = 0ull;
+        c->candidates = 0ull;
+        c->found = 0ull;
+        c->positive = 0ull;
+        c->weight_in = 0.0;
+        c->weight_out = 0.0;
+    }
+    for (int64_t x = gtid(); x < w.n; x += gstride()) {
+        w.mc[x] = -1;
+        w.mr[x] = -1;
+        w.wm[x] = 0.0;
+        w.gckey[x] = kKeyNone;
+        w.gcpos[x] = 0x7fffffff;
+        w.grkey[x] = kKeyNone;
+        w.grcol[x] = 0x7fffffff;
+    }
+    const int64_t words = ((int64_t)w.nnz + 31) / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride())
+        w.starts[x] = 0u;
+}
+
+// Entry checks of the greedy input: row range, sortedness, finite weights.
+__global__ void __launch_bounds__(kThreads) k_gm_check(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err & kErrInvalid)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    unsigned bits = 0;
+    for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
+        const int32_t p = (int32_t)(t * kTile) + lane;
+        const bool valid = p < w.nnz;
+        const uint32_t mask = __ldg(w.starts + t);
+        const int32_t r = valid ? __ldcs(w.rowidx + p) : 0;
+        const int32_t up = __shfl_up_sync(FULL_MASK, r, 1);
+        const int32_t before = lane == 0 ? ((valid && p > 0) ? __ldg(w.rowidx + p - 1) : 0) : up;
+        if (valid) {
+            if (r < 0 || r >= w.n)
+                bits |= kErrInvalid;
+            if ((__double2hiint(__ldcs(w.w + p)) & 0x7ff00000) == 0x7ff00000)
+                bits |= kErrNonfinite;
+            if (p > 0 && !((mask >> lane) & 1u) && before >= r)
+                bits |= kErrUnsorted;
+        }
+    }
+    bits = __reduce_or_sync(FULL_MASK, bits);
+    if (lane == 0 && bits)
+        raise_err(w.ctl, bits);
+}
+
+// Round, phase 1: the largest key among the free entries of every free
+// column (warp maximum per column segment, then a 64-bit atomic) and of
+// every free row (an atomic per entry, skipped when it cannot win).
+__global__ void __launch_bounds__(kThreads) k_gm_max(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (!gate(w.ctl))
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
+        const int32_t base = (int32_t)(t * kTile);
+        const int32_t p = base + lane;
+        const bool valid = p < w.nnz;
+        const int32_t c0 = __ldg(w.tile_col + t);
+        const uint32_t mask = __ldg(w.starts + t);
+        const int32_t j = valid ? lane_column(c0, mask, lane) : 0;
+        const int32_t i = valid ? __ldcs(w.rowidx + p) : 0;
+        const bool fr = valid && w.mc[j] < 0 && w.mr[i] < 0;
+        long long key = fr ? order_key(__ldcs(w.w + p)) : kKeyNone;
+        if (fr && key > *(volatile const long long *)(w.grkey + i))
+            atomicMax(w.grkey + i, key);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long o = __shfl_down_sync(FULL_MASK, key, off);
+            if (lane + off < 32 && ((mask >> (lane + 1)) & ((1u << off) - 1u)) == 0u && o > key)
+                key = o;
+        }
+        const bool head = valid && (lane == 0 || ((mask >> lane) & 1u));
+        if (head && key != kKeyNone && key > *(volatile const long long *)(w.gckey + j))
+            atomicMax(w.gckey + j, key);
+    }
+}
+
+// Round, phase 2: among the free entries holding the maximum key, the lowest
+// position of every column (= lowest row) and the lowest column of every row.
+__global__ void __launch_bounds__(kThreads) k_gm_min(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (!gate(w.ctl))
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
+        const int32_t base = (int32_t)(t * kTile);
+        const int32_t p = base + lane;
+        const bool valid = p < w.nnz;
+        const int32_t c0 = __ldg(w.tile_col + t);
+        const uint32_t mask = __ldg(w.starts + t);
+        const int32_t j = valid ? lane_column(c0, mask, lane) : 0;
+        const int32_t i = valid ? __ldcs(w.rowidx + p) : 0;
+        const bool fr = valid && w.mc[j] < 0 && w.mr[i] < 0;
+        const long long key = fr ? order_key(__ldcs(w.w + p)) : kKeyNone;
+        if (fr && key == w.grkey[i] && j < *(volatile const int32_t *)(w.grcol + i))
+            atomicMin(w.grcol + i, j);
+        int32_t pos = (fr && key == w.gckey[j]) ? p : 0x7fffffff;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int32_t o = __shfl_down_sync(FULL_MASK, pos, off);
+            if (lane + off < 32 && ((mask >> (lane + 1)) & ((1u << off) - 1u)) == 0u && o < pos)
+                pos = o;
+        }
+        const bool head = valid && (lane == 0 || ((mask >> lane) & 1u));
+        if (head && pos != 0x7fffffff)
+            atomicMin(w.gcpos + j, pos);
+    }
+}
+
+// Round, phase 3: a free column whose named entry is also named by its row
+// is matched; the column's records are cleared for the next round.
+__global__ void k_gm_match(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    unsigned long long matched = 0;
+    if (gate(w.ctl)) {
+        for (int64_t j = gtid(); j < w.n; j += gstride()) {
+            const int32_t p = w.gcpos[j];
+            if (p == 0x7fffffff)
+                continue;
+            w.gckey[j] = kKeyNone;
+            w.gcpos[j] = 0x7fffffff;
+            const int32_t i = w.rowidx[p];
+            if (w.grcol[i] == (int32_t)j) {
+                w.mc[j] = i;
+                w.mr[i] = (int32_t)j;
+                w.wm[j] = w.w[p];
+                ++matched;
+            }
+        }
+    }
+    block_add_u64(matched, &w.ctl->pass_flips);
+}
+
+// Round, phase 4: clear the rows' records for the next round.
+__global__ void k_gm_rows(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (!gate(w.ctl))
+        return;
+    for (int64_t i = gtid(); i < w.n; i += gstride()) {
+        w.grkey[i] = kKeyNone;
+        w.grcol[i] = 0x7fffffff;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launchers: fixed grids (a multiple of the SM count)
 // ---------------------------------------------------------------------------
 
@@ -1340,6 +1532,26 @@ void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditi
         k.launch((const void *)k_control_graph, 1, 1, ah);
     else
         k.launch((const void *)k_control, 1, 1, a);
+}
+
+void launch_greedy_init(const Work *d, const Shape &sh, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_gm_reset, util_grid(sh), kThreads, a);
+    k.launch((const void *)k_check_colptr, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_mark_starts, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_gm_check, init_tile_grid(sh), kThreads, a);
+}
+
+void launch_greedy_round(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,
+                         Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_gm_max, init_tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_gm_min, init_tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_gm_match, util_grid(sh), kThreads, a);
+    k.launch((const void *)k_gm_rows, util_grid(sh), kThreads, a);
+    launch_control(d, sh, graph, h, k);
 }
 
 void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k)
