@@ -310,12 +310,18 @@ def bench_greedy(awpm, torch, dev, g, reps=5):
         st = awpm.awpm_greedy(ctx, g.n, cp, ri, w, out)
         times.append(st["ms_total"])
     awpm.awpm_destroy(ctx)
+    # once more with the rounds launched from the host (kernels visible to a
+    # profiler; graphs with conditional nodes are not); same result required
+    tctx = awpm.awpm_create(device=dev.index or 0, flags=awpm.FLAG_TIME_SEARCH)
+    out2 = torch.empty_like(out)
+    awpm.awpm_greedy(tctx, g.n, cp, ri, w, out2)
+    awpm.awpm_destroy(tctx)
     ms = statistics.median(times)
     visits = 2 * g.nnz * st["rounds"]
     t0 = time.perf_counter()
     ref, rst = oracle.get().greedy(g)
     cpu_s = time.perf_counter() - t0
-    same = bool(np.array_equal(ref, out.cpu().numpy()))
+    same = bool(np.array_equal(ref, out.cpu().numpy())) and bool(torch.equal(out, out2))
     # per round: row indices and weights read twice (24 B per entry) plus
     # about 40 B per column of per-round records and matching state
     alg_bytes = st["rounds"] * (24 * g.nnz + 40 * g.n)

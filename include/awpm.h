@@ -162,7 +162,13 @@ int awpm_destroy(awpm_ctx *ctx);
 int awpm_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *weight,
                  const int32_t *mate_in, int32_t *mate_out, awpm_stats *stats);
 
-/* awpm_improve on an explicit context (its device, stream, options). */
+/*
+ * awpm_improve on an explicit context (its device, stream, options).
+ * mate_in may be NULL: the heavy-weight greedy maximal matching (awpm_greedy)
+ * is computed first and, when it is perfect, improved; when it is not,
+ * AWPM_ERR_NOT_PERFECT is returned and mate_out holds the greedy matching
+ * (-1 for unmatched columns).  The greedy's statistics are not reported.
+ */
 int awpm_improve_ctx(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
                      const double *weight, const int32_t *mate_in, int32_t *mate_out,
                      awpm_stats *stats);

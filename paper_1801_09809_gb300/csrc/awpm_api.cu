@@ -457,7 +457,7 @@ void teardown_ctx(awpm_ctx *c)
                       &c->b_tilemat, &c->b_i32,  &c->b_u64,    &c->b_f64,    &c->s_colptr,
                       &c->s_rowidx, &c->s_w,     &c->s_mate,   &c->s_out,    &c->s_gain,
                       &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey,     &c->bloom,    &c->gckey,
-                      &c->gcpos,   &c->grkey,    &c->grcol};
+                      &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_work)
@@ -892,6 +892,33 @@ int awpm_improve_ctx(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int3
     r.weight = weight;
     r.mate_in = mate_in;
     r.mate_out = mate_out;
+    if (!mate_in && n > 0) {
+        // no matching given: start from the greedy maximal matching
+        if (!mate_out)
+            return AWPM_ERR_INVALID_ARG;
+        int32_t *gm = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            CUDA_TRY(cudaSetDevice(ctx->device));
+            AWPM_TRY(ensure(ctx, ctx->gmate, sizeof(int32_t) * (size_t)n));
+            gm = (int32_t *)ctx->gmate.p;
+        }
+        awpm_greedy_stats gs;
+        AWPM_TRY(awpm_greedy(ctx, n, colptr, rowidx, weight, gm, &gs));
+        if (gs.cardinality != n) {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            const int l_out = where(ctx, mate_out);
+            if (l_out < 0)
+                return AWPM_ERR_INVALID_ARG;
+            CUDA_TRY(cudaMemcpyAsync(mate_out, gm, sizeof(int32_t) * (size_t)n,
+                                     l_out == 1 ? cudaMemcpyDeviceToDevice
+                                                : cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+            CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            return AWPM_ERR_NOT_PERFECT;
+        }
+        r.mate_in = gm;
+    }
     return solve_sync(ctx, r, stats, nullptr);
 }
 
@@ -1007,9 +1034,16 @@ int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
     AWPM_TRY(ensure(c, c->ctl, sizeof(Ctl)));
     AWPM_TRY(ensure(c, c->wpart, sizeof(double) * kWsumBlocks));
     const Shape sh = shape_of(c, false, AWPM_LOOKUP_BSEARCH, true, ntiles);
-    cudaGraphExec_t &g = c->g_greedy[sh.search_waves - 1];
-    if (!g)
-        AWPM_TRY(build_greedy_graph(c, sh, &g));
+    // AWPM_FLAG_TIME_SEARCH: a host loop over the rounds (every kernel a
+    // separate stream launch, visible to profilers) instead of the graph
+    const bool host_loop = (c->opt.flags & AWPM_FLAG_TIME_SEARCH) != 0;
+    cudaGraphExec_t g = nullptr;
+    if (!host_loop) {
+        cudaGraphExec_t &gg = c->g_greedy[sh.search_waves - 1];
+        if (!gg)
+            AWPM_TRY(build_greedy_graph(c, sh, &gg));
+        g = gg;
+    }
     CUDA_TRY(cudaEventRecord(c->ev_a, c->stream));
     Work &wk = *c->h_work;
     std::memset(&wk, 0, sizeof(Work));
@@ -1035,7 +1069,25 @@ int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
     wk.grcol = (int32_t *)c->grcol.p;
     CUDA_TRY(cudaMemcpyAsync(c->d_work.p, c->h_work, sizeof(Work), cudaMemcpyHostToDevice,
                              c->stream));
-    CUDA_TRY(cudaGraphLaunch(g, c->stream));
+    if (host_loop) {
+        const Work *d = (const Work *)c->d_work.p;
+        Sink k;
+        k.stream = c->stream;
+        launch_greedy_init(d, sh, k);
+        for (int32_t round = 0; round < wk.max_passes; ++round) {
+            launch_greedy_round(d, sh, false, cudaGraphConditionalHandle(), k);
+            AWPM_TRY(check_sink(k));
+            CUDA_TRY(cudaMemcpyAsync(c->h_ctl, wk.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
+                                     c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            if (!c->h_ctl->active)
+                break;
+        }
+        launch_weight_sum(d, sh, true, k);
+        AWPM_TRY(check_sink(k));
+    } else {
+        CUDA_TRY(cudaGraphLaunch(g, c->stream));
+    }
     CUDA_TRY(cudaMemcpyAsync(mate_out, wk.mc, sizeof(int32_t) * n,
                              l_out == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              c->stream));

@@ -154,3 +154,34 @@ def test_greedy_then_improve(ctx, torch):
     out = np.empty(g.n, dtype=np.int32)
     s2 = awpm.awpm_improve_ctx(ctx, g.n, g.colptr, g.rowidx, g.weight, got, out)
     assert out.tolist() == ref.tolist() and s2["iterations"] == rst["iterations"]
+
+
+def test_improve_without_matching(ctx, torch):
+    """awpm_improve with no matching: greedy first, then the 4-cycle phase
+    when greedy is perfect; otherwise NOT_PERFECT and the greedy matching."""
+    g = blocks_for_pipeline(500, 8601)
+    gm, _ = oracle.get().greedy(g)
+    ref, rst, _ = oracle.get().improve(g, mate=gm)
+    out = np.empty(g.n, dtype=np.int32)
+    st = awpm.awpm_improve_ctx(ctx, g.n, g.colptr, g.rowidx, g.weight, None, out)
+    assert out.tolist() == ref.tolist() and st["cycles_applied"] == rst["cycles_applied"]
+    h = gen.rmat(1 << 12, 8, 8602)
+    hm, hst = oracle.get().greedy(h)
+    assert hst["cardinality"] < h.n
+    out = np.empty(h.n, dtype=np.int32)
+    with pytest.raises(awpm.AwpmError) as ei:
+        awpm.awpm_improve_ctx(ctx, h.n, h.colptr, h.rowidx, h.weight, None, out)
+    assert ei.value.name == "NOT_PERFECT"
+    assert out.tolist() == hm.tolist()
+
+
+def test_host_loop_mode(torch):
+    """Rounds launched from the host (AWPM_FLAG_TIME_SEARCH) give the graph's
+    result."""
+    c = awpm.awpm_create(device=0, flags=awpm.FLAG_TIME_SEARCH)
+    try:
+        for g in (gen.rmat(1 << 13, 16, 8701), gen.random_small(500, 0.05, 8702, integer_weights=True)):
+            check(c, g, torch)
+    finally:
+        awpm.awpm_destroy(c)
+
