@@ -457,7 +457,8 @@ void teardown_ctx(awpm_ctx *c)
                       &c->b_tilemat, &c->b_i32,  &c->b_u64,    &c->b_f64,    &c->s_colptr,
                       &c->s_rowidx, &c->s_w,     &c->s_mate,   &c->s_out,    &c->s_gain,
                       &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey,     &c->bloom,    &c->gckey,
-                      &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate};
+                      &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate,
+                      &c->gtdead};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_work)
@@ -1029,6 +1030,7 @@ int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
     AWPM_TRY(ensure(c, c->gcpos, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->grkey, sizeof(long long) * n));
     AWPM_TRY(ensure(c, c->grcol, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->gtdead, (size_t)ntiles + 1));
     AWPM_TRY(ensure(c, c->tile_col, sizeof(int32_t) * ((size_t)ntiles + 1)));
     AWPM_TRY(ensure(c, c->starts, sizeof(uint32_t) * (((size_t)nnz + 31) / 32 + 1)));
     AWPM_TRY(ensure(c, c->ctl, sizeof(Ctl)));
@@ -1067,6 +1069,7 @@ int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
     wk.gcpos = (int32_t *)c->gcpos.p;
     wk.grkey = (long long *)c->grkey.p;
     wk.grcol = (int32_t *)c->grcol.p;
+    wk.gtdead = (uint8_t *)c->gtdead.p;
     CUDA_TRY(cudaMemcpyAsync(c->d_work.p, c->h_work, sizeof(Work), cudaMemcpyHostToDevice,
                              c->stream));
     if (host_loop) {

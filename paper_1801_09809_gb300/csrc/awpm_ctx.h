@@ -93,7 +93,7 @@ struct awpm_ctx {
     // per-solve device workspace
     awpm::DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
     awpm::DevBuf winbits, wkey, bloom;
-    awpm::DevBuf gckey, gcpos, grkey, grcol;  // greedy matching records
+    awpm::DevBuf gckey, gcpos, grkey, grcol, gtdead;  // greedy matching records
     awpm::DevBuf gmate;                       // greedy start of awpm_improve_ctx
     awpm::DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
     // staging of host-resident arrays

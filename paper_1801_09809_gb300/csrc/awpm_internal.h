@@ -123,6 +123,7 @@ struct Work {
     int32_t *gcpos;
     long long *grkey;
     int32_t *grcol;
+    uint8_t *gtdead;    // per tile: every column of the tile is matched
 };
 
 // Launch shape of a context: fixed grids sized by the GPU, not the problem.

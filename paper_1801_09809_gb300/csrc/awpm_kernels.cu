@@ -1235,6 +1235,8 @@ __global__ void k_gm_reset(const Work *__restrict__ W)
     const int64_t words = ((int64_t)w.nnz + 31) / 32 + 1;
     for (int64_t x = gtid(); x < words; x += gstride())
         w.starts[x] = 0u;
+    for (int64_t x = gtid(); x < w.ntiles; x += gstride())
+        w.gtdead[x] = 0;
 }
 
 // Entry checks of the greedy input: row range, sortedness, finite weights.
@@ -1269,7 +1271,9 @@ __global__ void __launch_bounds__(kThreads) k_gm_check(const Work *__restrict__ 
 
 // Round, phase 1: the largest key among the free entries of every free
 // column (warp maximum per column segment, then a 64-bit atomic) and of
-// every free row (an atomic per entry, skipped when it cannot win).
+// every free row (an atomic per entry, skipped when it cannot win).  A tile
+// whose columns are all matched is marked dead and skipped from then on
+// (columns never become free again).
 __global__ void __launch_bounds__(kThreads) k_gm_max(const Work *__restrict__ W)
 {
     const Work &w = *W;
@@ -1278,14 +1282,22 @@ __global__ void __launch_bounds__(kThreads) k_gm_max(const Work *__restrict__ W)
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = gstride() >> 5;
     for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
+        if (w.gtdead[t])
+            continue;
         const int32_t base = (int32_t)(t * kTile);
         const int32_t p = base + lane;
         const bool valid = p < w.nnz;
         const int32_t c0 = __ldg(w.tile_col + t);
         const uint32_t mask = __ldg(w.starts + t);
         const int32_t j = valid ? lane_column(c0, mask, lane) : 0;
+        const bool cfree = valid && w.mc[j] < 0;
+        if (!__any_sync(FULL_MASK, cfree)) {
+            if (lane == 0)
+                w.gtdead[t] = 1;
+            continue;
+        }
         const int32_t i = valid ? __ldcs(w.rowidx + p) : 0;
-        const bool fr = valid && w.mc[j] < 0 && w.mr[i] < 0;
+        const bool fr = cfree && w.mr[i] < 0;
         long long key = fr ? order_key(__ldcs(w.w + p)) : kKeyNone;
         if (fr && key > *(volatile const long long *)(w.grkey + i))
             atomicMax(w.grkey + i, key);
@@ -1311,6 +1323,8 @@ __global__ void __launch_bounds__(kThreads) k_gm_min(const Work *__restrict__ W)
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = gstride() >> 5;
     for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
+        if (w.gtdead[t])
+            continue;
         const int32_t base = (int32_t)(t * kTile);
         const int32_t p = base + lane;
         const bool valid = p < w.nnz;
