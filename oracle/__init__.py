@@ -90,6 +90,13 @@ class Oracle:
                                      ctypes.c_int32]
         L.oracle_step_c.restype = ctypes.c_int
         L.oracle_step_c.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p, f64p, i32p, i64p]
+        L.oracle_pass_mode.restype = ctypes.c_int64
+        L.oracle_pass_mode.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p, i32p, f64p,
+                                       f64p, i32p, i32p, i64p, ctypes.c_int32]
+        L.oracle_improve_mode.restype = ctypes.c_int
+        L.oracle_improve_mode.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p, i32p,
+                                          ctypes.c_int32, ctypes.POINTER(_Stats), f64p, i64p,
+                                          ctypes.c_int32, ctypes.c_int32]
         L.oracle_greedy.restype = ctypes.c_int
         L.oracle_greedy.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p,
                                     ctypes.POINTER(_GreedyStats)]
@@ -102,19 +109,21 @@ class Oracle:
                                       _p(w, ctypes.c_double), _p(m, ctypes.c_int32))
         return ERRORS[rc]
 
-    def improve(self, g, mate=None, max_iters: int = 0, trace_cap: int = 0):
+    def improve(self, g, mate=None, max_iters: int = 0, trace_cap: int = 0, select: int = 0):
         """Run the phase; returns (mate_out, stats dict, trace) where trace is
-        (weights after each pass, cycles flipped in each pass) when trace_cap>0."""
+        (weights after each pass, cycles flipped in each pass) when trace_cap>0.
+        select: 0 = Step D of Algorithm 6, 1 = the Pettie-Sanders selection."""
         cp, ri, w = _arrs(g)
         m = np.ascontiguousarray(g.mate if mate is None else mate, dtype=np.int32)
         out = np.empty(max(g.n, 1), dtype=np.int32)
         st = _Stats()
         tw = np.zeros(max(trace_cap, 1), dtype=np.float64) if trace_cap else None
         tf = np.zeros(max(trace_cap, 1), dtype=np.int64) if trace_cap else None
-        rc = self.lib.oracle_improve(g.n, _p(cp, ctypes.c_int32), _p(ri, ctypes.c_int32),
-                                     _p(w, ctypes.c_double), _p(m, ctypes.c_int32),
-                                     _p(out, ctypes.c_int32), max_iters, ctypes.byref(st),
-                                     _p(tw, ctypes.c_double), _p(tf, ctypes.c_int64), trace_cap)
+        rc = self.lib.oracle_improve_mode(g.n, _p(cp, ctypes.c_int32), _p(ri, ctypes.c_int32),
+                                          _p(w, ctypes.c_double), _p(m, ctypes.c_int32),
+                                          _p(out, ctypes.c_int32), max_iters, ctypes.byref(st),
+                                          _p(tw, ctypes.c_double), _p(tf, ctypes.c_int64),
+                                          trace_cap, select)
         if rc != 0:
             raise OracleError(rc)
         stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
@@ -153,9 +162,9 @@ class Oracle:
             raise OracleError(rc)
         return gain[:g.n].copy(), row[:g.n].copy(), counts
 
-    def one_pass(self, g, mate=None):
+    def one_pass(self, g, mate=None, select: int = 0):
         """One pass of Steps A-D plus the flip; returns (new mate, step-D roots
-        per key column, counts[4])."""
+        per key column, counts[4]).  select as for improve()."""
         cp, ri, w = _arrs(g)
         m = np.ascontiguousarray(g.mate if mate is None else mate, dtype=np.int32)
         if self.validate(g, m) != "OK":
@@ -169,10 +178,11 @@ class Oracle:
         wm = w[np.searchsorted(keys, np.arange(n, dtype=np.int64) * n + mc)].copy()
         droot = np.zeros(max(n, 1), dtype=np.int32)
         counts = np.zeros(4, dtype=np.int64)
-        f = self.lib.oracle_pass(n, _p(cp, ctypes.c_int32), _p(ri, ctypes.c_int32),
-                                 _p(w, ctypes.c_double), _p(mc, ctypes.c_int32),
-                                 _p(mr, ctypes.c_int32), _p(wm, ctypes.c_double), None, None,
-                                 _p(droot, ctypes.c_int32), _p(counts, ctypes.c_int64))
+        f = self.lib.oracle_pass_mode(n, _p(cp, ctypes.c_int32), _p(ri, ctypes.c_int32),
+                                      _p(w, ctypes.c_double), _p(mc, ctypes.c_int32),
+                                      _p(mr, ctypes.c_int32), _p(wm, ctypes.c_double), None,
+                                      None, _p(droot, ctypes.c_int32),
+                                      _p(counts, ctypes.c_int64), select)
         if f < 0:
             raise OracleError(5)
         return mc[:n].copy(), droot[:n].copy(), counts

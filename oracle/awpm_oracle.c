@@ -159,9 +159,36 @@ static double matching_weight(int32_t n, const double *wm)
  *   counts[4]: candidates, closing_found, positive, flipped for this pass.
  * Returns the number of cycles flipped, or -1 on allocation failure.
  */
-int64_t oracle_pass(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
-                    int32_t *mc, int32_t *mr, double *wm,
-                    double *stepc_gain, int32_t *stepc_row, int32_t *stepd_root, int64_t *counts)
+/* One Step-C winner in the order of the Pettie-Sanders selection. */
+typedef struct {
+    double g;
+    int32_t j;
+    int64_t x;  /* its B-request */
+} ps_item;
+
+/* gain descending, then root column ascending */
+static int ps_cmp(const void *a, const void *b)
+{
+    const ps_item *p = (const ps_item *)a, *q = (const ps_item *)b;
+    if (p->g > q->g)
+        return -1;
+    if (p->g < q->g)
+        return 1;
+    return (p->j > q->j) - (p->j < q->j);
+}
+
+/*
+ * select_mode 0: Step D as in Algorithm 6 (above).
+ * select_mode 1: the Pettie-Sanders selection the paper describes in
+ * Section 4 instead of Step D: the Step-C winners S sorted by gain,
+ * descending (equal gains: lower root column first), each added to D(S)
+ * when none of its four vertices (columns j and k = m_i, rows i and m_j)
+ * belongs to a cycle added before.
+ */
+int64_t oracle_pass_mode(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+                         int32_t *mc, int32_t *mr, double *wm, double *stepc_gain,
+                         int32_t *stepc_row, int32_t *stepd_root, int64_t *counts,
+                         int32_t select_mode)
 {
     int64_t nnz = n > 0 ? colptr[n] : 0;
     a_request *areq = (a_request *)malloc(sizeof(a_request) * (size_t)(nnz > 0 ? nnz : 1));
@@ -234,16 +261,47 @@ int64_t oracle_pass(int32_t n, const int32_t *colptr, const int32_t *rowidx, con
      * a C-request whose key column k itself sent a C-request is dropped. */
     for (int32_t k = 0; k < n; ++k)
         dwin[k] = -1;
-    for (int32_t j = 0; j < n; ++j) {
-        if (cwin[j] < 0)
-            continue;
-        b_request *c = &breq[cwin[j]];
-        int32_t k = c->mi;
-        if (cwin[k] >= 0)
-            continue;
-        int64_t cur = dwin[k];
-        if (cur < 0 || c->g > breq[cur].g || (c->g == breq[cur].g && c->j < breq[cur].j))
-            dwin[k] = cwin[j];
+    if (select_mode == 0) {
+        for (int32_t j = 0; j < n; ++j) {
+            if (cwin[j] < 0)
+                continue;
+            b_request *c = &breq[cwin[j]];
+            int32_t k = c->mi;
+            if (cwin[k] >= 0)
+                continue;
+            int64_t cur = dwin[k];
+            if (cur < 0 || c->g > breq[cur].g || (c->g == breq[cur].g && c->j < breq[cur].j))
+                dwin[k] = cwin[j];
+        }
+    } else {
+        int64_t ns = 0;
+        ps_item *items = (ps_item *)malloc(sizeof(ps_item) * (size_t)(n > 0 ? n : 1));
+        char *used_col = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+        char *used_row = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+        if (!items || !used_col || !used_row) {
+            free(items); free(used_col); free(used_row);
+            free(areq); free(breq); free(cwin); free(dwin);
+            return -1;
+        }
+        for (int32_t j = 0; j < n; ++j)
+            if (cwin[j] >= 0) {
+                items[ns].g = breq[cwin[j]].g;
+                items[ns].j = j;
+                items[ns].x = cwin[j];
+                ++ns;
+            }
+        qsort(items, (size_t)ns, sizeof(ps_item), ps_cmp);
+        for (int64_t t = 0; t < ns; ++t) {
+            b_request *c = &breq[items[t].x];
+            if (used_col[c->j] || used_col[c->mi] || used_row[c->i] || used_row[c->mj])
+                continue;
+            used_col[c->j] = used_col[c->mi] = 1;
+            used_row[c->i] = used_row[c->mj] = 1;
+            dwin[c->mi] = items[t].x;
+        }
+        free(items);
+        free(used_col);
+        free(used_row);
     }
 
     if (stepc_gain || stepc_row) {
@@ -285,6 +343,14 @@ int64_t oracle_pass(int32_t n, const int32_t *colptr, const int32_t *rowidx, con
     return flipped;
 }
 
+int64_t oracle_pass(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+                    int32_t *mc, int32_t *mr, double *wm,
+                    double *stepc_gain, int32_t *stepc_row, int32_t *stepd_root, int64_t *counts)
+{
+    return oracle_pass_mode(n, colptr, rowidx, w, mc, mr, wm, stepc_gain, stepc_row, stepd_root,
+                            counts, 0);
+}
+
 /*
  * Whole phase (Algorithm 2): initialise mates and matched weights from
  * mate_in, run passes until one finds nothing (or max_iters passes ran),
@@ -292,9 +358,10 @@ int64_t oracle_pass(int32_t n, const int32_t *colptr, const int32_t *rowidx, con
  * trace_weight / trace_flips (capacity trace_cap, may be NULL) receive the
  * matching weight and the number of cycles flipped after each pass.
  */
-int oracle_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
-                   const int32_t *mate_in, int32_t *mate_out, int32_t max_iters,
-                   oracle_stats *st, double *trace_weight, int64_t *trace_flips, int32_t trace_cap)
+int oracle_improve_mode(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+                        const int32_t *mate_in, int32_t *mate_out, int32_t max_iters,
+                        oracle_stats *st, double *trace_weight, int64_t *trace_flips,
+                        int32_t trace_cap, int32_t select_mode)
 {
     oracle_stats s;
     memset(&s, 0, sizeof(s));
@@ -323,7 +390,8 @@ int oracle_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, cons
     int32_t cap = max_iters > 0 ? max_iters : ORACLE_PASS_CAP;
     for (int32_t it = 1; it <= cap; ++it) {
         int64_t counts[4];
-        int64_t f = oracle_pass(n, colptr, rowidx, w, mc, mr, wm, NULL, NULL, NULL, counts);
+        int64_t f = oracle_pass_mode(n, colptr, rowidx, w, mc, mr, wm, NULL, NULL, NULL, counts,
+                                     select_mode);
         if (f < 0) {
             rc = OR_OOM;
             break;
@@ -353,6 +421,14 @@ int oracle_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, cons
     free(mr);
     free(wm);
     return rc;
+}
+
+int oracle_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+                   const int32_t *mate_in, int32_t *mate_out, int32_t max_iters,
+                   oracle_stats *st, double *trace_weight, int64_t *trace_flips, int32_t trace_cap)
+{
+    return oracle_improve_mode(n, colptr, rowidx, w, mate_in, mate_out, max_iters, st,
+                               trace_weight, trace_flips, trace_cap, 0);
 }
 
 /*

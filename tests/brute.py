@@ -83,9 +83,12 @@ def positive_4cycles(g, mate):
     return out
 
 
-def one_pass_bruteforce(g, mate):
+def one_pass_bruteforce(g, mate, select=0):
     """One pass of Steps A-D and the flip, restated over the dense matrix with
-    sets and sorting: returns (new mate, flipped cycles as (root, key))."""
+    sets and sorting: returns (new mate, flipped cycles as (root, key)).
+    select=1 replaces Step D by the Pettie-Sanders selection: the Step-C
+    winners by gain, descending (equal gains: lower root), each kept when it
+    shares no vertex with a cycle kept before."""
     W, S = dense(g)
     n = g.n
     mc = np.array(mate, dtype=np.int64)
@@ -105,6 +108,23 @@ def one_pass_bruteforce(g, mate):
     # Step C: maximum gain per root, lowest row on ties
     cwin = {j: max(lst)[2:] for j, lst in cands.items()}           # j -> (i, k)
     cgain = {j: max(lst)[0] for j, lst in cands.items()}
+    if select == 1:
+        order = sorted(cwin, key=lambda j: (-cgain[j], j))
+        used_cols, used_rows = set(), set()
+        new = mc.copy()
+        flips = []
+        for j in order:
+            i, k = cwin[j]
+            verts_c, verts_r = {j, k}, {i, mc[j]}
+            if verts_c & used_cols or verts_r & used_rows:
+                continue
+            used_cols |= verts_c
+            used_rows |= verts_r
+            r = mc[j]
+            new[j] = i
+            new[k] = r
+            flips.append((j, k))
+        return new.astype(np.int32), sorted(flips)
     # Step D: drop if key is a Step-C root; maximum gain per key, lowest root on ties
     bykey = {}
     for j, (i, k) in cwin.items():

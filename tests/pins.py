@@ -256,6 +256,44 @@ def pin_rank_simulation(orc):
             assert cur.tolist() == out.tolist() and it + 1 == st["iterations"], (s, side)
 
 
+def pin_pettie_sanders_selection(orc):
+    """The Pettie-Sanders selection mode (Section 4: Step-C winners by gain,
+    each kept when disjoint from those kept before): one pass equals the
+    dense set-and-sort restatement (integer weights: ties); the kept cycles
+    are disjoint and maximal among the Step-C winners; whole runs end with
+    no positive-gain 4-cycle and a non-decreasing weight."""
+    rng = np.random.default_rng(6)
+    for s in range(60):
+        n = 3 + s % 6
+        g = gen.random_small(n, 0.7, 2600 + s, integer_weights=(s % 2 == 0))
+        mats = list(brute.all_perfect_matchings(g))
+        for m in [mats[x] for x in rng.choice(len(mats), size=min(4, len(mats)), replace=False)]:
+            new, flips = brute.one_pass_bruteforce(g, m, select=1)
+            got, droot, counts = orc.one_pass(g, m, select=1)
+            assert got.tolist() == new.tolist(), (s, m)
+            assert sorted((int(droot[k]), k) for k in range(n) if droot[k] >= 0) == flips
+    for s in range(6):
+        g = gen.random_small(150 + 50 * s, 0.05, 2700 + s, integer_weights=(s % 2 == 0))
+        gain, row, _ = orc.step_c(g)
+        _, droot, counts = orc.one_pass(g, select=1)
+        mc = g.mate
+        mr = np.empty(g.n, dtype=np.int64)
+        mr[mc] = np.arange(g.n)
+        roots = [j for j in range(g.n) if row[j] >= 0]
+        key = {j: int(mr[row[j]]) for j in roots}
+        kept = {int(droot[k]) for k in range(g.n) if droot[k] >= 0}
+        used = set()
+        for j in kept:
+            assert not ({j, key[j]} & used)
+            used |= {j, key[j]}
+        for j in roots:
+            if j not in kept:
+                assert {j, key[j]} & used, (s, j)
+        out, st, trace = orc.improve(g, select=1, trace_cap=64)
+        assert st["converged"] == 1 and brute.no_positive_4cycle_vectorized(g, out)
+        assert np.all(np.diff(np.concatenate([[st["weight_in"]], trace[0]])) >= 0)
+
+
 def pin_greedy_matching(orc):
     """Heavy-weight greedy maximal matching (Section 5.1): the round-based
     matching equals the textbook sequential greedy over the entries sorted by
@@ -357,4 +395,4 @@ def pin_paper_maxiters(orc):
 PINS = [pin_hand_cases, pin_2x2_closed_form, pin_block_diagonal, pin_six_cycle,
         pin_bruteforce_small, pin_one_pass_bruteforce, pin_rank_simulation,
         pin_local_optimality_midsize, pin_validation, pin_resume, pin_paper_maxiters,
-        pin_greedy_matching]
+        pin_pettie_sanders_selection, pin_greedy_matching]

@@ -33,7 +33,8 @@ MUTANTS = [
     ("step C tie to highest row", "breq[x].i < breq[cur].i", "breq[x].i > breq[cur].i"),
     ("step D tie to highest root", "c->j < breq[cur].j", "c->j > breq[cur].j"),
     ("step D keeps minimum", "c->g > breq[cur].g ||", "c->g < breq[cur].g ||"),
-    ("step D discard rule dropped", "if (cwin[k] >= 0)\n            continue;\n        int64_t cur = dwin[k];",
+    ("step D discard rule dropped",
+     "if (cwin[k] >= 0)\n                continue;\n            int64_t cur = dwin[k];",
      "int64_t cur = dwin[k];"),
     ("flip gives key column the wrong row", "mc[c.mi] = c.mj;", "mc[c.mi] = c.i;"),
     ("flip forgets the row side", "mr[c.mj] = c.mi;", "mr[c.mj] = c.j;"),
@@ -41,6 +42,13 @@ MUTANTS = [
     ("stops one pass early", "if (f == 0) {", "if (f <= 1) {"),
     ("duplicate mates accepted", "if (r < 0 || r >= n || seen[r] ||", "if (r < 0 || r >= n ||"),
     ("non-finite weights accepted", "if (!isfinite(w[p]))", "if (0)"),
+    ("Pettie-Sanders order ascending", "    if (p->g > q->g)\n        return -1;",
+     "    if (p->g < q->g)\n        return -1;"),
+    ("Pettie-Sanders tie to the highest root", "return (p->j > q->j) - (p->j < q->j);",
+     "return (p->j < q->j) - (p->j > q->j);"),
+    ("Pettie-Sanders ignores the key column",
+     "if (used_col[c->j] || used_col[c->mi] || used_row[c->i] || used_row[c->mj])",
+     "if (used_col[c->j] || used_row[c->mj])"),
     ("greedy column keeps the lightest", "if (cbest[j] < 0 || w[p] > w[cbest[j]])",
      "if (cbest[j] < 0 || w[p] < w[cbest[j]])"),
     ("greedy column tie to the highest row", "if (cbest[j] < 0 || w[p] > w[cbest[j]])",
