@@ -70,6 +70,22 @@ extern "C" {
                                  (nnz < 2^30; larger problems use the binary search,
                                  as awpm_stats.lookup_used reports)                    */
 
+/* awpm_options.select: how a pass turns its Step-C winners into the disjoint
+ * cycles it flips.
+ *   AWPM_SELECT_STEP_D (default): Step D of Algorithm 6 -- drop a winner whose
+ *     second matched edge is the root edge of another winner, keep per
+ *     remaining key column the largest gain (equal gains: lowest root).
+ *   AWPM_SELECT_GREEDY: the selection the paper attributes to Pettie and
+ *     Sanders (Section 4): the winners in order of gain, descending (equal
+ *     gains: lower root column first), each kept when it shares no vertex
+ *     with a cycle kept before.  On the GPU it is computed in rounds: every
+ *     column names the first remaining winner that touches it, and a winner
+ *     named by both of its columns is kept; the winners touching a kept
+ *     cycle are dropped.  Searches (awpm_search, awpm_search_noalloc) stop
+ *     before either selection. */
+#define AWPM_SELECT_STEP_D 0
+#define AWPM_SELECT_GREEDY 1
+
 /* awpm_options.flags */
 #define AWPM_FLAG_TIME_SEARCH 1u /* time every cycle-search launch with CUDA events
                                     (host-driven pass loop instead of one CUDA graph) */
@@ -89,7 +105,7 @@ typedef struct {
     size_t mem_budget_bytes;   /* device bytes the context may hold; 0 = unlimited;
                                   for the request server: all its slots together     */
     int32_t slots;             /* request server: concurrent solves (0 = 4)          */
-    int32_t reserved;
+    int32_t select;            /* AWPM_SELECT_*: how a pass picks disjoint cycles    */
 } awpm_options;
 
 /* One request of the request server (awpm_submit). */

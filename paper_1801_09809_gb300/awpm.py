@@ -19,6 +19,7 @@ AWPM_OK = 0
 ERRORS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_PERFECT", 3: "UNSORTED_OR_DUP", 4: "NONFINITE",
           5: "OOM", 6: "BUDGET", 7: "CUDA", 8: "TIMEOUT", 9: "NOT_FOUND", 10: "TOO_LARGE"}
 LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_HASH = 0, 1, 2
+SELECT_STEP_D, SELECT_GREEDY = 0, 1
 FLAG_TIME_SEARCH = 1
 PASS_CAP = 65536
 
@@ -27,7 +28,7 @@ class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("lookup", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("stream", ctypes.c_void_p), ("mem_budget_bytes", ctypes.c_size_t),
-                ("slots", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("slots", ctypes.c_int32), ("select", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
@@ -155,7 +156,8 @@ class Context:
 
 
 def awpm_create(device: int = -1, max_iters: int = 0, lookup: int = LOOKUP_AUTO,
-                flags: int = 0, stream=None, mem_budget_bytes: int = 0, slots: int = 0) -> Context:
+                flags: int = 0, stream=None, mem_budget_bytes: int = 0, slots: int = 0,
+                select: int = 0) -> Context:
     L = lib()
     o = Options()
     L.awpm_default_options(ctypes.byref(o))
@@ -163,6 +165,7 @@ def awpm_create(device: int = -1, max_iters: int = 0, lookup: int = LOOKUP_AUTO,
     o.stream = _stream_handle(stream)
     o.mem_budget_bytes = mem_budget_bytes
     o.slots = slots
+    o.select = select
     h = _VP()
     _check(L.awpm_create(ctypes.byref(h), ctypes.byref(o)))
     return Context(h.value)

@@ -151,6 +151,7 @@ Shape shape_of(const awpm_ctx *c, bool batch, int lookup, bool wide, int32_t nti
     sh.wide = wide;
     sh.search_bps = c->search_bps[batch ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0][wide ? 1 : 0];
     sh.search_waves = search_waves(sh.num_sms, sh.search_bps, ntiles);
+    sh.select = c->opt.select == AWPM_SELECT_GREEDY ? AWPM_SELECT_GREEDY : AWPM_SELECT_STEP_D;
     return sh;
 }
 
@@ -210,7 +211,41 @@ int build_graph(awpm_ctx *c, const Shape &sh, cudaGraphExec_t *out)
     }
     sb.graph = cp.conditional.phGraph_out[0];
     launch_search(d, sh, sb);
-    launch_select_and_flip(d, sh, sb);
+    if (sh.select == AWPM_SELECT_GREEDY) {
+        // the selection's rounds: a WHILE node nested in the pass body
+        cudaGraphConditionalHandle h2;
+        cudaGraphNodeParams cp2 = {cudaGraphNodeTypeConditional};
+        cudaGraphNode_t n_inner;
+        if ((e = cudaGraphConditionalHandleCreate(&h2, sb.graph, 0, 0)) != cudaSuccess) {
+            note_cuda_error(e, "inner conditional handle", __LINE__);
+            rc = AWPM_ERR_CUDA;
+            goto done;
+        }
+        launch_greedy_select_begin(d, sh, true, h2, sb);
+        cp2.conditional.handle = h2;
+        cp2.conditional.type = cudaGraphCondTypeWhile;
+        cp2.conditional.size = 1;
+        if (sb.err != cudaSuccess ||
+            (e = cudaGraphAddNode(&n_inner, sb.graph, &sb.last, nullptr, 1, &cp2)) !=
+                cudaSuccess) {
+            note_cuda_error(sb.err != cudaSuccess ? sb.err : e, "inner conditional node",
+                            __LINE__);
+            rc = AWPM_ERR_CUDA;
+            goto done;
+        }
+        Sink sr;
+        sr.graph = cp2.conditional.phGraph_out[0];
+        launch_greedy_select_round(d, sh, true, h2, sr);
+        if (sr.err != cudaSuccess) {
+            note_cuda_error(sr.err, "selection round nodes", __LINE__);
+            rc = AWPM_ERR_CUDA;
+            goto done;
+        }
+        sb.last = n_inner;
+        launch_greedy_select_end_and_flip(d, sh, sb);
+    } else {
+        launch_select_and_flip(d, sh, sb);
+    }
     launch_control(d, sh, true, h, sb);
     if (sb.err != cudaSuccess) {
         note_cuda_error(sb.err, "pass body nodes", __LINE__);
@@ -339,7 +374,25 @@ int run_timed(awpm_ctx *c, const Shape &sh, int max_passes, int *passes_enqueued
         CUDA_TRY(cudaEventRecord(c->tev[2 * t], s));
         launch_search(d, sh, k);
         CUDA_TRY(cudaEventRecord(c->tev[2 * t + 1], s));
-        launch_select_and_flip(d, sh, k);
+        if (sh.select == AWPM_SELECT_GREEDY) {
+            // the selection's rounds, driven from the host by the count of
+            // undecided winners
+            launch_greedy_select_begin(d, sh, false, cudaGraphConditionalHandle(), k);
+            for (;;) {
+                AWPM_TRY(check_sink(k));
+                CUDA_TRY(cudaMemcpyAsync(&c->h_ctl->live, &ctl->live, sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, s));
+                CUDA_TRY(cudaStreamSynchronize(s));
+                const int32_t live = c->h_ctl->live;
+                CUDA_TRY(cudaMemsetAsync(&ctl->live, 0, sizeof(int32_t), s));
+                if (live <= 0)
+                    break;
+                launch_greedy_select_round(d, sh, false, cudaGraphConditionalHandle(), k);
+            }
+            launch_greedy_select_end_and_flip(d, sh, k);
+        } else {
+            launch_select_and_flip(d, sh, k);
+        }
         launch_control(d, sh, false, cudaGraphConditionalHandle(), k);
         AWPM_TRY(check_sink(k));
         CUDA_TRY(cudaMemcpyAsync(&c->h_active[t % kRing], &ctl->active, sizeof(int32_t),
@@ -399,7 +452,8 @@ int setup_ctx(awpm_ctx *c, const awpm_options *opt)
         c->opt = *opt;
     else
         awpm_default_options(&c->opt);
-    if (c->opt.max_iters < 0 || c->opt.lookup < 0 || c->opt.lookup > 2 || c->opt.slots < 0)
+    if (c->opt.max_iters < 0 || c->opt.lookup < 0 || c->opt.lookup > 2 || c->opt.slots < 0 ||
+        c->opt.select < 0 || c->opt.select > 1)
         return AWPM_ERR_INVALID_ARG;
     int dev = c->opt.device;
     if (dev < 0)
@@ -442,10 +496,11 @@ void teardown_ctx(awpm_ctx *c)
         for (int h = 0; h < 2; ++h)
             for (int p = 0; p < 2; ++p)
                 for (int v = 0; v < 2; ++v)
-                    if (c->g_exec[b][h][p][v]) {
-                        cudaGraphExecDestroy(c->g_exec[b][h][p][v]);
-                        c->g_exec[b][h][p][v] = nullptr;
-                    }
+                    for (int q = 0; q < 2; ++q)
+                        if (c->g_exec[b][h][p][v][q]) {
+                            cudaGraphExecDestroy(c->g_exec[b][h][p][v][q]);
+                            c->g_exec[b][h][p][v][q] = nullptr;
+                        }
     for (int v = 0; v < 2; ++v)
         if (c->g_greedy[v]) {
             cudaGraphExecDestroy(c->g_greedy[v]);
@@ -458,7 +513,7 @@ void teardown_ctx(awpm_ctx *c)
                       &c->s_rowidx, &c->s_w,     &c->s_mate,   &c->s_out,    &c->s_gain,
                       &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey,     &c->bloom,    &c->gckey,
                       &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate,
-                      &c->gtdead};
+                      &c->gtdead,  &c->psel,     &c->pslive,   &c->pstaken,  &c->psused};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_work)
@@ -566,13 +621,20 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
         AWPM_TRY(ensure(c, c->htab, sizeof(unsigned long long) * 2 * (size_t)nnz));
     else
         AWPM_TRY(ensure(c, c->bloom, sizeof(uint32_t) * ((size_t)nnz / 4 + 1)));
+    const bool ps = c->opt.select == AWPM_SELECT_GREEDY && !r.search_only;
+    if (ps) {
+        AWPM_TRY(ensure(c, c->psel, sizeof(Sel) * n));
+        AWPM_TRY(ensure(c, c->pslive, sizeof(uint32_t) * ((size_t)n / 32 + 1)));
+        AWPM_TRY(ensure(c, c->pstaken, sizeof(uint32_t) * ((size_t)n / 32 + 1)));
+        AWPM_TRY(ensure(c, c->psused, sizeof(uint32_t) * ((size_t)n / 32 + 1)));
+    }
 
     // the solve graph of this launch shape, built once (before the timed span)
     const Shape sh = shape_of(c, count > 0, lookup, wide, ntiles);
     cudaGraphExec_t gexec = nullptr;
     if (!r.search_only && !timed) {
         cudaGraphExec_t &g = c->g_exec[count > 0 ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0]
-                                      [wide ? 1 : 0][sh.search_waves - 1];
+                                      [wide ? 1 : 0][sh.search_waves - 1][sh.select];
         if (!g)
             AWPM_TRY(build_graph(c, sh, &g));
         gexec = g;
@@ -597,6 +659,12 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     wk.colsig = (unsigned long long *)c->colsig.p;
     wk.htab = lookup == AWPM_LOOKUP_HASH ? (unsigned long long *)c->htab.p : nullptr;
     wk.bloom = lookup == AWPM_LOOKUP_HASH ? nullptr : (uint32_t *)c->bloom.p;
+    if (ps) {
+        wk.psel = (Sel *)c->psel.p;
+        wk.pslive = (uint32_t *)c->pslive.p;
+        wk.pstaken = (uint32_t *)c->pstaken.p;
+        wk.psused = (uint32_t *)c->psused.p;
+    }
     wk.best = (Rec *)c->best.p;
     wk.dsel = (Sel *)c->dsel.p;
     wk.winbits = (uint32_t *)c->winbits.p;
@@ -830,6 +898,7 @@ void awpm_default_options(awpm_options *opt)
     opt->stream = nullptr;
     opt->mem_budget_bytes = 0;
     opt->slots = 0;
+    opt->select = AWPM_SELECT_STEP_D;
 }
 
 int awpm_create(awpm_ctx **out, const awpm_options *opt)

@@ -95,6 +95,7 @@ struct awpm_ctx {
     awpm::DevBuf winbits, wkey, bloom;
     awpm::DevBuf gckey, gcpos, grkey, grcol, gtdead;  // greedy matching records
     awpm::DevBuf gmate;                       // greedy start of awpm_improve_ctx
+    awpm::DevBuf psel, pslive, pstaken, psused;  // greedy (Pettie-Sanders) selection
     awpm::DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
     // staging of host-resident arrays
     awpm::DevBuf s_colptr, s_rowidx, s_w, s_mate, s_out, s_gain, s_row;
@@ -107,8 +108,8 @@ struct awpm_ctx {
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     std::vector<cudaEvent_t> tev;     // timing pairs of the timed loop
     std::vector<cudaEvent_t> flagev;  // ring of the timed loop
-    // one instantiated graph per [batch][hash][wide][search waves - 1]
-    cudaGraphExec_t g_exec[2][2][2][2] = {};
+    // one instantiated graph per [batch][hash][wide][search waves - 1][select]
+    cudaGraphExec_t g_exec[2][2][2][2][2] = {};
     cudaGraphExec_t g_greedy[2] = {};  // greedy matching, [search waves - 1] of the shape
     std::map<uint64_t, awpm::TuneEntry> tune;  // autotuner state per problem class
     awpm::Pending pend;

@@ -53,7 +53,7 @@ struct Ctl {
     int32_t iterations;          // passes run
     int32_t converged;           // last pass flipped nothing
     int32_t max_passes;          // cap on passes
-    int32_t pad0;
+    int32_t live;                // greedy selection: winners still undecided
     unsigned long long pass_flips;   // cycles flipped in the running pass
     unsigned long long cycles;       // cycles flipped in total
     unsigned long long candidates;   // Step A requests (i > m_j)
@@ -124,6 +124,13 @@ struct Work {
     long long *grkey;
     int32_t *grcol;
     uint8_t *gtdead;    // per tile: every column of the tile is matched
+    // greedy (Pettie-Sanders) selection: per column the first remaining
+    // winner touching it; bitmaps of undecided and kept winners and of the
+    // columns of kept cycles
+    Sel *psel;
+    uint32_t *pslive;
+    uint32_t *pstaken;
+    uint32_t *psused;
 };
 
 // Launch shape of a context: fixed grids sized by the GPU, not the problem.
@@ -134,6 +141,7 @@ struct Shape {
     bool batch;
     bool wide;          // search kernel takes four tiles per warp round (else one)
     int search_waves;   // search grid = search_waves full waves of resident blocks
+    int select;         // AWPM_SELECT_STEP_D or AWPM_SELECT_GREEDY
 };
 
 constexpr int kWsumBlocks = 256;
@@ -156,6 +164,15 @@ void launch_init(const Work *d, const Shape &sh, Sink &k);
 void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k);
 void launch_search(const Work *d, const Shape &sh, Sink &k);
 void launch_select_and_flip(const Work *d, const Shape &sh, Sink &k);
+// Greedy selection: the kernels before the rounds (keys, undecided set,
+// condition of the rounds' loop), one round (the loop condition is set at
+// its end), and the kernels after (records for the flip).  With graph ==
+// false the conditions are not set; the host reads Ctl::live instead.
+void launch_greedy_select_begin(const Work *d, const Shape &sh, bool graph,
+                                cudaGraphConditionalHandle h, Sink &k);
+void launch_greedy_select_round(const Work *d, const Shape &sh, bool graph,
+                                cudaGraphConditionalHandle h, Sink &k);
+void launch_greedy_select_end_and_flip(const Work *d, const Shape &sh, Sink &k);
 void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,
                     Sink &k);
 void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k);

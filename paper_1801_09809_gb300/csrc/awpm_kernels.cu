@@ -334,6 +334,7 @@ __global__ void k_reset(const Work *__restrict__ W)
         c->active = 1;
         c->iterations = 0;
         c->converged = 0;
+        c->live = 0;
         c->max_passes = w.max_passes;
         c->pass_flips = 0ull;
         c->cycles = 0ull;
@@ -363,6 +364,15 @@ __global__ void k_reset(const Work *__restrict__ W)
     if (w.bloom)
         for (int64_t x = gtid(); x <= (int64_t)w.nnz / 4; x += gstride())
             w.bloom[x] = 0u;
+    if (w.psel) {
+        for (int64_t j = gtid(); j < w.n; j += gstride())
+            w.psel[j] = Sel{0.0, 0, 0};
+        for (int64_t x = gtid(); x <= w.n / 32; x += gstride()) {
+            w.pslive[x] = 0u;
+            w.pstaken[x] = 0u;
+            w.psused[x] = 0u;
+        }
+    }
     for (int64_t b = gtid(); b < w.bw.count; b += gstride()) {
         w.bw.mdone[b] = 0;
         w.bw.miter[b] = 0;
@@ -1181,6 +1191,178 @@ __global__ void k_export_stepc(const Work *__restrict__ W, double *gain, int32_t
 }
 
 // ---------------------------------------------------------------------------
+// Greedy (Pettie-Sanders) selection of the Step-C winners (Section 4)
+// ---------------------------------------------------------------------------
+// Instead of Step D: the winners in order of gain, descending (equal gains:
+// lower root column), each kept when its columns j and k = m_i -- hence also
+// its rows m_j and i -- belong to no cycle kept before.  Computed in rounds:
+// every column names the first undecided winner touching it (maximum gain,
+// then lowest root, through the 128-bit compare-and-swap of the Step-D
+// records); a winner named by both its columns is kept; undecided winners
+// touching a kept cycle are dropped.  The first undecided winner is always
+// named by both its columns, so every round decides at least one.  At the
+// end the kept winners are handed to k_flip exactly as Step D hands them:
+// the key column's record names the root, dropped winners get key -1.
+
+__device__ __forceinline__ void warp_add_i32(int v, int32_t *dst)
+{
+    v = __reduce_add_sync(FULL_MASK, v);
+    if ((threadIdx.x & 31) == 0 && v)
+        atomicAdd(dst, v);
+}
+
+// Keys of all winners; every winner undecided; their number into Ctl::live.
+__global__ void k_ps_begin(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    int live = 0;
+    if (gate(w.ctl)) {
+        const int64_t words = (int64_t)w.n / 32 + 1;
+        for (int64_t x = gtid(); x < words; x += gstride()) {
+            uint32_t bits = w.winbits[x];
+            w.pslive[x] = bits;
+            live += __popc(bits);
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int32_t j = (int32_t)(x * 32 + b);
+                w.wkey[j] = w.mr[w.rowidx[w.best[j].p]];
+            }
+        }
+    }
+    warp_add_i32(live, &w.ctl->live);
+}
+
+// Loop condition of the rounds: undecided winners remain (counter reset).
+__global__ void k_ps_cond(const Work *__restrict__ W, cudaGraphConditionalHandle h)
+{
+    Ctl *c = W->ctl;
+    const int32_t live = c->live;
+    c->live = 0;
+    cudaGraphSetConditional(h, (live > 0 && c->err == 0u && c->active) ? 1u : 0u);
+}
+
+// Round, step 1: every undecided winner names itself at both its columns.
+__global__ void k_ps_name(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (!gate(w.ctl))
+        return;
+    const int64_t words = (int64_t)w.n / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride()) {
+        uint32_t bits = w.pslive[x];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int32_t j = (int32_t)(x * 32 + b);
+            Sel s;
+            s.g = w.best[j].g;
+            s.j = j;
+            s.pad = 0;
+            sel_combine(w.psel + j, s, w.ctl);
+            sel_combine(w.psel + w.wkey[j], s, w.ctl);
+        }
+    }
+}
+
+// Round, step 2: a winner named by both its columns is kept; its columns
+// are marked used.
+__global__ void k_ps_take(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (!gate(w.ctl))
+        return;
+    const int64_t words = (int64_t)w.n / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride()) {
+        uint32_t bits = w.pslive[x];
+        uint32_t kept = 0u;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int32_t j = (int32_t)(x * 32 + b);
+            const int32_t k = w.wkey[j];
+            const Sel a = w.psel[j], c = w.psel[k];
+            if (gbits(a.g) > 0ll && a.j == j && gbits(c.g) > 0ll && c.j == j) {
+                kept |= 1u << b;
+                atomicOr(w.psused + (j >> 5), 1u << (j & 31));
+                atomicOr(w.psused + (k >> 5), 1u << (k & 31));
+            }
+        }
+        if (kept)
+            w.pstaken[x] |= kept;
+    }
+}
+
+// Round, step 3: clear the records this round touched; drop the undecided
+// winners that touch a used column; count the undecided ones left.
+__global__ void k_ps_prune(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    int live = 0;
+    if (gate(w.ctl)) {
+        const int64_t words = (int64_t)w.n / 32 + 1;
+        for (int64_t x = gtid(); x < words; x += gstride()) {
+            uint32_t bits = w.pslive[x];
+            if (!bits)
+                continue;
+            const uint32_t kept = w.pstaken[x];
+            uint32_t still = 0u;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int32_t j = (int32_t)(x * 32 + b);
+                const int32_t k = w.wkey[j];
+                w.psel[j] = Sel{0.0, 0, 0};
+                w.psel[k] = Sel{0.0, 0, 0};
+                if ((kept >> b) & 1u)
+                    continue;
+                const bool used = ((w.psused[j >> 5] >> (j & 31)) & 1u) ||
+                                  ((w.psused[k >> 5] >> (k & 31)) & 1u);
+                if (!used)
+                    still |= 1u << b;
+            }
+            w.pslive[x] = still;
+            live += __popc(still);
+        }
+    }
+    warp_add_i32(live, &w.ctl->live);
+}
+
+// After the rounds: kept winners get their key column's record (the form
+// k_flip reads), dropped ones key -1; the kept-set and used-column bitmaps
+// are cleared for the next pass.
+__global__ void k_ps_end(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (!gate(w.ctl))
+        return;
+    const int64_t words = (int64_t)w.n / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride()) {
+        uint32_t bits = w.winbits[x];
+        const uint32_t kept = w.pstaken[x];
+        if (kept)
+            w.pstaken[x] = 0u;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int32_t j = (int32_t)(x * 32 + b);
+            const int32_t k = w.wkey[j];
+            if ((kept >> b) & 1u) {
+                Sel s;
+                s.g = w.best[j].g;
+                s.j = j;
+                s.pad = 0;
+                w.dsel[k] = s;
+                atomicAnd(w.psused + (j >> 5), ~(1u << (j & 31)));
+                atomicAnd(w.psused + (k >> 5), ~(1u << (k & 31)));
+            } else {
+                w.wkey[j] = -1;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Heavy-weight greedy maximal matching (Section 5.1)
 // ---------------------------------------------------------------------------
 // The matching that greedy builds when it takes the stored entries from
@@ -1214,6 +1396,7 @@ __global__ void k_gm_reset(const Work *__restrict__ W)
         c->active = 1;
         c->iterations = 0;
         c->converged = 0;
+        c->live = 0;
         c->max_passes = w.max_passes;
         c->pass_flips = 0ull;
         c->cycles = 0ull;
@@ -1520,6 +1703,35 @@ int search_waves(int num_sms, int search_bps, int32_t ntiles)
 {
     const int64_t warps = (int64_t)num_sms * (search_bps > 0 ? search_bps : 1) * (kThreads / 32);
     return (int64_t)ntiles >= 64 * warps ? 2 : 1;
+}
+
+void launch_greedy_select_begin(const Work *d, const Shape &sh, bool graph,
+                                cudaGraphConditionalHandle h, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    void *ah[] = {(void *)&d, (void *)&h};
+    k.launch((const void *)k_ps_begin, tile_grid(sh), kThreads, a);
+    if (graph)
+        k.launch((const void *)k_ps_cond, 1, 1, ah);
+}
+
+void launch_greedy_select_round(const Work *d, const Shape &sh, bool graph,
+                                cudaGraphConditionalHandle h, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    void *ah[] = {(void *)&d, (void *)&h};
+    k.launch((const void *)k_ps_name, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_ps_take, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_ps_prune, tile_grid(sh), kThreads, a);
+    if (graph)
+        k.launch((const void *)k_ps_cond, 1, 1, ah);
+}
+
+void launch_greedy_select_end_and_flip(const Work *d, const Shape &sh, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_ps_end, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_flip, tile_grid(sh), kThreads, a);
 }
 
 void launch_select_and_flip(const Work *d, const Shape &sh, Sink &k)

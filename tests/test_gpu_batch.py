@@ -34,12 +34,12 @@ def run_batch(ctx, graphs, torch, host=False):
     return gen.split(n_off, out.cpu().numpy()), tot, pm
 
 
-def check_batch(ctx, graphs, torch, max_iters=0, host=False):
+def check_batch(ctx, graphs, torch, max_iters=0, host=False, select=0):
     mates, tot, pm = run_batch(ctx, graphs, torch, host=host)
     orc = oracle.get()
     passes = 0
     for b, g in enumerate(graphs):
-        ref, rst, _ = orc.improve(g, max_iters=max_iters)
+        ref, rst, _ = orc.improve(g, max_iters=max_iters, select=select)
         assert np.array_equal(mates[b], ref), (b, g.name)
         assert pm[b]["iterations"] == rst["iterations"], (b, g.name, pm[b], rst)
         assert pm[b]["converged"] == rst["converged"], (b, g.name)
@@ -133,3 +133,16 @@ def test_batch_rejects_cross_block_entries(torch):
             assert ei.value.name == "INVALID_ARG"
         finally:
             awpm.awpm_destroy(ctx)
+
+
+def test_batch_greedy_selection(torch):
+    """The Pettie-Sanders selection on a batch: cycles of different matrices
+    never share a column, so the union's selection is each matrix's own."""
+    graphs = [gen.build_spec(sp) for sp in gen.batch_spec(24, seed=6060)]
+    graphs += [gen.random_small(40, 0.2, 6100 + k, integer_weights=True) for k in range(8)]
+    ctx = awpm.awpm_create(device=0, select=awpm.SELECT_GREEDY)
+    try:
+        check_batch(ctx, graphs, torch, select=1)
+    finally:
+        awpm.awpm_destroy(ctx)
+

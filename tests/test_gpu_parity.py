@@ -369,3 +369,32 @@ def test_autotuner_trials_are_exact(torch, orc):
         assert_same_as_oracle(g2, got2, st2, ref2, rst2, "autotuned 2")
     finally:
         awpm.awpm_destroy(c)
+
+
+@pytest.mark.parametrize("flags", [0, awpm.FLAG_TIME_SEARCH], ids=["graph", "timed"])
+def test_greedy_selection(torch, orc, flags):
+    """The Pettie-Sanders selection instead of Step D (rounds of winners named
+    by both their columns; a WHILE node nested in the pass graph, or rounds
+    driven from the host): the oracle's result in that mode, ties included."""
+    c = awpm.awpm_create(device=0, select=awpm.SELECT_GREEDY, flags=flags)
+    try:
+        graphs = [gen.random_small(300, 0.2, 161, integer_weights=True), gen.config1(),
+                  gen.stencil_2d(60, 162), gen.stencil_3d(12, 163), gen.rmat(1 << 13, 16, 164),
+                  gen.banded(4000, 9, 165)]
+        graphs += [gen.random_small(8 + s, 0.7, 170 + s, integer_weights=True) for s in range(10)]
+        for g in graphs:
+            ref, rst, _ = orc.improve(g, select=1)
+            got, st = run_gpu(c, g, torch=torch)
+            assert_same_as_oracle(g, got, st, ref, rst, f"{g.name} select=greedy")
+        for mi in (1, 2):
+            g = gen.stencil_3d(10, 166)
+            c2 = awpm.awpm_create(device=0, select=awpm.SELECT_GREEDY, flags=flags, max_iters=mi)
+            try:
+                ref, rst, _ = orc.improve(g, select=1, max_iters=mi)
+                got, st = run_gpu(c2, g, torch=torch)
+                assert_same_as_oracle(g, got, st, ref, rst, f"max_iters={mi}")
+            finally:
+                awpm.awpm_destroy(c2)
+    finally:
+        awpm.awpm_destroy(c)
+
