@@ -333,6 +333,30 @@ def bench_greedy(awpm, torch, dev, g, reps=5):
             "identical_to_oracle": same}
 
 
+def bench_selection(awpm, torch, dev, reps=3):
+    """Step D against the Pettie-Sanders selection (awpm_options.select) on
+    the 27-point stencil, where many cycles compete: passes, cycles flipped,
+    final weight and solve time of each."""
+    from paper_1801_09809_gb300 import gen
+    g = gen.config3a()
+    t = [torch.from_numpy(a).to(dev) for a in (g.colptr, g.rowidx, g.weight, g.mate)]
+    out = torch.empty_like(t[3])
+    res = {}
+    for name, sel in (("step_d", awpm.SELECT_STEP_D), ("greedy", awpm.SELECT_GREEDY)):
+        ctx = awpm.awpm_create(device=dev.index or 0, lookup=awpm.LOOKUP_BSEARCH, select=sel)
+        st = awpm.awpm_improve_ctx(ctx, g.n, *t, out)
+        ms = []
+        for _ in range(reps):
+            st = awpm.awpm_improve_ctx(ctx, g.n, *t, out)
+            ms.append(st["ms_total"])
+        awpm.awpm_destroy(ctx)
+        res[name] = {"passes": st["iterations"], "cycles": st["cycles_applied"],
+                     "weight_in": st["weight_in"], "weight_out": st["weight_out"],
+                     "ms": statistics.median(ms)}
+    res["workload"] = "3D 27-point stencil 96^3 (n = 884,736), planted matching"
+    return res
+
+
 def bench_batched(awpm, torch, dev, count):
     """4,096 matrices (n log-uniform in [200, 20000], random sparse / 2D 5-point /
     banded): one batched graph launch vs one launch per matrix, same GPU,
@@ -623,6 +647,7 @@ def main():
     awpm.awpm_destroy(tctx)
     if not args.no_greedy:
         line["greedy"] = bench_greedy(awpm, torch, dev, g)
+        line["selection"] = bench_selection(awpm, torch, dev)
     if not args.no_batched:
         line["batched"] = bench_batched(awpm, torch, dev, args.batch_count)
     if not args.no_served:

@@ -97,6 +97,8 @@ class Oracle:
         L.oracle_improve_mode.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p, i32p,
                                           ctypes.c_int32, ctypes.POINTER(_Stats), f64p, i64p,
                                           ctypes.c_int32, ctypes.c_int32]
+        L.oracle_weights.restype = ctypes.c_int
+        L.oracle_weights.argtypes = [ctypes.c_int32, i32p, i32p, f64p, ctypes.c_int32, f64p]
         L.oracle_greedy.restype = ctypes.c_int
         L.oracle_greedy.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p,
                                     ctypes.POINTER(_GreedyStats)]
@@ -132,6 +134,19 @@ class Oracle:
             k = min(st.iterations, trace_cap)
             trace = (tw[:k].copy(), tf[:k].copy())
         return out[:g.n].copy(), stats, trace
+
+    def weights(self, n, colptr, rowidx, values, mode):
+        """Equilibrated weights from matrix values: mode 0 the scaled
+        magnitudes (Option A), mode 1 their logarithms (Option B)."""
+        cp = np.ascontiguousarray(colptr, dtype=np.int32)
+        ri = np.ascontiguousarray(rowidx, dtype=np.int32)
+        a = np.ascontiguousarray(values, dtype=np.float64)
+        out = np.empty(max(len(a), 1), dtype=np.float64)
+        rc = self.lib.oracle_weights(int(n), _p(cp, ctypes.c_int32), _p(ri, ctypes.c_int32),
+                                     _p(a, ctypes.c_double), int(mode), _p(out, ctypes.c_double))
+        if rc != 0:
+            raise OracleError(rc)
+        return out[:len(a)].copy()
 
     def greedy(self, g):
         """Heavy-weight greedy maximal matching: (mate_out with -1 for

@@ -570,3 +570,64 @@ int oracle_greedy(int32_t n, const int32_t *colptr, const int32_t *rowidx, const
     free(mc); free(mr); free(cbest); free(rbest); free(rbw);
     return OR_OK;
 }
+
+/*
+ * Matching weights from matrix values (Section 6.1, the experiments' setup):
+ * the matrix is equilibrated by diagonal scaling so that the largest
+ * magnitude in every row and column is at most 1 -- here one sweep, columns
+ * first (each column divided by its largest |a|), then rows (each row divided
+ * by its largest scaled magnitude), so every row's largest entry is exactly 1
+ * -- and the weight is the scaled magnitude (mode 0, Option A: maximise the
+ * sum) or its logarithm (mode 1, Option B: maximise the product).
+ *   v_ij = |a_ij| / max_k |a_kj|,  w_ij = v_ij / max_l v_il,  mode 1: log(w_ij)
+ * Values must be finite and nonzero (the paper removes explicit zeros).
+ */
+int oracle_weights(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *a,
+                   int32_t mode, double *w)
+{
+    if (n < 0 || (n > 0 && !colptr) || (mode != 0 && mode != 1))
+        return OR_INVALID_ARG;
+    if (n == 0)
+        return OR_OK;
+    if (colptr[0] != 0)
+        return OR_INVALID_ARG;
+    for (int32_t j = 0; j < n; ++j)
+        if (colptr[j + 1] < colptr[j])
+            return OR_INVALID_ARG;
+    int64_t nnz = colptr[n];
+    if (nnz > 0 && (!rowidx || !a || !w))
+        return OR_INVALID_ARG;
+    for (int64_t p = 0; p < nnz; ++p)
+        if (rowidx[p] < 0 || rowidx[p] >= n)
+            return OR_INVALID_ARG;
+    for (int64_t p = 0; p < nnz; ++p)
+        if (!isfinite(a[p]) || a[p] == 0.0)
+            return OR_NONFINITE;
+    double *cmax = (double *)calloc((size_t)n, sizeof(double));
+    double *rmax = (double *)calloc((size_t)n, sizeof(double));
+    if (!cmax || !rmax) {
+        free(cmax);
+        free(rmax);
+        return OR_OOM;
+    }
+    for (int32_t j = 0; j < n; ++j)
+        for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p)
+            if (fabs(a[p]) > cmax[j])
+                cmax[j] = fabs(a[p]);
+    for (int32_t j = 0; j < n; ++j)
+        for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+            double v = fabs(a[p]) / cmax[j];
+            if (v > rmax[rowidx[p]])
+                rmax[rowidx[p]] = v;
+        }
+    for (int32_t j = 0; j < n; ++j)
+        for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+            double v = fabs(a[p]) / cmax[j];
+            double x = v / rmax[rowidx[p]];
+            w[p] = mode == 0 ? x : log(x);
+        }
+    free(cmax);
+    free(rmax);
+    return OR_OK;
+}
+

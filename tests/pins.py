@@ -335,6 +335,44 @@ def pin_greedy_matching(orc):
     assert orc.greedy(full2(1.0, 3.0, 2.0, 1.0))[0].tolist() == [1, 0]
 
 
+def pin_weights(orc):
+    """Equilibrated weights (Section 6.1, Options A and B): a 2x2 by hand;
+    every row's largest weight is exactly 1 (log: 0) and no weight exceeds
+    it; scaling a column by a power of two changes nothing (exact in
+    binary floating point; columns are normalised first, so this holds for
+    column scalings); a diagonal matrix gives all ones; Option B is the
+    logarithm of Option A; zeros and non-finite values are rejected."""
+    import math
+    W = np.array([[2.0, 1.0], [4.0, -8.0]])
+    g = gen.from_dense(W, np.ones((2, 2), dtype=bool), [0, 1])
+    wa = orc.weights(2, g.colptr, g.rowidx, g.weight, 0)
+    assert wa.tolist() == [1.0, 1.0, 0.25, 1.0]      # column-major: (0,0),(1,0),(0,1),(1,1)
+    rng = np.random.default_rng(7)
+    for s in range(8):
+        h = gen.random_small(60 + 30 * s, 0.08, 3100 + s)
+        a = rng.standard_normal(h.nnz) * np.exp(rng.uniform(-20, 20, h.nnz))
+        wa = orc.weights(h.n, h.colptr, h.rowidx, a, 0)
+        wb = orc.weights(h.n, h.colptr, h.rowidx, a, 1)
+        col = np.repeat(np.arange(h.n), np.diff(h.colptr))
+        rowmax = np.full(h.n, -np.inf)
+        np.maximum.at(rowmax, h.rowidx, wa)
+        assert np.all(rowmax == 1.0) and np.all(wa <= 1.0) and np.all(wa > 0.0)
+        assert np.allclose(wb, np.log(wa), rtol=0, atol=1e-15)
+        sc = a * np.exp2(rng.integers(-30, 30, h.n))[col]
+        assert np.array_equal(orc.weights(h.n, h.colptr, h.rowidx, sc, 0), wa)
+    d = gen.from_dense(np.diag([3.0, -0.5, 7.0]), np.eye(3, dtype=bool), [0, 1, 2])
+    assert orc.weights(3, d.colptr, d.rowidx, d.weight, 0).tolist() == [1.0, 1.0, 1.0]
+    assert orc.weights(3, d.colptr, d.rowidx, d.weight, 1).tolist() == [0.0, 0.0, 0.0]
+    for bad in (0.0, math.inf, math.nan):
+        z = d.weight.copy()
+        z[1] = bad
+        try:
+            orc.weights(3, d.colptr, d.rowidx, z, 0)
+            raise AssertionError("bad value accepted")
+        except Exception as e:  # noqa: BLE001
+            assert getattr(e, "name", "") == "NONFINITE", e
+
+
 def pin_validation(orc):
     """Input checks: error classes for malformed inputs."""
     g = gen.random_small(5, 0.6, 3)
@@ -395,4 +433,4 @@ def pin_paper_maxiters(orc):
 PINS = [pin_hand_cases, pin_2x2_closed_form, pin_block_diagonal, pin_six_cycle,
         pin_bruteforce_small, pin_one_pass_bruteforce, pin_rank_simulation,
         pin_local_optimality_midsize, pin_validation, pin_resume, pin_paper_maxiters,
-        pin_pettie_sanders_selection, pin_greedy_matching]
+        pin_pettie_sanders_selection, pin_greedy_matching, pin_weights]

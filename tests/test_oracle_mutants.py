@@ -49,6 +49,10 @@ MUTANTS = [
     ("Pettie-Sanders ignores the key column",
      "if (used_col[c->j] || used_col[c->mi] || used_row[c->i] || used_row[c->mj])",
      "if (used_col[c->j] || used_row[c->mj])"),
+    ("weights skip the row normalisation", "double x = v / rmax[rowidx[p]];", "double x = v;"),
+    ("weights take the column maximum of signed values", "if (fabs(a[p]) > cmax[j])\n                cmax[j] = fabs(a[p]);",
+     "if (a[p] > cmax[j])\n                cmax[j] = fabs(a[p]);"),
+    ("weights accept zeros", "if (!isfinite(a[p]) || a[p] == 0.0)", "if (!isfinite(a[p]))"),
     ("greedy column keeps the lightest", "if (cbest[j] < 0 || w[p] > w[cbest[j]])",
      "if (cbest[j] < 0 || w[p] < w[cbest[j]])"),
     ("greedy column tie to the highest row", "if (cbest[j] < 0 || w[p] > w[cbest[j]])",
