@@ -269,6 +269,27 @@ int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
                 const double *weight, int32_t *mate_out, awpm_greedy_stats *stats);
 
 /*
+ * Matching weights from the values of a sparse matrix, as the paper prepares
+ * its inputs (Section 6.1): the matrix is equilibrated by diagonal scaling --
+ * one sweep, columns first: v_ij = |a_ij| / max_k |a_kj|, then rows:
+ * w_ij = v_ij / max_l v_il, so every row's largest entry is exactly 1 and no
+ * entry exceeds 1 -- and the weight is
+ *   AWPM_WEIGHTS_SUM (Option A, maximise the sum of weights): w_ij,
+ *   AWPM_WEIGHTS_PRODUCT (Option B, maximise the product): log(w_ij).
+ * colptr, rowidx: the pattern as for awpm_improve (rows need not be sorted
+ * here); values[nnz] finite and nonzero (the paper removes explicit zeros,
+ * otherwise AWPM_ERR_NONFINITE); weight_out[nnz]: host or device.  Option A
+ * uses only divisions and maxima, so it is bit-for-bit reproducible; Option
+ * B calls the device logarithm (within its documented error of the exact
+ * value).
+ */
+#define AWPM_WEIGHTS_SUM 0
+#define AWPM_WEIGHTS_PRODUCT 1
+
+int awpm_weights(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                 const double *values, int32_t mode, double *weight_out);
+
+/*
  * One cycle search from a given matching without flipping anything: Steps
  * A-C of a single pass (Algorithms 3-5).  For every column j,
  * stepc_gain[j] / stepc_row[j] receive the Step-C winner rooted at j (its gain

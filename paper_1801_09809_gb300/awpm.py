@@ -92,6 +92,7 @@ SIGNATURES = [
                                            ctypes.POINTER(Stats)]),
     ("awpm_greedy", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP,
                                    ctypes.POINTER(GreedyStats)]),
+    ("awpm_weights", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int32, _VP]),
 ]
 NOALLOC_MAX_N = 262144
 NOALLOC_MAX_NNZ = 4194304
@@ -223,6 +224,16 @@ def awpm_greedy(ctx: Context, n, colptr, rowidx, weight, mate_out) -> dict:
                              _ptr(weight, "float64"), _ptr(mate_out, "int32"),
                              ctypes.byref(st)))
     return st.as_dict()
+
+
+WEIGHTS_SUM, WEIGHTS_PRODUCT = 0, 1
+
+
+def awpm_weights(ctx: Context, n, colptr, rowidx, values, mode, weight_out) -> None:
+    """Equilibrated matching weights from matrix values into weight_out
+    (mode WEIGHTS_SUM: scaled magnitudes; WEIGHTS_PRODUCT: their logs)."""
+    _check(lib().awpm_weights(ctx.handle, int(n), _ptr(colptr, "int32"), _ptr(rowidx, "int32"),
+                              _ptr(values, "float64"), int(mode), _ptr(weight_out, "float64")))
 
 
 def awpm_search_noalloc(n, colptr, rowidx, weight, mate, stepc_gain, stepc_row,

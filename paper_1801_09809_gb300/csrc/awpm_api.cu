@@ -513,7 +513,8 @@ void teardown_ctx(awpm_ctx *c)
                       &c->s_rowidx, &c->s_w,     &c->s_mate,   &c->s_out,    &c->s_gain,
                       &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey,     &c->bloom,    &c->gckey,
                       &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate,
-                      &c->gtdead,  &c->psel,     &c->pslive,   &c->pstaken,  &c->psused};
+                      &c->gtdead,  &c->psel,     &c->pslive,   &c->pstaken,  &c->psused,
+                      &c->wt_cmax, &c->wt_rmax,  &c->wt_stage};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_work)
@@ -1179,6 +1180,70 @@ int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
     if (stats)
         *stats = S;
     return AWPM_OK;
+}
+
+int awpm_weights(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                 const double *values, int32_t mode, double *weight_out)
+{
+    if (!ctx || n < 0 || (n > 0 && !colptr) ||
+        (mode != AWPM_WEIGHTS_SUM && mode != AWPM_WEIGHTS_PRODUCT))
+        return AWPM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    awpm_ctx *c = ctx;
+    if (n == 0)
+        return AWPM_OK;
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int l_colptr = where(c, colptr), l_rowidx = where(c, rowidx), l_a = where(c, values),
+              l_out = where(c, weight_out);
+    if (l_colptr < 0 || l_rowidx < 0 || l_a < 0 || l_out < 0)
+        return AWPM_ERR_INVALID_ARG;
+    int32_t nnz = 0;
+    if (l_colptr == 1) {
+        CUDA_TRY(cudaMemcpyAsync(c->h_ctl, colptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        std::memcpy(&nnz, c->h_ctl, sizeof(int32_t));
+    } else {
+        nnz = colptr[n];
+    }
+    if (nnz < 0 || nnz > kMaxNnz || (nnz > 0 && (!rowidx || !values || !weight_out)))
+        return AWPM_ERR_INVALID_ARG;
+    const int32_t ntiles = (int32_t)(((int64_t)nnz + kTile - 1) / kTile);
+    AWPM_TRY(ensure(c, c->wt_cmax, sizeof(double) * n));
+    AWPM_TRY(ensure(c, c->wt_rmax, sizeof(unsigned long long) * n));
+    AWPM_TRY(ensure(c, c->ctl, sizeof(Ctl)));
+    double *dout = weight_out;
+    if (l_out != 1) {
+        AWPM_TRY(ensure(c, c->wt_stage, sizeof(double) * (size_t)nnz));
+        dout = (double *)c->wt_stage.p;
+    }
+    const Shape sh = shape_of(c, false, AWPM_LOOKUP_BSEARCH, true, ntiles);
+    Work &wk = *c->h_work;
+    std::memset(&wk, 0, sizeof(Work));
+    wk.n = n;
+    wk.nnz = nnz;
+    wk.ntiles = ntiles;
+    AWPM_TRY(stage_in(c, c->s_colptr, colptr, (size_t)n + 1, l_colptr, &wk.colptr));
+    AWPM_TRY(stage_in(c, c->s_rowidx, rowidx, (size_t)nnz, l_rowidx, &wk.rowidx));
+    AWPM_TRY(stage_in(c, c->s_w, values, (size_t)nnz, l_a, &wk.wt_a));
+    wk.wt_out = dout;
+    wk.wt_cmax = (double *)c->wt_cmax.p;
+    wk.wt_rmax = (unsigned long long *)c->wt_rmax.p;
+    wk.wt_mode = mode;
+    wk.ctl = (Ctl *)c->ctl.p;
+    CUDA_TRY(cudaMemcpyAsync(c->d_work.p, c->h_work, sizeof(Work), cudaMemcpyHostToDevice,
+                             c->stream));
+    Sink k;
+    k.stream = c->stream;
+    launch_weights((const Work *)c->d_work.p, sh, k);
+    AWPM_TRY(check_sink(k));
+    if (l_out != 1 && nnz > 0)
+        CUDA_TRY(cudaMemcpyAsync(weight_out, dout, sizeof(double) * (size_t)nnz,
+                                 cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->h_ctl, wk.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    // a column without entries is no error here (no matching is asked for)
+    return code_of(c->h_ctl->err & ~kErrNotPerfect);
 }
 
 int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,

@@ -131,6 +131,14 @@ struct Work {
     uint32_t *pslive;
     uint32_t *pstaken;
     uint32_t *psused;
+    // weights from matrix values: values, output, column maxima, row maxima
+    // (bit patterns of positive doubles), mode (0 scaled magnitude, 1 its log)
+    const double *wt_a;
+    double *wt_out;
+    double *wt_cmax;
+    unsigned long long *wt_rmax;
+    int32_t wt_mode;
+    int32_t wt_pad;
 };
 
 // Launch shape of a context: fixed grids sized by the GPU, not the problem.
@@ -173,6 +181,8 @@ void launch_greedy_select_begin(const Work *d, const Shape &sh, bool graph,
 void launch_greedy_select_round(const Work *d, const Shape &sh, bool graph,
                                 cudaGraphConditionalHandle h, Sink &k);
 void launch_greedy_select_end_and_flip(const Work *d, const Shape &sh, Sink &k);
+// Weights from matrix values (equilibration, Options A / B).
+void launch_weights(const Work *d, const Shape &sh, Sink &k);
 void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,
                     Sink &k);
 void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k);

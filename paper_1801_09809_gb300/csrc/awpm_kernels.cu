@@ -1570,6 +1570,112 @@ __global__ void k_gm_rows(const Work *__restrict__ W)
 }
 
 // ---------------------------------------------------------------------------
+// Matching weights from matrix values (Section 6.1)
+// ---------------------------------------------------------------------------
+// One sweep of max-equilibration, columns first: v_ij = |a_ij| / max_k |a_kj|,
+// w_ij = v_ij / max_l v_il, so every row's largest weight is exactly 1; the
+// weight is w (Option A, sum objective) or log(w) (Option B, product
+// objective).  Divisions and maxima are exact IEEE operations, so Option A
+// is bit-for-bit reproducible; Option B calls the device logarithm.  A warp
+// takes a column at a time.
+
+__device__ __forceinline__ bool wt_gate(const Ctl *ctl)
+{
+    return (*(volatile const unsigned *)&ctl->err & (kErrInvalid | kErrNonfinite)) == 0u;
+}
+
+// The control block (the only state besides the weights' own arrays).
+__global__ void k_wt_reset(const Work *__restrict__ W)
+{
+    Ctl *c = W->ctl;
+    c->err = 0u;
+    c->active = 1;
+}
+
+// Checks (rows in range; values finite and nonzero) and the column maxima;
+// clears the row maxima.
+__global__ void k_wt_colmax(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err & kErrInvalid)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t x = gtid(); x < w.n; x += gstride())
+        w.wt_rmax[x] = 0ull;
+    unsigned bits = 0;
+    for (int64_t j = gtid() >> 5; j < w.n; j += nwarps) {
+        const int32_t s = w.colptr[j], e = w.colptr[j + 1];
+        double m = 0.0;
+        for (int32_t p = s + lane; p < e; p += 32) {
+            const int32_t r = __ldcs(w.rowidx + p);
+            const double a = __ldcs(w.wt_a + p);
+            if (r < 0 || r >= w.n)
+                bits |= kErrInvalid;
+            const long long b = __double_as_longlong(a) & 0x7fffffffffffffffll;
+            if (b == 0ll || b >= 0x7ff0000000000000ll)
+                bits |= kErrNonfinite;
+            const double v = fabs(a);
+            if (v > m)
+                m = v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_down_sync(FULL_MASK, m, o);
+            if (y > m)
+                m = y;
+        }
+        if (lane == 0)
+            w.wt_cmax[j] = m;
+    }
+    bits = __reduce_or_sync(FULL_MASK, bits);
+    if (lane == 0 && bits)
+        raise_err(w.ctl, bits);
+}
+
+// Row maxima of the column-scaled magnitudes (positive doubles compare like
+// their bit patterns as unsigned integers).
+__global__ void k_wt_rowmax(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (!wt_gate(w.ctl))
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t j = gtid() >> 5; j < w.n; j += nwarps) {
+        const int32_t s = w.colptr[j], e = w.colptr[j + 1];
+        const double cm = w.wt_cmax[j];
+        for (int32_t p = s + lane; p < e; p += 32) {
+            const double v = fabs(w.wt_a[p]) / cm;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+            const int32_t r = w.rowidx[p];
+            if (b > *(volatile const unsigned long long *)(w.wt_rmax + r))
+                atomicMax(w.wt_rmax + r, b);
+        }
+    }
+}
+
+// The weights.
+__global__ void k_wt_out(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (!wt_gate(w.ctl))
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t j = gtid() >> 5; j < w.n; j += nwarps) {
+        const int32_t s = w.colptr[j], e = w.colptr[j + 1];
+        const double cm = w.wt_cmax[j];
+        for (int32_t p = s + lane; p < e; p += 32) {
+            const double v = fabs(w.wt_a[p]) / cm;
+            const double rm = __longlong_as_double((long long)w.wt_rmax[w.rowidx[p]]);
+            const double x = v / rm;
+            w.wt_out[p] = w.wt_mode ? log(x) : x;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launchers: fixed grids (a multiple of the SM count)
 // ---------------------------------------------------------------------------
 
@@ -1778,6 +1884,16 @@ void launch_greedy_round(const Work *d, const Shape &sh, bool graph, cudaGraphCo
     k.launch((const void *)k_gm_match, util_grid(sh), kThreads, a);
     k.launch((const void *)k_gm_rows, util_grid(sh), kThreads, a);
     launch_control(d, sh, graph, h, k);
+}
+
+void launch_weights(const Work *d, const Shape &sh, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_wt_reset, 1, 1, a);
+    k.launch((const void *)k_check_colptr, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_wt_colmax, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_wt_rowmax, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_wt_out, init_grid(sh), kThreads, a);
 }
 
 void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k)
