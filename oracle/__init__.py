@@ -99,6 +99,9 @@ class Oracle:
                                           ctypes.c_int32, ctypes.c_int32]
         L.oracle_weights.restype = ctypes.c_int
         L.oracle_weights.argtypes = [ctypes.c_int32, i32p, i32p, f64p, ctypes.c_int32, f64p]
+        L.oracle_mcm.restype = ctypes.c_int
+        L.oracle_mcm.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p,
+                                 ctypes.POINTER(ctypes.c_int32 * 2)]
         L.oracle_greedy.restype = ctypes.c_int
         L.oracle_greedy.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p,
                                     ctypes.POINTER(_GreedyStats)]
@@ -147,6 +150,20 @@ class Oracle:
         if rc != 0:
             raise OracleError(rc)
         return out[:len(a)].copy()
+
+    def mcm(self, g, mate=None):
+        """Maximum cardinality matching with the heavy-weight tie-break from
+        the matching `mate` (-1: unmatched; default empty): (mate_out, stats
+        {phases, cardinality})."""
+        cp, ri, w = _arrs(g)
+        m = (np.full(max(g.n, 1), -1, dtype=np.int32) if mate is None
+             else np.ascontiguousarray(mate, dtype=np.int32).copy())
+        st = (ctypes.c_int32 * 2)()
+        rc = self.lib.oracle_mcm(g.n, _p(cp, ctypes.c_int32), _p(ri, ctypes.c_int32),
+                                 _p(w, ctypes.c_double), _p(m, ctypes.c_int32), ctypes.byref(st))
+        if rc != 0:
+            raise OracleError(rc)
+        return m[:g.n], {"phases": st[0], "cardinality": st[1]}
 
     def greedy(self, g):
         """Heavy-weight greedy maximal matching: (mate_out with -1 for

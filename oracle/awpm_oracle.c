@@ -631,3 +631,154 @@ int oracle_weights(int32_t n, const int32_t *colptr, const int32_t *rowidx, cons
     return OR_OK;
 }
 
+/*
+ * Maximum cardinality matching with the heavy-weight tie-break (Section 5.2):
+ * augmenting paths searched from all free columns at once, breadth first,
+ * choosing heavier edges when several searches reach the same row.
+ *
+ * Reading (the paper gives the idea, not the steps): phases; in each phase
+ * every free column roots a search tree and the trees grow level by level.
+ * At a level every frontier column offers each of its rows that no tree has
+ * reached yet (through an unmatched edge); a row offered by several columns
+ * joins the tree of the column with the heaviest edge (equal weights: lower
+ * column).  A row so reached that is free ends an augmenting path of its
+ * tree; a tree takes, among the free rows it reaches at that level, the one
+ * with the heaviest last edge (equal weights: lower row) and stops growing.
+ * A reached row that is matched brings its matched column into the next
+ * frontier of its tree.  When no frontier remains, every tree with an end
+ * is augmented along its path (the trees are vertex-disjoint).  A phase that
+ * augments nothing ends the algorithm: no augmenting path is left, so the
+ * matching is maximum (Berge).
+ *
+ * mate[n] in/out: row of column j or -1 (a valid matching on entry).
+ */
+typedef struct {
+    int32_t phases;        /* phases run, the last one (augmenting nothing) included */
+    int32_t cardinality;
+} oracle_mcm_stats;
+
+int oracle_mcm(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
+               int32_t *mate, oracle_mcm_stats *st)
+{
+    int rc = validate_matrix(n, colptr, rowidx, w);
+    if (rc != OR_OK)
+        return rc;
+    if (n > 0 && !mate)
+        return OR_INVALID_ARG;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t *mc = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *mr = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *root = (int32_t *)malloc(sizeof(int32_t) * nn);    /* tree of a column */
+    int32_t *rpar = (int32_t *)malloc(sizeof(int32_t) * nn);    /* column that reached a row */
+    int32_t *front = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *next = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *tend = (int32_t *)malloc(sizeof(int32_t) * nn);    /* end row of a tree, or -1 */
+    double *tw = (double *)malloc(sizeof(double) * nn);         /* its last edge's weight */
+    int32_t *bestc = (int32_t *)malloc(sizeof(int32_t) * nn);   /* level: winning column */
+    double *bestw = (double *)malloc(sizeof(double) * nn);      /* level: its weight */
+    if (!mc || !mr || !root || !rpar || !front || !next || !tend || !tw || !bestc || !bestw) {
+        rc = OR_OOM;
+        goto out;
+    }
+    for (int32_t x = 0; x < n; ++x)
+        mr[x] = -1;
+    for (int32_t j = 0; j < n; ++j) {
+        int32_t r = mate[j];
+        if (r >= n || (r >= 0 && (mr[r] != -1 || find_entry(colptr, rowidx, r, j) < 0))) {
+            rc = OR_NOT_PERFECT;   /* not a matching over stored entries */
+            goto out;
+        }
+        mc[j] = r < 0 ? -1 : r;
+        if (r >= 0)
+            mr[r] = j;
+    }
+    oracle_mcm_stats S;
+    memset(&S, 0, sizeof(S));
+    for (;;) {
+        S.phases += 1;
+        int32_t nf = 0;
+        for (int32_t x = 0; x < n; ++x) {
+            rpar[x] = -1;
+            tend[x] = -1;
+            bestc[x] = -1;
+            if (mc[x] < 0) {
+                root[x] = x;
+                front[nf++] = x;
+            }
+        }
+        while (nf > 0) {
+            /* offers: for every row not yet reached, the heaviest offering
+             * edge, then the lowest column (frontier columns in any order) */
+            for (int32_t f = 0; f < nf; ++f) {
+                int32_t c = front[f];
+                for (int64_t p = colptr[c]; p < colptr[c + 1]; ++p) {
+                    int32_t r = rowidx[p];
+                    if (r == mc[c] || rpar[r] != -1)
+                        continue;
+                    if (bestc[r] < 0 || w[p] > bestw[r] || (w[p] == bestw[r] && c < bestc[r])) {
+                        bestc[r] = c;
+                        bestw[r] = w[p];
+                    }
+                }
+            }
+            /* rows join the winning column's tree */
+            int32_t nn2 = 0;
+            for (int32_t f = 0; f < nf; ++f) {
+                int32_t c = front[f];
+                for (int64_t p = colptr[c]; p < colptr[c + 1]; ++p) {
+                    int32_t r = rowidx[p];
+                    if (bestc[r] != c || rpar[r] != -1)
+                        continue;
+                    rpar[r] = c;
+                    bestc[r] = -1;
+                    int32_t t = root[c];
+                    if (mr[r] < 0) {
+                        if (tend[t] < 0 || w[p] > tw[t] || (w[p] == tw[t] && r < tend[t])) {
+                            tend[t] = r;
+                            tw[t] = w[p];
+                        }
+                    } else {
+                        int32_t c2 = mr[r];
+                        root[c2] = t;
+                        next[nn2++] = c2;
+                    }
+                }
+            }
+            /* trees with an end stop growing */
+            nf = 0;
+            for (int32_t f = 0; f < nn2; ++f)
+                if (tend[root[next[f]]] < 0)
+                    front[nf++] = next[f];
+        }
+        int32_t aug = 0;
+        for (int32_t t = 0; t < n; ++t) {
+            if (mc[t] >= 0 || tend[t] < 0)
+                continue;
+            int32_t r = tend[t];
+            for (;;) {
+                int32_t c = rpar[r];
+                int32_t old = mc[c];
+                mc[c] = r;
+                mr[r] = c;
+                if (old < 0)
+                    break;
+                r = old;
+            }
+            ++aug;
+        }
+        if (aug == 0)
+            break;
+    }
+    S.cardinality = 0;
+    for (int32_t j = 0; j < n; ++j) {
+        mate[j] = mc[j];
+        S.cardinality += mc[j] >= 0;
+    }
+    if (st)
+        *st = S;
+out:
+    free(mc); free(mr); free(root); free(rpar); free(front); free(next);
+    free(tend); free(tw); free(bestc); free(bestw);
+    return rc;
+}
+

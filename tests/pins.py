@@ -373,6 +373,52 @@ def pin_weights(orc):
             assert getattr(e, "name", "") == "NONFINITE", e
 
 
+def random_pattern(n, per_col, seed, integer_weights=False):
+    """Random sparse pattern without a planted matching (so possibly without
+    a perfect one): per_col uniform rows per column, duplicates merged."""
+    rng = np.random.default_rng(seed)
+    rows = rng.integers(0, n, n * per_col)
+    cols = np.repeat(np.arange(n), per_col)
+    colptr, rowidx = gen._csc_from_coo(n, rows, cols)
+    w = (rng.integers(0, 4, len(rowidx)).astype(np.float64) if integer_weights
+         else rng.standard_normal(len(rowidx)))
+    return gen.Graph(n, colptr, rowidx, w, np.arange(n, dtype=np.int32), f"pattern_{seed}")
+
+
+def pin_mcm(orc):
+    """Maximum cardinality matching (Section 5.2): its cardinality equals the
+    maximum from scipy's bipartite matching, from an empty start and from the
+    greedy matching; it is a matching over stored entries; columns matched on
+    entry stay matched; with one free column and two free rows, and with two
+    free columns offering one free row, the heavier edge is taken."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import maximum_bipartite_matching
+    cases = [random_pattern(60 + 40 * s, 1 + s % 3, 4200 + s, integer_weights=(s % 2 == 0))
+             for s in range(10)]
+    cases += [gen.rmat(1 << 11, 4, 4300), gen.random_small(300, 0.01, 4301)]
+    for g in cases:
+        A = csr_matrix((np.ones(g.nnz), g.rowidx, g.colptr), shape=(g.n, g.n))  # A^T as CSR
+        best = int(np.sum(maximum_bipartite_matching(A, perm_type="column") >= 0))
+        for start in (None, orc.greedy(g)[0]):
+            m, st = orc.mcm(g, start)
+            assert st["cardinality"] == best == int(np.sum(m >= 0)), (g.name, st, best)
+            rows = m[m >= 0]
+            assert len(set(rows.tolist())) == len(rows)
+            for j in np.nonzero(m >= 0)[0]:
+                assert m[j] in g.rowidx[g.colptr[j]:g.colptr[j + 1]]
+            if start is not None:
+                assert np.all(m[start >= 0] >= 0)
+    h = gen.from_dense(np.array([[1.0, 0.0], [5.0, 0.0]]), np.array([[True, False], [True, False]]),
+                       [0, 1])
+    m, _ = orc.mcm(h)
+    assert m.tolist() == [1, -1]
+    # two free columns offer the same free row: the heavier edge wins it
+    h2 = gen.from_dense(np.array([[1.0, 5.0], [0.0, 0.0]]),
+                        np.array([[True, True], [False, False]]), [0, 1])
+    m, _ = orc.mcm(h2)
+    assert m.tolist() == [-1, 0]
+
+
 def pin_validation(orc):
     """Input checks: error classes for malformed inputs."""
     g = gen.random_small(5, 0.6, 3)
@@ -433,4 +479,4 @@ def pin_paper_maxiters(orc):
 PINS = [pin_hand_cases, pin_2x2_closed_form, pin_block_diagonal, pin_six_cycle,
         pin_bruteforce_small, pin_one_pass_bruteforce, pin_rank_simulation,
         pin_local_optimality_midsize, pin_validation, pin_resume, pin_paper_maxiters,
-        pin_pettie_sanders_selection, pin_greedy_matching, pin_weights]
+        pin_pettie_sanders_selection, pin_greedy_matching, pin_weights, pin_mcm]

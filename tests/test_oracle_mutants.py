@@ -53,6 +53,14 @@ MUTANTS = [
     ("weights take the column maximum of signed values", "if (fabs(a[p]) > cmax[j])\n                cmax[j] = fabs(a[p]);",
      "if (a[p] > cmax[j])\n                cmax[j] = fabs(a[p]);"),
     ("weights accept zeros", "if (!isfinite(a[p]) || a[p] == 0.0)", "if (!isfinite(a[p]))"),
+    ("maximum matching offers prefer the lighter edge",
+     "if (bestc[r] < 0 || w[p] > bestw[r] || (w[p] == bestw[r] && c < bestc[r])) {",
+     "if (bestc[r] < 0 || w[p] < bestw[r] || (w[p] == bestw[r] && c < bestc[r])) {"),
+    ("maximum matching ends at the lowest free row",
+     "if (tend[t] < 0 || w[p] > tw[t] || (w[p] == tw[t] && r < tend[t])) {",
+     "if (tend[t] < 0 || r < tend[t]) {"),
+    ("maximum matching stops after one phase", "        if (aug == 0)\n            break;",
+     "        break;"),
     ("greedy column keeps the lightest", "if (cbest[j] < 0 || w[p] > w[cbest[j]])",
      "if (cbest[j] < 0 || w[p] < w[cbest[j]])"),
     ("greedy column tie to the highest row", "if (cbest[j] < 0 || w[p] > w[cbest[j]])",
