@@ -333,6 +333,46 @@ def bench_greedy(awpm, torch, dev, g, reps=5):
             "identical_to_oracle": same}
 
 
+def bench_pipeline(awpm, torch, dev, g, reps=3):
+    """The paper's whole pipeline from scratch on the bench graph: greedy
+    maximal matching, maximum cardinality matching to complete it, then the
+    4-cycle phase (awpm_improve_ctx with no matching).  Each step timed on
+    the device; the maximum matching compared with the oracle's (and the
+    oracle's time for that step, one host thread)."""
+    import oracle
+    ctx = awpm.awpm_create(device=dev.index or 0, lookup=awpm.LOOKUP_BSEARCH)
+    cp, ri, w = (torch.from_numpy(a).to(dev) for a in (g.colptr, g.rowidx, g.weight))
+    m = torch.empty(g.n, dtype=torch.int32, device=dev)
+    out = torch.empty_like(m)
+    rows = []
+    for _ in range(reps + 1):
+        gs = awpm.awpm_greedy(ctx, g.n, cp, ri, w, m)
+        ms = awpm.awpm_mcm(ctx, g.n, cp, ri, w, m)
+        mcm_out = m.cpu().numpy()
+        st = awpm.awpm_improve_ctx(ctx, g.n, cp, ri, w, m, out)
+        rows.append((gs["ms_total"], ms["ms_total"], st["ms_total"]))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        awpm.awpm_improve_ctx(ctx, g.n, cp, ri, w, None, out)
+        torch.cuda.synchronize()
+        rows[-1] = rows[-1] + (1e3 * (time.perf_counter() - t0),)
+    awpm.awpm_destroy(ctx)
+    rows = rows[1:]
+    med = [statistics.median(r[k] for r in rows) for k in range(4)]
+    orc = oracle.get()
+    gm, _ = orc.greedy(g)
+    t0 = time.perf_counter()
+    om, ost = orc.mcm(g, gm)
+    cpu_s = time.perf_counter() - t0
+    return {"workload": "greedy -> maximum matching -> 4-cycle phase, bench graph from scratch",
+            "greedy_cardinality": gs["cardinality"], "mcm_phases": ms["phases"],
+            "mcm_cardinality": ms["cardinality"], "passes": st["iterations"],
+            "greedy_ms": med[0], "mcm_ms": med[1], "improve_ms": med[2],
+            "pipeline_ms_host_clock": med[3],
+            "mcm_identical_to_oracle": bool(np.array_equal(om, mcm_out)),
+            "mcm_cpu_oracle_s": cpu_s, "mcm_speedup_vs_cpu_oracle": cpu_s / (med[1] * 1e-3)}
+
+
 def bench_selection(awpm, torch, dev, reps=3):
     """Step D against the Pettie-Sanders selection (awpm_options.select) on
     the 27-point stencil, where many cycles compete: passes, cycles flipped,
@@ -648,6 +688,7 @@ def main():
     if not args.no_greedy:
         line["greedy"] = bench_greedy(awpm, torch, dev, g)
         line["selection"] = bench_selection(awpm, torch, dev)
+        line["pipeline"] = bench_pipeline(awpm, torch, dev, g)
     if not args.no_batched:
         line["batched"] = bench_batched(awpm, torch, dev, args.batch_count)
     if not args.no_served:

@@ -180,10 +180,13 @@ int awpm_improve(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
 
 /*
  * awpm_improve on an explicit context (its device, stream, options).
- * mate_in may be NULL: the heavy-weight greedy maximal matching (awpm_greedy)
- * is computed first and, when it is perfect, improved; when it is not,
- * AWPM_ERR_NOT_PERFECT is returned and mate_out holds the greedy matching
- * (-1 for unmatched columns).  The greedy's statistics are not reported.
+ * mate_in may be NULL: the paper's whole pipeline then runs -- the
+ * heavy-weight greedy maximal matching (awpm_greedy), completed when it is
+ * not perfect by the maximum cardinality matching (awpm_mcm), then the
+ * 4-cycle phase.  When the matrix has no perfect matching,
+ * AWPM_ERR_NOT_PERFECT is returned and mate_out holds a maximum matching
+ * (-1 for unmatched columns).  The first two steps' statistics are not
+ * reported.
  */
 int awpm_improve_ctx(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
                      const double *weight, const int32_t *mate_in, int32_t *mate_out,
@@ -267,6 +270,34 @@ typedef struct {
 
 int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
                 const double *weight, int32_t *mate_out, awpm_greedy_stats *stats);
+
+/*
+ * Maximum cardinality matching with the heavy-weight tie-break (Section 5.2:
+ * augmenting paths, preferring heavier edges when several choices exist).
+ * mate[n] (host or device, in/out): a matching on entry (row of column j or
+ * -1, each row at most once, every pair a stored entry; all -1 is fine), a
+ * maximum matching on return that keeps every column matched on entry.
+ * Phases of breadth-first searches from all free columns: at each level a
+ * row offered by several columns goes to the heaviest edge (equal weights:
+ * lower column); a tree ends at the free row with the heaviest last edge
+ * (equal weights: lower row) and stops growing; all trees with an end are
+ * augmented; a phase that augments nothing ends the search.  Columns
+ * without entries are allowed (they stay unmatched).
+ *   stats (may be NULL): phases (the last, augmenting nothing, included),
+ *     cardinality, elapsed milliseconds.
+ * Errors: AWPM_ERR_INVALID_ARG, _UNSORTED_OR_DUP, _NONFINITE as for
+ * awpm_improve; AWPM_ERR_NOT_PERFECT when mate is not a matching over
+ * stored entries.
+ */
+typedef struct {
+    int32_t phases;
+    int32_t cardinality;
+    double ms_total;
+    int64_t reserved[2];
+} awpm_mcm_stats;
+
+int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
+             const double *weight, int32_t *mate, awpm_mcm_stats *stats);
 
 /*
  * Matching weights from the values of a sparse matrix, as the paper prepares

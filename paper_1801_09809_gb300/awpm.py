@@ -59,6 +59,14 @@ class GreedyStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class McmStats(ctypes.Structure):
+    _fields_ = [("phases", ctypes.c_int32), ("cardinality", ctypes.c_int32),
+                ("ms_total", ctypes.c_double), ("reserved", ctypes.c_int64 * 2)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class AwpmError(RuntimeError):
     def __init__(self, code: int, detail: str = ""):
         self.code = code
@@ -93,6 +101,8 @@ SIGNATURES = [
     ("awpm_greedy", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP,
                                    ctypes.POINTER(GreedyStats)]),
     ("awpm_weights", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int32, _VP]),
+    ("awpm_mcm", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP,
+                                ctypes.POINTER(McmStats)]),
 ]
 NOALLOC_MAX_N = 262144
 NOALLOC_MAX_NNZ = 4194304
@@ -223,6 +233,15 @@ def awpm_greedy(ctx: Context, n, colptr, rowidx, weight, mate_out) -> dict:
     _check(lib().awpm_greedy(ctx.handle, int(n), _ptr(colptr, "int32"), _ptr(rowidx, "int32"),
                              _ptr(weight, "float64"), _ptr(mate_out, "int32"),
                              ctypes.byref(st)))
+    return st.as_dict()
+
+
+def awpm_mcm(ctx: Context, n, colptr, rowidx, weight, mate) -> dict:
+    """Maximum cardinality matching (heavy-weight tie-break) in place in
+    `mate` (-1: unmatched)."""
+    st = McmStats()
+    _check(lib().awpm_mcm(ctx.handle, int(n), _ptr(colptr, "int32"), _ptr(rowidx, "int32"),
+                          _ptr(weight, "float64"), _ptr(mate, "int32"), ctypes.byref(st)))
     return st.as_dict()
 
 

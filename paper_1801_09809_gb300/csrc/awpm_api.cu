@@ -514,7 +514,9 @@ void teardown_ctx(awpm_ctx *c)
                       &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey,     &c->bloom,    &c->gckey,
                       &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate,
                       &c->gtdead,  &c->psel,     &c->pslive,   &c->pstaken,  &c->psused,
-                      &c->wt_cmax, &c->wt_rmax,  &c->wt_stage};
+                      &c->wt_cmax, &c->wt_rmax,  &c->wt_stage,
+                      &c->mroot,   &c->mrpar,    &c->mfront,   &c->mnext,    &c->mrkey,
+                      &c->mrcol,   &c->mtkey,    &c->mtrow,    &c->mstage};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_work)
@@ -976,7 +978,14 @@ int awpm_improve_ctx(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int3
         }
         awpm_greedy_stats gs;
         AWPM_TRY(awpm_greedy(ctx, n, colptr, rowidx, weight, gm, &gs));
-        if (gs.cardinality != n) {
+        int32_t card = gs.cardinality;
+        if (card != n) {
+            // greedy is not perfect: complete it with augmenting paths
+            awpm_mcm_stats ms;
+            AWPM_TRY(awpm_mcm(ctx, n, colptr, rowidx, weight, gm, &ms));
+            card = ms.cardinality;
+        }
+        if (card != n) {
             std::lock_guard<std::mutex> lk(ctx->mu);
             const int l_out = where(ctx, mate_out);
             if (l_out < 0)
@@ -1176,6 +1185,139 @@ int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
     S.rounds = h.iterations;
     S.cardinality = (int32_t)h.cycles;
     S.weight = h.weight_out;
+    S.ms_total = ms;
+    if (stats)
+        *stats = S;
+    return AWPM_OK;
+}
+
+int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
+             const double *weight, int32_t *mate, awpm_mcm_stats *stats)
+{
+    if (!ctx || n < 0 || (n > 0 && (!colptr || !mate)))
+        return AWPM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    awpm_ctx *c = ctx;
+    awpm_mcm_stats S;
+    std::memset(&S, 0, sizeof(S));
+    if (n == 0) {
+        S.phases = 1;
+        if (stats)
+            *stats = S;
+        return AWPM_OK;
+    }
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int l_colptr = where(c, colptr), l_rowidx = where(c, rowidx), l_w = where(c, weight),
+              l_m = where(c, mate);
+    if (l_colptr < 0 || l_rowidx < 0 || l_w < 0 || l_m < 0)
+        return AWPM_ERR_INVALID_ARG;
+    int32_t nnz = 0;
+    if (l_colptr == 1) {
+        CUDA_TRY(cudaMemcpyAsync(c->h_ctl, colptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        std::memcpy(&nnz, c->h_ctl, sizeof(int32_t));
+    } else {
+        nnz = colptr[n];
+    }
+    if (nnz < 0 || nnz > kMaxNnz || (nnz > 0 && (!rowidx || !weight)))
+        return AWPM_ERR_INVALID_ARG;
+    const int32_t ntiles = (int32_t)(((int64_t)nnz + kTile - 1) / kTile);
+    const size_t words = (size_t)n / 32 + 1;
+    AWPM_TRY(ensure(c, c->mc, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->mr, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->mroot, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->mrpar, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->mrcol, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->mtrow, sizeof(int32_t) * n));
+    AWPM_TRY(ensure(c, c->mrkey, sizeof(long long) * n));
+    AWPM_TRY(ensure(c, c->mtkey, sizeof(long long) * n));
+    AWPM_TRY(ensure(c, c->mfront, sizeof(uint32_t) * words));
+    AWPM_TRY(ensure(c, c->mnext, sizeof(uint32_t) * words));
+    AWPM_TRY(ensure(c, c->tile_col, sizeof(int32_t) * ((size_t)ntiles + 1)));
+    AWPM_TRY(ensure(c, c->starts, sizeof(uint32_t) * (((size_t)nnz + 31) / 32 + 1)));
+    AWPM_TRY(ensure(c, c->ctl, sizeof(Ctl)));
+    int32_t *dmate = mate;
+    if (l_m != 1) {
+        AWPM_TRY(ensure(c, c->mstage, sizeof(int32_t) * n));
+        dmate = (int32_t *)c->mstage.p;
+        CUDA_TRY(cudaMemcpyAsync(dmate, mate, sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                                 c->stream));
+    }
+    const Shape sh = shape_of(c, false, AWPM_LOOKUP_BSEARCH, true, ntiles);
+    CUDA_TRY(cudaEventRecord(c->ev_a, c->stream));
+    Work &wk = *c->h_work;
+    std::memset(&wk, 0, sizeof(Work));
+    wk.n = n;
+    wk.nnz = nnz;
+    wk.ntiles = ntiles;
+    AWPM_TRY(stage_in(c, c->s_colptr, colptr, (size_t)n + 1, l_colptr, &wk.colptr));
+    AWPM_TRY(stage_in(c, c->s_rowidx, rowidx, (size_t)nnz, l_rowidx, &wk.rowidx));
+    AWPM_TRY(stage_in(c, c->s_w, weight, (size_t)nnz, l_w, &wk.w));
+    wk.mc = (int32_t *)c->mc.p;
+    wk.mr = (int32_t *)c->mr.p;
+    wk.tile_col = (int32_t *)c->tile_col.p;
+    wk.starts = (uint32_t *)c->starts.p;
+    wk.ctl = (Ctl *)c->ctl.p;
+    wk.mroot = (int32_t *)c->mroot.p;
+    wk.mrpar = (int32_t *)c->mrpar.p;
+    wk.mfront = (uint32_t *)c->mfront.p;
+    wk.mnext = (uint32_t *)c->mnext.p;
+    wk.mrkey = (long long *)c->mrkey.p;
+    wk.mrcol = (int32_t *)c->mrcol.p;
+    wk.mtkey = (long long *)c->mtkey.p;
+    wk.mtrow = (int32_t *)c->mtrow.p;
+    wk.mmate = dmate;
+    CUDA_TRY(cudaMemcpyAsync(c->d_work.p, c->h_work, sizeof(Work), cudaMemcpyHostToDevice,
+                             c->stream));
+    const Work *d = (const Work *)c->d_work.p;
+    Ctl *dctl = (Ctl *)c->ctl.p;
+    Sink k;
+    k.stream = c->stream;
+    launch_mcm_load(d, sh, k);
+    AWPM_TRY(check_sink(k));
+    // read one counter of the control block, then zero it on the device
+    auto take = [&](void *field, size_t bytes, void *host) -> int {
+        CUDA_TRY(cudaMemcpyAsync(host, field, bytes, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(&c->h_ctl->err, &dctl->err, sizeof(unsigned),
+                                 cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        CUDA_TRY(cudaMemsetAsync(field, 0, bytes, c->stream));
+        return code_of(c->h_ctl->err);
+    };
+    unsigned long long have = 0;
+    AWPM_TRY(take(&dctl->cycles, sizeof(unsigned long long), &have));
+    unsigned long long total = have;
+    for (int32_t phase = 0; phase <= n; ++phase) {
+        S.phases += 1;
+        launch_mcm_phase(d, sh, k);
+        AWPM_TRY(check_sink(k));
+        for (int32_t level = 0; level <= n; ++level) {
+            int32_t live = 0;
+            AWPM_TRY(take(&dctl->live, sizeof(int32_t), &live));
+            if (live <= 0)
+                break;
+            launch_mcm_level(d, sh, k);
+            AWPM_TRY(check_sink(k));
+        }
+        launch_mcm_augment(d, sh, k);
+        AWPM_TRY(check_sink(k));
+        unsigned long long aug = 0;
+        AWPM_TRY(take(&dctl->pass_flips, sizeof(unsigned long long), &aug));
+        total += aug;
+        if (aug == 0)
+            break;
+    }
+    launch_mcm_store(d, sh, k);
+    AWPM_TRY(check_sink(k));
+    if (l_m != 1)
+        CUDA_TRY(cudaMemcpyAsync(mate, dmate, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                                 c->stream));
+    CUDA_TRY(cudaEventRecord(c->ev_b, c->stream));
+    CUDA_TRY(cudaEventSynchronize(c->ev_b));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev_a, c->ev_b));
+    S.cardinality = (int32_t)total;
     S.ms_total = ms;
     if (stats)
         *stats = S;

@@ -97,6 +97,7 @@ struct awpm_ctx {
     awpm::DevBuf gmate;                       // greedy start of awpm_improve_ctx
     awpm::DevBuf psel, pslive, pstaken, psused;  // greedy (Pettie-Sanders) selection
     awpm::DevBuf wt_cmax, wt_rmax, wt_stage;     // weights from matrix values
+    awpm::DevBuf mroot, mrpar, mfront, mnext, mrkey, mrcol, mtkey, mtrow, mstage;  // maximum matching
     awpm::DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
     // staging of host-resident arrays
     awpm::DevBuf s_colptr, s_rowidx, s_w, s_mate, s_out, s_gain, s_row;

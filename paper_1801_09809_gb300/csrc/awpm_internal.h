@@ -139,6 +139,18 @@ struct Work {
     unsigned long long *wt_rmax;
     int32_t wt_mode;
     int32_t wt_pad;
+    // maximum cardinality matching: tree of a column, column that reached a
+    // row, frontier bitmaps, per row the best offer (key, column), per tree
+    // its end (key of the last edge, row); mate in/out
+    int32_t *mroot;
+    int32_t *mrpar;
+    uint32_t *mfront;
+    uint32_t *mnext;
+    long long *mrkey;
+    int32_t *mrcol;
+    long long *mtkey;
+    int32_t *mtrow;
+    int32_t *mmate;
 };
 
 // Launch shape of a context: fixed grids sized by the GPU, not the problem.
@@ -183,6 +195,14 @@ void launch_greedy_select_round(const Work *d, const Shape &sh, bool graph,
 void launch_greedy_select_end_and_flip(const Work *d, const Shape &sh, Sink &k);
 // Weights from matrix values (equilibration, Options A / B).
 void launch_weights(const Work *d, const Shape &sh, Sink &k);
+// Maximum cardinality matching: load and check the starting matching; start
+// a phase (Ctl::live = free columns); one level of the searches (Ctl::live =
+// next frontier); augment (Ctl::pass_flips = paths augmented); write back.
+void launch_mcm_load(const Work *d, const Shape &sh, Sink &k);
+void launch_mcm_phase(const Work *d, const Shape &sh, Sink &k);
+void launch_mcm_level(const Work *d, const Shape &sh, Sink &k);
+void launch_mcm_augment(const Work *d, const Shape &sh, Sink &k);
+void launch_mcm_store(const Work *d, const Shape &sh, Sink &k);
 void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,
                     Sink &k);
 void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k);

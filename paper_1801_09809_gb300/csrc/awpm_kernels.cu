@@ -1676,6 +1676,295 @@ __global__ void k_wt_out(const Work *__restrict__ W)
 }
 
 // ---------------------------------------------------------------------------
+// Maximum cardinality matching with the heavy-weight tie-break (Section 5.2)
+// ---------------------------------------------------------------------------
+// Phases of breadth-first augmenting-path searches from every free column.
+// Per level, every frontier column offers its rows not reached yet (through
+// unmatched edges); a row goes to the offer with the heaviest edge, then the
+// lowest column (order keys, 64-bit atomics: maximum key, then minimum
+// column).  A free row so reached ends a path of its tree (the tree keeps
+// the heaviest last edge, then the lowest row, and stops growing); a
+// matched row brings its matched column into the next frontier.  The trees
+// are vertex-disjoint, so all paths found in a phase are augmented at once.
+// A phase that augments nothing ends the search: the matching is maximum.
+// The levels and phases are driven from the host through Ctl::live and
+// Ctl::pass_flips.
+
+// Clear the per-solve state; mr = -1.
+__global__ void k_mc_reset(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (gtid() == 0) {
+        Ctl *c = w.ctl;
+        c->err = 0u;
+        c->active = 1;
+        c->iterations = 0;
+        c->converged = 0;
+        c->live = 0;
+        c->pass_flips = 0ull;
+        c->cycles = 0ull;
+    }
+    for (int64_t x = gtid(); x < w.n; x += gstride())
+        w.mr[x] = -1;
+    const int64_t words = ((int64_t)w.nnz + 31) / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride())
+        w.starts[x] = 0u;
+}
+
+// A column without entries is no error for the maximum matching (it stays
+// unmatched): drop that report of the column-pointer check.
+__global__ void k_mc_allow_empty(const Work *__restrict__ W)
+{
+    atomicAnd(&W->ctl->err, ~kErrNotPerfect);
+}
+
+// The starting matching: row of every column or -1, each row once, every
+// pair a stored entry (binary search in the sorted column); its size.
+__global__ void k_mc_load(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    unsigned long long have = 0;
+    if (!w.ctl->err) {
+        for (int64_t j = gtid(); j < w.n; j += gstride()) {
+            const int32_t r = w.mmate[j];
+            w.mc[j] = r < 0 ? -1 : r;
+            if (r < 0)
+                continue;
+            if (r >= w.n || atomicCAS(&w.mr[r], -1, (int32_t)j) != -1) {
+                raise_err(w.ctl, kErrNotPerfect);
+                continue;
+            }
+            int32_t lo = w.colptr[j], len = w.colptr[j + 1] - lo;
+            while (len > 0) {
+                const int32_t half = len >> 1;
+                if (w.rowidx[lo + half] < r) {
+                    lo += half + 1;
+                    len -= half + 1;
+                } else {
+                    len = half;
+                }
+            }
+            if (lo >= w.colptr[j + 1] || w.rowidx[lo] != r)
+                raise_err(w.ctl, kErrNotPerfect);
+            ++have;
+        }
+    }
+    block_add_u64(have, &w.ctl->cycles);
+}
+
+// A phase: every free column roots a tree and forms the frontier; rows
+// unreached; offers and tree ends cleared.
+__global__ void k_mc_phase(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    int live = 0;
+    if (!w.ctl->err) {
+        for (int64_t x = gtid(); x < w.n; x += gstride()) {
+            w.mrpar[x] = -1;
+            w.mrkey[x] = kKeyNone;
+            w.mrcol[x] = 0x7fffffff;
+            w.mtkey[x] = kKeyNone;
+            w.mtrow[x] = 0x7fffffff;
+            if (w.mc[x] < 0)
+                w.mroot[x] = (int32_t)x;
+        }
+        const int64_t words = (int64_t)w.n / 32 + 1;
+        for (int64_t x = gtid(); x < words; x += gstride()) {
+            uint32_t bits = 0u;
+            for (int b = 0; b < 32; ++b) {
+                const int64_t j = x * 32 + b;
+                if (j < w.n && w.mc[j] < 0)
+                    bits |= 1u << b;
+            }
+            w.mfront[x] = bits;
+            w.mnext[x] = 0u;
+            live += __popc(bits);
+        }
+    }
+    warp_add_i32(live, &w.ctl->live);
+}
+
+// Level, step 1: the heaviest offer per unreached row.
+__global__ void k_mc_offer_max(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    const int64_t words = (int64_t)w.n / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride()) {
+        uint32_t bits = w.mfront[x];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int32_t c = (int32_t)(x * 32 + b);
+            const int32_t own = w.mc[c];
+            for (int32_t p = w.colptr[c]; p < w.colptr[c + 1]; ++p) {
+                const int32_t r = w.rowidx[p];
+                if (r == own || w.mrpar[r] != -1)
+                    continue;
+                const long long key = order_key(w.w[p]);
+                if (key > *(volatile const long long *)(w.mrkey + r))
+                    atomicMax(w.mrkey + r, key);
+            }
+        }
+    }
+}
+
+// Level, step 2: the lowest column among the heaviest offers.
+__global__ void k_mc_offer_min(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    const int64_t words = (int64_t)w.n / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride()) {
+        uint32_t bits = w.mfront[x];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int32_t c = (int32_t)(x * 32 + b);
+            const int32_t own = w.mc[c];
+            for (int32_t p = w.colptr[c]; p < w.colptr[c + 1]; ++p) {
+                const int32_t r = w.rowidx[p];
+                if (r == own || w.mrpar[r] != -1)
+                    continue;
+                if (order_key(w.w[p]) == w.mrkey[r] && c < *(volatile const int32_t *)(w.mrcol + r))
+                    atomicMin(w.mrcol + r, c);
+            }
+        }
+    }
+}
+
+// Level, step 3: rows join the winning column's tree; a free row is a
+// candidate end of the tree (heaviest last edge), a matched row brings its
+// column into the next frontier.
+__global__ void k_mc_join(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    const int64_t words = (int64_t)w.n / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride()) {
+        uint32_t bits = w.mfront[x];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int32_t c = (int32_t)(x * 32 + b);
+            const int32_t own = w.mc[c];
+            const int32_t t = w.mroot[c];
+            for (int32_t p = w.colptr[c]; p < w.colptr[c + 1]; ++p) {
+                const int32_t r = w.rowidx[p];
+                if (r == own || w.mrcol[r] != c || w.mrpar[r] != -1)
+                    continue;
+                w.mrpar[r] = c;
+                const long long key = order_key(w.w[p]);
+                w.mrkey[r] = kKeyNone;
+                w.mrcol[r] = 0x7fffffff;
+                const int32_t c2 = w.mr[r];
+                if (c2 < 0) {
+                    if (key > *(volatile const long long *)(w.mtkey + t))
+                        atomicMax(w.mtkey + t, key);
+                } else {
+                    w.mroot[c2] = t;
+                    atomicOr(w.mnext + (c2 >> 5), 1u << (c2 & 31));
+                }
+            }
+        }
+    }
+}
+
+// Level, step 4: among a tree's free rows with the heaviest last edge, the
+// lowest row is its end.
+__global__ void k_mc_end(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    const int64_t words = (int64_t)w.n / 32 + 1;
+    for (int64_t x = gtid(); x < words; x += gstride()) {
+        uint32_t bits = w.mfront[x];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int32_t c = (int32_t)(x * 32 + b);
+            const int32_t t = w.mroot[c];
+            for (int32_t p = w.colptr[c]; p < w.colptr[c + 1]; ++p) {
+                const int32_t r = w.rowidx[p];
+                if (w.mrpar[r] != c || w.mr[r] >= 0)
+                    continue;
+                if (order_key(w.w[p]) == w.mtkey[t] && r < *(volatile const int32_t *)(w.mtrow + t))
+                    atomicMin(w.mtrow + t, r);
+            }
+        }
+    }
+}
+
+// Level, step 5: the next frontier without the trees that have an end; its
+// size into Ctl::live.
+__global__ void k_mc_advance(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    int live = 0;
+    if (!w.ctl->err) {
+        const int64_t words = (int64_t)w.n / 32 + 1;
+        for (int64_t x = gtid(); x < words; x += gstride()) {
+            uint32_t bits = w.mnext[x];
+            uint32_t keep = 0u;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int32_t c = (int32_t)(x * 32 + b);
+                if (w.mtkey[w.mroot[c]] == kKeyNone)
+                    keep |= 1u << b;
+            }
+            w.mfront[x] = keep;
+            w.mnext[x] = 0u;
+            live += __popc(keep);
+        }
+    }
+    warp_add_i32(live, &w.ctl->live);
+}
+
+// Every tree with an end flips its path; their number into Ctl::pass_flips.
+__global__ void k_mc_augment(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    unsigned long long aug = 0;
+    if (!w.ctl->err) {
+        for (int64_t t = gtid(); t < w.n; t += gstride()) {
+            if (w.mc[t] >= 0 || w.mtrow[t] == 0x7fffffff)
+                continue;
+            int32_t r = w.mtrow[t];
+            for (int32_t guard = 0; guard <= w.n; ++guard) {
+                const int32_t c = w.mrpar[r];
+                if (c < 0) {  // a broken tree: report instead of walking on
+                    raise_err(w.ctl, kErrInternal);
+                    break;
+                }
+                const int32_t old = w.mc[c];
+                w.mc[c] = r;
+                w.mr[r] = c;
+                if (old < 0)
+                    break;
+                r = old;
+            }
+            ++aug;
+        }
+    }
+    block_add_u64(aug, &w.ctl->pass_flips);
+}
+
+// The result back into the caller's matching array.
+__global__ void k_mc_store(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    for (int64_t j = gtid(); j < w.n; j += gstride())
+        w.mmate[j] = w.mc[j];
+}
+
+// ---------------------------------------------------------------------------
 // launchers: fixed grids (a multiple of the SM count)
 // ---------------------------------------------------------------------------
 
@@ -1894,6 +2183,45 @@ void launch_weights(const Work *d, const Shape &sh, Sink &k)
     k.launch((const void *)k_wt_colmax, init_grid(sh), kThreads, a);
     k.launch((const void *)k_wt_rowmax, init_grid(sh), kThreads, a);
     k.launch((const void *)k_wt_out, init_grid(sh), kThreads, a);
+}
+
+void launch_mcm_load(const Work *d, const Shape &sh, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_mc_reset, util_grid(sh), kThreads, a);
+    k.launch((const void *)k_check_colptr, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_allow_empty, 1, 1, a);
+    k.launch((const void *)k_mark_starts, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_gm_check, init_tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_load, init_grid(sh), kThreads, a);
+}
+
+void launch_mcm_phase(const Work *d, const Shape &sh, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_mc_phase, util_grid(sh), kThreads, a);
+}
+
+void launch_mcm_level(const Work *d, const Shape &sh, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_mc_offer_max, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_offer_min, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_join, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_end, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_advance, util_grid(sh), kThreads, a);
+}
+
+void launch_mcm_augment(const Work *d, const Shape &sh, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_mc_augment, util_grid(sh), kThreads, a);
+}
+
+void launch_mcm_store(const Work *d, const Shape &sh, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    k.launch((const void *)k_mc_store, util_grid(sh), kThreads, a);
 }
 
 void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k)

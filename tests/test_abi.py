@@ -55,6 +55,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(awpm.Stats) == 8 + 40 + 32 + 8
     # awpm_greedy_stats: 2 int32 + 2 double + 2 int64
     assert ctypes.sizeof(awpm.GreedyStats) == 8 + 16 + 16
+    # awpm_mcm_stats: 2 int32 + double + 2 int64
+    assert ctypes.sizeof(awpm.McmStats) == 8 + 8 + 16
 
 
 def test_host_only_entry_points(built_lib):

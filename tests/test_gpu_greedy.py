@@ -157,22 +157,35 @@ def test_greedy_then_improve(ctx, torch):
 
 
 def test_improve_without_matching(ctx, torch):
-    """awpm_improve with no matching: greedy first, then the 4-cycle phase
-    when greedy is perfect; otherwise NOT_PERFECT and the greedy matching."""
+    """awpm_improve with no matching runs the pipeline: greedy, then the
+    maximum matching when greedy is not perfect, then the 4-cycle phase;
+    NOT_PERFECT with a maximum matching when no perfect one exists."""
+    orc = oracle.get()
     g = blocks_for_pipeline(500, 8601)
-    gm, _ = oracle.get().greedy(g)
-    ref, rst, _ = oracle.get().improve(g, mate=gm)
+    gm, _ = orc.greedy(g)
+    ref, rst, _ = orc.improve(g, mate=gm)
     out = np.empty(g.n, dtype=np.int32)
     st = awpm.awpm_improve_ctx(ctx, g.n, g.colptr, g.rowidx, g.weight, None, out)
     assert out.tolist() == ref.tolist() and st["cycles_applied"] == rst["cycles_applied"]
-    h = gen.rmat(1 << 12, 8, 8602)
-    hm, hst = oracle.get().greedy(h)
+    h = gen.rmat(1 << 12, 8, 8602)            # greedy is not perfect here, the maximum is
+    hm, hst = orc.greedy(h)
     assert hst["cardinality"] < h.n
+    mm, mst = orc.mcm(h, hm)
+    assert mst["cardinality"] == h.n
+    ref, rst, _ = orc.improve(h, mate=mm)
     out = np.empty(h.n, dtype=np.int32)
+    st = awpm.awpm_improve_ctx(ctx, h.n, h.colptr, h.rowidx, h.weight, None, out)
+    assert out.tolist() == ref.tolist() and st["iterations"] == rst["iterations"]
+    import pins
+    z = pins.random_pattern(2000, 2, 8603)   # no perfect matching
+    zm, zst = orc.greedy(z)
+    zm, zst = orc.mcm(z, zm)
+    assert zst["cardinality"] < z.n
+    out = np.empty(z.n, dtype=np.int32)
     with pytest.raises(awpm.AwpmError) as ei:
-        awpm.awpm_improve_ctx(ctx, h.n, h.colptr, h.rowidx, h.weight, None, out)
+        awpm.awpm_improve_ctx(ctx, z.n, z.colptr, z.rowidx, z.weight, None, out)
     assert ei.value.name == "NOT_PERFECT"
-    assert out.tolist() == hm.tolist()
+    assert out.tolist() == zm.tolist()
 
 
 def test_host_loop_mode(torch):
