@@ -114,10 +114,13 @@ class Oracle:
                                       _p(w, ctypes.c_double), _p(m, ctypes.c_int32))
         return ERRORS[rc]
 
-    def improve(self, g, mate=None, max_iters: int = 0, trace_cap: int = 0, select: int = 0):
+    def improve(self, g, mate=None, max_iters: int = 0, trace_cap: int = 0, select: int = 0,
+                row_marking: bool = False):
         """Run the phase; returns (mate_out, stats dict, trace) where trace is
         (weights after each pass, cycles flipped in each pass) when trace_cap>0.
-        select: 0 = Step D of Algorithm 6, 1 = the Pettie-Sanders selection."""
+        select: 0 = Step D of Algorithm 6, 1 = the Pettie-Sanders selection.
+        row_marking: closing entries found by marking row m_j's neighbourhood
+        (Section 4) instead of searching column m_i."""
         cp, ri, w = _arrs(g)
         m = np.ascontiguousarray(g.mate if mate is None else mate, dtype=np.int32)
         out = np.empty(max(g.n, 1), dtype=np.int32)
@@ -128,7 +131,7 @@ class Oracle:
                                           _p(w, ctypes.c_double), _p(m, ctypes.c_int32),
                                           _p(out, ctypes.c_int32), max_iters, ctypes.byref(st),
                                           _p(tw, ctypes.c_double), _p(tf, ctypes.c_int64),
-                                          trace_cap, select)
+                                          trace_cap, select | (2 if row_marking else 0))
         if rc != 0:
             raise OracleError(rc)
         stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
@@ -194,9 +197,9 @@ class Oracle:
             raise OracleError(rc)
         return gain[:g.n].copy(), row[:g.n].copy(), counts
 
-    def one_pass(self, g, mate=None, select: int = 0):
+    def one_pass(self, g, mate=None, select: int = 0, row_marking: bool = False):
         """One pass of Steps A-D plus the flip; returns (new mate, step-D roots
-        per key column, counts[4]).  select as for improve()."""
+        per key column, counts[4]).  select, row_marking as for improve()."""
         cp, ri, w = _arrs(g)
         m = np.ascontiguousarray(g.mate if mate is None else mate, dtype=np.int32)
         if self.validate(g, m) != "OK":
@@ -214,7 +217,8 @@ class Oracle:
                                       _p(w, ctypes.c_double), _p(mc, ctypes.c_int32),
                                       _p(mr, ctypes.c_int32), _p(wm, ctypes.c_double), None,
                                       None, _p(droot, ctypes.c_int32),
-                                      _p(counts, ctypes.c_int64), select)
+                                      _p(counts, ctypes.c_int64),
+                                      select | (2 if row_marking else 0))
         if f < 0:
             raise OracleError(5)
         return mc[:n].copy(), droot[:n].copy(), counts

@@ -178,12 +178,54 @@ static int ps_cmp(const void *a, const void *b)
 }
 
 /*
- * select_mode 0: Step D as in Algorithm 6 (above).
- * select_mode 1: the Pettie-Sanders selection the paper describes in
+ * Row marking (Section 4): the neighbourhood of row m_j -- the columns k with
+ * a stored (m_j, k) -- is marked once per root column j, and each candidate i
+ * of j then finds its closing entry (m_j, m_i) by reading the mark of column
+ * m_i.  The rows' neighbourhoods come from the transpose of the matrix (CSR),
+ * built here by a counting sort of the entries by row, which keeps each row's
+ * columns ascending.  rowptr[n+1]; rowpos[nnz], rowcol[nnz]: position in the
+ * CSC arrays and column of each entry, row by row.
+ */
+static int transpose_by_rows(int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                             int64_t **rowptr_out, int64_t **rowpos_out, int32_t **rowcol_out)
+{
+    int64_t nnz = n > 0 ? colptr[n] : 0;
+    int64_t *rowptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t *rowpos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    int32_t *rowcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!rowptr || !rowpos || !rowcol || !fill) {
+        free(rowptr); free(rowpos); free(rowcol); free(fill);
+        return -1;
+    }
+    for (int64_t p = 0; p < nnz; ++p)
+        rowptr[rowidx[p] + 1] += 1;
+    for (int32_t i = 0; i < n; ++i)
+        rowptr[i + 1] += rowptr[i];
+    for (int32_t i = 0; i < n; ++i)
+        fill[i] = rowptr[i];
+    for (int32_t j = 0; j < n; ++j)
+        for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+            rowpos[fill[rowidx[p]]] = p;
+            rowcol[fill[rowidx[p]]++] = j;
+        }
+    free(fill);
+    *rowptr_out = rowptr;
+    *rowpos_out = rowpos;
+    *rowcol_out = rowcol;
+    return 0;
+}
+
+/*
+ * select_mode bit 0 clear: Step D as in Algorithm 6 (above).
+ * select_mode bit 0 set: the Pettie-Sanders selection the paper describes in
  * Section 4 instead of Step D: the Step-C winners S sorted by gain,
  * descending (equal gains: lower root column first), each added to D(S)
  * when none of its four vertices (columns j and k = m_i, rows i and m_j)
  * belongs to a cycle added before.
+ * select_mode bit 1 set: Step B finds the closing entries by row marking
+ * (above) instead of searching column m_i; the entries found, and so every
+ * result, are the same.
  */
 int64_t oracle_pass_mode(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *w,
                          int32_t *mc, int32_t *mr, double *wm, double *stepc_gain,
@@ -200,6 +242,21 @@ int64_t oracle_pass_mode(int32_t n, const int32_t *colptr, const int32_t *rowidx
         return -1;
     }
     int64_t na = 0, nb = 0, nfound = 0;
+    const int row_marking = (select_mode & 2) != 0;
+    select_mode &= 1;
+    int64_t *rowptr = NULL, *rowpos = NULL, *mark_pos = NULL;
+    int32_t *rowcol = NULL, *mark_root = NULL;
+    if (row_marking) {
+        mark_pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+        mark_root = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        if (!mark_pos || !mark_root || transpose_by_rows(n, colptr, rowidx, &rowptr, &rowpos, &rowcol)) {
+            free(mark_pos); free(mark_root);
+            free(areq); free(breq); free(cwin); free(dwin);
+            return -1;
+        }
+        for (int32_t k = 0; k < n; ++k)
+            mark_root[k] = -1;
+    }
 
     /* Step A (Algorithm 3): every stored (i, j) with i > m_j asks the owner of
      * {m_j, m_i} to close the cycle i - j - m_j - m_i. */
@@ -225,7 +282,19 @@ int64_t oracle_pass_mode(int32_t n, const int32_t *colptr, const int32_t *rowidx
      * w(m_j, j) the matched weight of column j. */
     for (int64_t x = 0; x < na; ++x) {
         a_request a = areq[x];
-        int64_t q = find_entry(colptr, rowidx, a.mj, a.mi);
+        int64_t q;
+        if (row_marking) {
+            /* the A-requests come grouped by root column: mark row m_j's
+             * neighbourhood when a new root starts */
+            if (x == 0 || areq[x - 1].j != a.j)
+                for (int64_t t = rowptr[a.mj]; t < rowptr[a.mj + 1]; ++t) {
+                    mark_pos[rowcol[t]] = rowpos[t];
+                    mark_root[rowcol[t]] = a.j;
+                }
+            q = mark_root[a.mi] == a.j ? mark_pos[a.mi] : -1;
+        } else {
+            q = find_entry(colptr, rowidx, a.mj, a.mi);
+        }
         if (q < 0)
             continue;
         ++nfound;
@@ -336,6 +405,11 @@ int64_t oracle_pass_mode(int32_t n, const int32_t *colptr, const int32_t *rowidx
         counts[2] = nb;
         counts[3] = flipped;
     }
+    free(rowptr);
+    free(rowpos);
+    free(rowcol);
+    free(mark_pos);
+    free(mark_root);
     free(areq);
     free(breq);
     free(cwin);

@@ -294,6 +294,37 @@ def pin_pettie_sanders_selection(orc):
         assert np.all(np.diff(np.concatenate([[st["weight_in"]], trace[0]])) >= 0)
 
 
+def pin_row_marking(orc):
+    """Row marking (Section 4: the neighbourhood of row m_j marked once per
+    root, each candidate reads the mark of column m_i): one pass equals the
+    dense set-and-sort restatement under both selections (the dense view looks
+    entries up by (row, column), neither by column search nor by marks); a
+    whole run reaches the same matching, passes and counts as the column
+    search, on graphs with short and long rows."""
+    rng = np.random.default_rng(7)
+    for s in range(40):
+        n = 3 + s % 6
+        g = gen.random_small(n, 0.7, 2800 + s, integer_weights=(s % 2 == 0))
+        mats = list(brute.all_perfect_matchings(g))
+        for m in [mats[x] for x in rng.choice(len(mats), size=min(3, len(mats)), replace=False)]:
+            for sel in (0, 1):
+                new, flips = brute.one_pass_bruteforce(g, m, select=sel)
+                got, droot, counts = orc.one_pass(g, m, select=sel, row_marking=True)
+                assert got.tolist() == new.tolist(), (s, sel, m)
+                assert sorted((int(droot[k]), k) for k in range(n) if droot[k] >= 0) == flips
+    graphs = [gen.random_small(300 + 70 * s, 0.03, 2900 + s, integer_weights=(s % 2 == 0))
+              for s in range(4)]
+    graphs += [gen.rmat(1 << 10, 8, 2910), gen.stencil_2d(24, 2911)]
+    for g in graphs:
+        for sel in (0, 1):
+            a, sa, _ = orc.improve(g, select=sel)
+            b, sb, _ = orc.improve(g, select=sel, row_marking=True)
+            assert a.tolist() == b.tolist(), g.name
+            for f in ("iterations", "candidates", "closing_found", "positive",
+                      "cycles_applied"):
+                assert sa[f] == sb[f], (g.name, f)
+
+
 def pin_greedy_matching(orc):
     """Heavy-weight greedy maximal matching (Section 5.1): the round-based
     matching equals the textbook sequential greedy over the entries sorted by
@@ -479,4 +510,5 @@ def pin_paper_maxiters(orc):
 PINS = [pin_hand_cases, pin_2x2_closed_form, pin_block_diagonal, pin_six_cycle,
         pin_bruteforce_small, pin_one_pass_bruteforce, pin_rank_simulation,
         pin_local_optimality_midsize, pin_validation, pin_resume, pin_paper_maxiters,
-        pin_pettie_sanders_selection, pin_greedy_matching, pin_weights, pin_mcm]
+        pin_pettie_sanders_selection, pin_row_marking, pin_greedy_matching, pin_weights,
+        pin_mcm]

@@ -42,6 +42,13 @@ MUTANTS = [
     ("stops one pass early", "if (f == 0) {", "if (f <= 1) {"),
     ("duplicate mates accepted", "if (r < 0 || r >= n || seen[r] ||", "if (r < 0 || r >= n ||"),
     ("non-finite weights accepted", "if (!isfinite(w[p]))", "if (0)"),
+    ("row marking reads the root's own row", "for (int64_t t = rowptr[a.mj]; t < rowptr[a.mj + 1]; ++t) {",
+     "for (int64_t t = rowptr[a.i]; t < rowptr[a.i + 1]; ++t) {"),
+    ("row marking keeps stale marks", "q = mark_root[a.mi] == a.j ? mark_pos[a.mi] : -1;",
+     "q = mark_root[a.mi] >= 0 ? mark_pos[a.mi] : -1;"),
+    ("row marking marks once per pass", "if (x == 0 || areq[x - 1].j != a.j)", "if (x == 0)"),
+    ("transpose records the previous column", "rowpos[fill[rowidx[p]]] = p;\n            rowcol[fill[rowidx[p]]++] = j;",
+     "rowpos[fill[rowidx[p]]] = p;\n            rowcol[fill[rowidx[p]]++] = j > 0 ? j - 1 : j;"),
     ("Pettie-Sanders order ascending", "    if (p->g > q->g)\n        return -1;",
      "    if (p->g < q->g)\n        return -1;"),
     ("Pettie-Sanders tie to the highest root", "return (p->j > q->j) - (p->j < q->j);",
