@@ -366,6 +366,7 @@ def bench_pipeline(awpm, torch, dev, g, reps=3):
     cpu_s = time.perf_counter() - t0
     return {"workload": "greedy -> maximum matching -> 4-cycle phase, bench graph from scratch",
             "greedy_cardinality": gs["cardinality"], "mcm_phases": ms["phases"],
+            "mcm_levels": ms["levels"],
             "mcm_cardinality": ms["cardinality"], "passes": st["iterations"],
             "greedy_ms": med[0], "mcm_ms": med[1], "improve_ms": med[2],
             "pipeline_ms_host_clock": med[3],

@@ -284,7 +284,7 @@ int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
  * augmented; a phase that augments nothing ends the search.  Columns
  * without entries are allowed (they stay unmatched).
  *   stats (may be NULL): phases (the last, augmenting nothing, included),
- *     cardinality, elapsed milliseconds.
+ *     cardinality, elapsed milliseconds, search levels.
  * Errors: AWPM_ERR_INVALID_ARG, _UNSORTED_OR_DUP, _NONFINITE as for
  * awpm_improve; AWPM_ERR_NOT_PERFECT when mate is not a matching over
  * stored entries.
@@ -293,7 +293,8 @@ typedef struct {
     int32_t phases;
     int32_t cardinality;
     double ms_total;
-    int64_t reserved[2];
+    int64_t levels;        /* search levels over all phases */
+    int64_t reserved;
 } awpm_mcm_stats;
 
 int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,

@@ -61,7 +61,8 @@ class GreedyStats(ctypes.Structure):
 
 class McmStats(ctypes.Structure):
     _fields_ = [("phases", ctypes.c_int32), ("cardinality", ctypes.c_int32),
-                ("ms_total", ctypes.c_double), ("reserved", ctypes.c_int64 * 2)]
+                ("ms_total", ctypes.c_double), ("levels", ctypes.c_int64),
+                ("reserved", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -338,6 +338,97 @@ done:
     return rc;
 }
 
+// Graph of the maximum cardinality matching: load and checks; a WHILE node
+// over the phases whose body starts a phase, runs a WHILE node over the
+// levels, augments and decides whether to continue; the result stored.
+int build_mcm_graph(awpm_ctx *c, const Shape &sh, cudaGraphExec_t *out)
+{
+    const Work *d = (const Work *)c->d_work.p;
+    cudaGraph_t top = nullptr, g_init = nullptr, g_final = nullptr;
+    cudaGraphNode_t n_init, n_cond, n_final, n_inner;
+    cudaGraphConditionalHandle h1, h2;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cudaGraphNodeParams cp2 = {cudaGraphNodeTypeConditional};
+    int rc = AWPM_OK;
+    cudaError_t e;
+    Sink si, sf, sb, sl;
+    if ((e = cudaGraphCreate(&g_init, 0)) != cudaSuccess ||
+        (e = cudaGraphCreate(&g_final, 0)) != cudaSuccess ||
+        (e = cudaGraphCreate(&top, 0)) != cudaSuccess) {
+        note_cuda_error(e, "cudaGraphCreate", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    si.graph = g_init;
+    launch_mcm_load(d, sh, si);
+    sf.graph = g_final;
+    launch_mcm_store(d, sh, sf);
+    if (si.err != cudaSuccess || sf.err != cudaSuccess) {
+        note_cuda_error(si.err != cudaSuccess ? si.err : sf.err, "kernel nodes", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    if ((e = cudaGraphAddChildGraphNode(&n_init, top, nullptr, 0, g_init)) != cudaSuccess ||
+        (e = cudaGraphConditionalHandleCreate(&h1, top, 1, cudaGraphCondAssignDefault)) !=
+            cudaSuccess) {
+        note_cuda_error(e, "graph assembly", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    cp.conditional.handle = h1;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&n_cond, top, &n_init, nullptr, 1, &cp)) != cudaSuccess) {
+        note_cuda_error(e, "phase node", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    sb.graph = cp.conditional.phGraph_out[0];
+    if ((e = cudaGraphConditionalHandleCreate(&h2, sb.graph, 0, 0)) != cudaSuccess) {
+        note_cuda_error(e, "level handle", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    launch_mcm_phase(d, sh, sb);
+    launch_mcm_cond_level(d, sh, h2, sb);
+    cp2.conditional.handle = h2;
+    cp2.conditional.type = cudaGraphCondTypeWhile;
+    cp2.conditional.size = 1;
+    if (sb.err != cudaSuccess ||
+        (e = cudaGraphAddNode(&n_inner, sb.graph, &sb.last, nullptr, 1, &cp2)) != cudaSuccess) {
+        note_cuda_error(sb.err != cudaSuccess ? sb.err : e, "level node", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    sl.graph = cp2.conditional.phGraph_out[0];
+    launch_mcm_level(d, sh, sl);
+    launch_mcm_cond_level(d, sh, h2, sl);
+    sb.last = n_inner;
+    launch_mcm_augment(d, sh, sb);
+    launch_mcm_cond_phase(d, sh, h1, sb);
+    if (sb.err != cudaSuccess || sl.err != cudaSuccess) {
+        note_cuda_error(sb.err != cudaSuccess ? sb.err : sl.err, "phase body nodes", __LINE__);
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+    if ((e = cudaGraphAddChildGraphNode(&n_final, top, &n_cond, 1, g_final)) != cudaSuccess ||
+        (e = cudaGraphInstantiate(out, top, 0)) != cudaSuccess) {
+        note_cuda_error(e, "graph instantiation", __LINE__);
+        *out = nullptr;
+        rc = AWPM_ERR_CUDA;
+        goto done;
+    }
+done:
+    if (top)
+        cudaGraphDestroy(top);
+    if (g_init)
+        cudaGraphDestroy(g_init);
+    if (g_final)
+        cudaGraphDestroy(g_final);
+    cudaGetLastError();
+    return rc;
+}
+
 int ensure_timing_events(awpm_ctx *c, size_t pairs)
 {
     while (c->tev.size() < 2 * pairs) {
@@ -501,11 +592,16 @@ void teardown_ctx(awpm_ctx *c)
                             cudaGraphExecDestroy(c->g_exec[b][h][p][v][q]);
                             c->g_exec[b][h][p][v][q] = nullptr;
                         }
-    for (int v = 0; v < 2; ++v)
+    for (int v = 0; v < 2; ++v) {
         if (c->g_greedy[v]) {
             cudaGraphExecDestroy(c->g_greedy[v]);
             c->g_greedy[v] = nullptr;
         }
+        if (c->g_mcm[v]) {
+            cudaGraphExecDestroy(c->g_mcm[v]);
+            c->g_mcm[v] = nullptr;
+        }
+    }
     DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->wmr,
                       &c->colsig,  &c->best,     &c->dsel,     &c->tile_col, &c->starts,
                       &c->ctl,     &c->wpart,    &c->htab,     &c->b_noff,   &c->b_colmat,
@@ -516,7 +612,8 @@ void teardown_ctx(awpm_ctx *c)
                       &c->gtdead,  &c->psel,     &c->pslive,   &c->pstaken,  &c->psused,
                       &c->wt_cmax, &c->wt_rmax,  &c->wt_stage,
                       &c->mroot,   &c->mrpar,    &c->mfront,   &c->mnext,    &c->mrkey,
-                      &c->mrcol,   &c->mtkey,    &c->mtrow,    &c->mstage};
+                      &c->mrcol,   &c->mtkey,    &c->mtrow,    &c->mstage,   &c->mcolof,
+                      &c->mtiles};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_work)
@@ -1233,7 +1330,9 @@ int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *row
     AWPM_TRY(ensure(c, c->mrkey, sizeof(long long) * n));
     AWPM_TRY(ensure(c, c->mtkey, sizeof(long long) * n));
     AWPM_TRY(ensure(c, c->mfront, sizeof(uint32_t) * words));
+    AWPM_TRY(ensure(c, c->mcolof, sizeof(int32_t) * ((size_t)nnz + 1)));
     AWPM_TRY(ensure(c, c->mnext, sizeof(uint32_t) * words));
+    AWPM_TRY(ensure(c, c->mtiles, sizeof(int32_t) * ((size_t)ntiles + 1)));
     AWPM_TRY(ensure(c, c->tile_col, sizeof(int32_t) * ((size_t)ntiles + 1)));
     AWPM_TRY(ensure(c, c->starts, sizeof(uint32_t) * (((size_t)nnz + 31) / 32 + 1)));
     AWPM_TRY(ensure(c, c->ctl, sizeof(Ctl)));
@@ -1268,10 +1367,39 @@ int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *row
     wk.mtkey = (long long *)c->mtkey.p;
     wk.mtrow = (int32_t *)c->mtrow.p;
     wk.mmate = dmate;
+    wk.mcolof = (int32_t *)c->mcolof.p;
+    wk.mtiles = (int32_t *)c->mtiles.p;
     CUDA_TRY(cudaMemcpyAsync(c->d_work.p, c->h_work, sizeof(Work), cudaMemcpyHostToDevice,
                              c->stream));
     const Work *d = (const Work *)c->d_work.p;
     Ctl *dctl = (Ctl *)c->ctl.p;
+    if (!(c->opt.flags & AWPM_FLAG_TIME_SEARCH)) {
+        // the whole search in one graph launch (loops on the device)
+        cudaGraphExec_t &g = c->g_mcm[sh.search_waves - 1];
+        if (!g)
+            AWPM_TRY(build_mcm_graph(c, sh, &g));
+        CUDA_TRY(cudaGraphLaunch(g, c->stream));
+        if (l_m != 1)
+            CUDA_TRY(cudaMemcpyAsync(mate, dmate, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                                     c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->h_ctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaEventRecord(c->ev_b, c->stream));
+        CUDA_TRY(cudaEventSynchronize(c->ev_b));
+        const int rc = code_of(c->h_ctl->err);
+        if (rc != AWPM_OK)
+            return rc;
+        float gms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&gms, c->ev_a, c->ev_b));
+        S.phases = c->h_ctl->iterations;
+        S.cardinality = (int32_t)c->h_ctl->cycles;
+        S.levels = (int64_t)c->h_ctl->levels;
+        S.ms_total = gms;
+        if (stats)
+            *stats = S;
+        return AWPM_OK;
+    }
+    // AWPM_FLAG_TIME_SEARCH: levels and phases driven from the host
     Sink k;
     k.stream = c->stream;
     launch_mcm_load(d, sh, k);
@@ -1297,6 +1425,7 @@ int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *row
             AWPM_TRY(take(&dctl->live, sizeof(int32_t), &live));
             if (live <= 0)
                 break;
+            S.levels += 1;
             launch_mcm_level(d, sh, k);
             AWPM_TRY(check_sink(k));
         }

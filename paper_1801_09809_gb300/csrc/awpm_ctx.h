@@ -97,7 +97,8 @@ struct awpm_ctx {
     awpm::DevBuf gmate;                       // greedy start of awpm_improve_ctx
     awpm::DevBuf psel, pslive, pstaken, psused;  // greedy (Pettie-Sanders) selection
     awpm::DevBuf wt_cmax, wt_rmax, wt_stage;     // weights from matrix values
-    awpm::DevBuf mroot, mrpar, mfront, mnext, mrkey, mrcol, mtkey, mtrow, mstage;  // maximum matching
+    awpm::DevBuf mroot, mrpar, mfront, mnext, mrkey, mrcol, mtkey, mtrow, mstage,
+        mcolof, mtiles;  // maximum matching
     awpm::DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
     // staging of host-resident arrays
     awpm::DevBuf s_colptr, s_rowidx, s_w, s_mate, s_out, s_gain, s_row;
@@ -113,6 +114,7 @@ struct awpm_ctx {
     // one instantiated graph per [batch][hash][wide][search waves - 1][select]
     cudaGraphExec_t g_exec[2][2][2][2][2] = {};
     cudaGraphExec_t g_greedy[2] = {};  // greedy matching, [search waves - 1] of the shape
+    cudaGraphExec_t g_mcm[2] = {};     // maximum matching, [search waves - 1] of the shape
     std::map<uint64_t, awpm::TuneEntry> tune;  // autotuner state per problem class
     awpm::Pending pend;
     // the request server of this context (awpm_submit), created on first use

@@ -54,6 +54,10 @@ struct Ctl {
     int32_t converged;           // last pass flipped nothing
     int32_t max_passes;          // cap on passes
     int32_t live;                // greedy selection: winners still undecided
+    int32_t nonempty;            // maximum matching: no column is empty
+    int32_t phase_levels;        // maximum matching: levels of the running phase
+    int32_t level_tiles;         // maximum matching: tiles listed for this level
+    unsigned long long levels;   // maximum matching: search levels run
     unsigned long long pass_flips;   // cycles flipped in the running pass
     unsigned long long cycles;       // cycles flipped in total
     unsigned long long candidates;   // Step A requests (i > m_j)
@@ -151,6 +155,8 @@ struct Work {
     long long *mtkey;
     int32_t *mtrow;
     int32_t *mmate;
+    int32_t *mcolof;    // column of every entry
+    int32_t *mtiles;    // tiles holding a frontier column, this level
 };
 
 // Launch shape of a context: fixed grids sized by the GPU, not the problem.
@@ -203,6 +209,10 @@ void launch_mcm_phase(const Work *d, const Shape &sh, Sink &k);
 void launch_mcm_level(const Work *d, const Shape &sh, Sink &k);
 void launch_mcm_augment(const Work *d, const Shape &sh, Sink &k);
 void launch_mcm_store(const Work *d, const Shape &sh, Sink &k);
+// Graph forms: the condition of the level loop (undecided frontier left),
+// and the end of a phase (count it, continue while it augmented).
+void launch_mcm_cond_level(const Work *d, const Shape &sh, cudaGraphConditionalHandle h, Sink &k);
+void launch_mcm_cond_phase(const Work *d, const Shape &sh, cudaGraphConditionalHandle h, Sink &k);
 void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,
                     Sink &k);
 void launch_export_stepc(const Work *d, const Shape &sh, double *gain, int32_t *row, Sink &k);

@@ -1701,6 +1701,7 @@ __global__ void k_mc_reset(const Work *__restrict__ W)
         c->iterations = 0;
         c->converged = 0;
         c->live = 0;
+        c->levels = 0ull;
         c->pass_flips = 0ull;
         c->cycles = 0ull;
     }
@@ -1715,7 +1716,9 @@ __global__ void k_mc_reset(const Work *__restrict__ W)
 // unmatched): drop that report of the column-pointer check.
 __global__ void k_mc_allow_empty(const Work *__restrict__ W)
 {
-    atomicAnd(&W->ctl->err, ~kErrNotPerfect);
+    Ctl *c = W->ctl;
+    c->nonempty = (c->err & kErrNotPerfect) ? 0 : 1;
+    atomicAnd(&c->err, ~kErrNotPerfect);
 }
 
 // The starting matching: row of every column or -1, each row once, every
@@ -1781,8 +1784,75 @@ __global__ void k_mc_phase(const Work *__restrict__ W)
             live += __popc(bits);
         }
     }
+    if (gtid() == 0) {
+        w.ctl->phase_levels = 0;
+        w.ctl->level_tiles = 0;
+    }
     warp_add_i32(live, &w.ctl->live);
 }
+
+// Level, step 0: list the 32-entry tiles that hold an entry of a frontier
+// column.  A tile covers the columns from its first entry's column to the
+// next tile's first column (a superset: the lanes check their own column).
+// The list's order is free: every level step below takes the same decisions
+// in any order of its tiles.
+__global__ void k_mc_tiles(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    const int lane = threadIdx.x & 31;
+    for (int64_t t0 = gtid() - lane; t0 < w.ntiles; t0 += gstride()) {
+        const int64_t t = t0 + lane;
+        bool act = false;
+        if (t < w.ntiles) {
+            const int32_t c0 = __ldg(w.tile_col + t);
+            const int32_t c1 = t + 1 < w.ntiles ? __ldg(w.tile_col + t + 1) : w.n - 1;
+            for (int32_t x = c0 >> 5; x <= (c1 >> 5) && !act; ++x) {
+                uint32_t bits = w.mfront[x];
+                if (x == (c0 >> 5))
+                    bits &= ~0u << (c0 & 31);
+                if (x == (c1 >> 5) && (c1 & 31) != 31)
+                    bits &= (2u << (c1 & 31)) - 1u;
+                act = bits != 0u;
+            }
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, act);
+        if (!m)
+            continue;
+        int base = 0;
+        if (lane == 0)
+            base = atomicAdd(&w.ctl->level_tiles, __popc(m));
+        base = __shfl_sync(FULL_MASK, base, 0);
+        if (act)
+            w.mtiles[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)t;
+    }
+}
+
+// Level steps 1-4 run over the listed tiles (one warp per tile): a column of
+// any length, a hub included, is spread over many warps, and the work of a
+// level follows the size of its frontier.  The column of an entry comes from
+// the tile's first column and start bits when no column is empty, else from
+// the colof array.
+#define MC_TILE_LOOP_BEGIN                                                          \
+    const int lane = threadIdx.x & 31;                                              \
+    const int64_t nwarps = gstride() >> 5;                                          \
+    const bool exact = w.ctl->nonempty != 0;                                        \
+    const int64_t listed = w.ctl->level_tiles;                                      \
+    for (int64_t x = gtid() >> 5; x < listed; x += nwarps) {                        \
+        const int64_t t = w.mtiles[x];                                              \
+        const int32_t p = (int32_t)(t * kTile) + lane;                              \
+        const bool valid = p < w.nnz;                                               \
+        const int32_t c = !valid ? 0                                                \
+                          : exact ? lane_column(__ldg(w.tile_col + t), __ldg(w.starts + t), lane) \
+                                  : __ldg(w.mcolof + p);                            \
+        const bool inf = valid && ((w.mfront[c >> 5] >> (c & 31)) & 1u);           \
+        if (!__any_sync(FULL_MASK, inf))                                            \
+            continue;                                                               \
+        if (!inf)                                                                   \
+            continue;                                                               \
+        const int32_t r = w.rowidx[p];
+#define MC_TILE_LOOP_END }
 
 // Level, step 1: the heaviest offer per unreached row.
 __global__ void k_mc_offer_max(const Work *__restrict__ W)
@@ -1790,24 +1860,13 @@ __global__ void k_mc_offer_max(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    const int64_t words = (int64_t)w.n / 32 + 1;
-    for (int64_t x = gtid(); x < words; x += gstride()) {
-        uint32_t bits = w.mfront[x];
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const int32_t c = (int32_t)(x * 32 + b);
-            const int32_t own = w.mc[c];
-            for (int32_t p = w.colptr[c]; p < w.colptr[c + 1]; ++p) {
-                const int32_t r = w.rowidx[p];
-                if (r == own || w.mrpar[r] != -1)
-                    continue;
-                const long long key = order_key(w.w[p]);
-                if (key > *(volatile const long long *)(w.mrkey + r))
-                    atomicMax(w.mrkey + r, key);
-            }
-        }
-    }
+    MC_TILE_LOOP_BEGIN
+    if (r == w.mc[c] || w.mrpar[r] != -1)
+        continue;
+    const long long key = order_key(w.w[p]);
+    if (key > *(volatile const long long *)(w.mrkey + r))
+        atomicMax(w.mrkey + r, key);
+    MC_TILE_LOOP_END
 }
 
 // Level, step 2: the lowest column among the heaviest offers.
@@ -1816,23 +1875,12 @@ __global__ void k_mc_offer_min(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    const int64_t words = (int64_t)w.n / 32 + 1;
-    for (int64_t x = gtid(); x < words; x += gstride()) {
-        uint32_t bits = w.mfront[x];
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const int32_t c = (int32_t)(x * 32 + b);
-            const int32_t own = w.mc[c];
-            for (int32_t p = w.colptr[c]; p < w.colptr[c + 1]; ++p) {
-                const int32_t r = w.rowidx[p];
-                if (r == own || w.mrpar[r] != -1)
-                    continue;
-                if (order_key(w.w[p]) == w.mrkey[r] && c < *(volatile const int32_t *)(w.mrcol + r))
-                    atomicMin(w.mrcol + r, c);
-            }
-        }
-    }
+    MC_TILE_LOOP_BEGIN
+    if (r == w.mc[c] || w.mrpar[r] != -1)
+        continue;
+    if (order_key(w.w[p]) == w.mrkey[r] && c < *(volatile const int32_t *)(w.mrcol + r))
+        atomicMin(w.mrcol + r, c);
+    MC_TILE_LOOP_END
 }
 
 // Level, step 3: rows join the winning column's tree; a free row is a
@@ -1843,34 +1891,23 @@ __global__ void k_mc_join(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    const int64_t words = (int64_t)w.n / 32 + 1;
-    for (int64_t x = gtid(); x < words; x += gstride()) {
-        uint32_t bits = w.mfront[x];
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const int32_t c = (int32_t)(x * 32 + b);
-            const int32_t own = w.mc[c];
-            const int32_t t = w.mroot[c];
-            for (int32_t p = w.colptr[c]; p < w.colptr[c + 1]; ++p) {
-                const int32_t r = w.rowidx[p];
-                if (r == own || w.mrcol[r] != c || w.mrpar[r] != -1)
-                    continue;
-                w.mrpar[r] = c;
-                const long long key = order_key(w.w[p]);
-                w.mrkey[r] = kKeyNone;
-                w.mrcol[r] = 0x7fffffff;
-                const int32_t c2 = w.mr[r];
-                if (c2 < 0) {
-                    if (key > *(volatile const long long *)(w.mtkey + t))
-                        atomicMax(w.mtkey + t, key);
-                } else {
-                    w.mroot[c2] = t;
-                    atomicOr(w.mnext + (c2 >> 5), 1u << (c2 & 31));
-                }
-            }
-        }
+    MC_TILE_LOOP_BEGIN
+    if (r == w.mc[c] || w.mrcol[r] != c || w.mrpar[r] != -1)
+        continue;
+    w.mrpar[r] = c;
+    const long long key = order_key(w.w[p]);
+    w.mrkey[r] = kKeyNone;
+    w.mrcol[r] = 0x7fffffff;
+    const int32_t t_root = w.mroot[c];
+    const int32_t c2 = w.mr[r];
+    if (c2 < 0) {
+        if (key > *(volatile const long long *)(w.mtkey + t_root))
+            atomicMax(w.mtkey + t_root, key);
+    } else {
+        w.mroot[c2] = t_root;
+        atomicOr(w.mnext + (c2 >> 5), 1u << (c2 & 31));
     }
+    MC_TILE_LOOP_END
 }
 
 // Level, step 4: among a tree's free rows with the heaviest last edge, the
@@ -1880,23 +1917,29 @@ __global__ void k_mc_end(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    const int64_t words = (int64_t)w.n / 32 + 1;
-    for (int64_t x = gtid(); x < words; x += gstride()) {
-        uint32_t bits = w.mfront[x];
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const int32_t c = (int32_t)(x * 32 + b);
-            const int32_t t = w.mroot[c];
-            for (int32_t p = w.colptr[c]; p < w.colptr[c + 1]; ++p) {
-                const int32_t r = w.rowidx[p];
-                if (w.mrpar[r] != c || w.mr[r] >= 0)
-                    continue;
-                if (order_key(w.w[p]) == w.mtkey[t] && r < *(volatile const int32_t *)(w.mtrow + t))
-                    atomicMin(w.mtrow + t, r);
-            }
-        }
-    }
+    MC_TILE_LOOP_BEGIN
+    if (w.mrpar[r] != c || w.mr[r] >= 0)
+        continue;
+    const int32_t t_root = w.mroot[c];
+    if (order_key(w.w[p]) == w.mtkey[t_root] && r < *(volatile const int32_t *)(w.mtrow + t_root))
+        atomicMin(w.mtrow + t_root, r);
+    MC_TILE_LOOP_END
+}
+
+#undef MC_TILE_LOOP_BEGIN
+#undef MC_TILE_LOOP_END
+
+// Column of every entry (a warp per column), for the level kernels.
+__global__ void k_mc_colof(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if ((w.ctl->err & kErrInvalid) || w.ctl->nonempty)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t j = gtid() >> 5; j < w.n; j += nwarps)
+        for (int32_t p = w.colptr[j] + lane; p < w.colptr[j + 1]; p += 32)
+            w.mcolof[p] = (int32_t)j;
 }
 
 // Level, step 5: the next frontier without the trees that have an end; its
@@ -1922,7 +1965,37 @@ __global__ void k_mc_advance(const Work *__restrict__ W)
             live += __popc(keep);
         }
     }
+    if (gtid() == 0)
+        w.ctl->level_tiles = 0;
     warp_add_i32(live, &w.ctl->live);
+}
+
+// Graph form of the level loop's condition: a frontier is left.
+__global__ void k_mc_cond_level(const Work *__restrict__ W, cudaGraphConditionalHandle h)
+{
+    Ctl *c = W->ctl;
+    const int32_t live = c->live;
+    c->live = 0;
+    if (live > 0) {
+        c->levels += 1;
+        // every level adds at least one row to the search forest
+        if (++c->phase_levels > W->n + 1)
+            raise_err(c, kErrInternal);
+    }
+    cudaGraphSetConditional(h, (live > 0 && c->err == 0u) ? 1u : 0u);
+}
+
+// Graph form of the end of a phase: count it and the paths it augmented;
+// continue while it augmented something.
+__global__ void k_mc_cond_phase(const Work *__restrict__ W, cudaGraphConditionalHandle h)
+{
+    Ctl *c = W->ctl;
+    const unsigned long long aug = c->pass_flips;
+    c->pass_flips = 0ull;
+    c->cycles += aug;
+    c->iterations += 1;
+    const bool go = aug > 0 && c->err == 0u && c->iterations <= W->n;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 // Every tree with an end flips its path; their number into Ctl::pass_flips.
@@ -2194,6 +2267,7 @@ void launch_mcm_load(const Work *d, const Shape &sh, Sink &k)
     k.launch((const void *)k_mark_starts, init_grid(sh), kThreads, a);
     k.launch((const void *)k_gm_check, init_tile_grid(sh), kThreads, a);
     k.launch((const void *)k_mc_load, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_colof, init_grid(sh), kThreads, a);
 }
 
 void launch_mcm_phase(const Work *d, const Shape &sh, Sink &k)
@@ -2205,10 +2279,11 @@ void launch_mcm_phase(const Work *d, const Shape &sh, Sink &k)
 void launch_mcm_level(const Work *d, const Shape &sh, Sink &k)
 {
     void *a[] = {(void *)&d};
-    k.launch((const void *)k_mc_offer_max, tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_mc_offer_min, tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_mc_join, tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_mc_end, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_tiles, init_tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_offer_max, init_tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_offer_min, init_tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_join, init_tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_end, init_tile_grid(sh), kThreads, a);
     k.launch((const void *)k_mc_advance, util_grid(sh), kThreads, a);
 }
 
@@ -2216,6 +2291,18 @@ void launch_mcm_augment(const Work *d, const Shape &sh, Sink &k)
 {
     void *a[] = {(void *)&d};
     k.launch((const void *)k_mc_augment, util_grid(sh), kThreads, a);
+}
+
+void launch_mcm_cond_level(const Work *d, const Shape &sh, cudaGraphConditionalHandle h, Sink &k)
+{
+    void *ah[] = {(void *)&d, (void *)&h};
+    k.launch((const void *)k_mc_cond_level, 1, 1, ah);
+}
+
+void launch_mcm_cond_phase(const Work *d, const Shape &sh, cudaGraphConditionalHandle h, Sink &k)
+{
+    void *ah[] = {(void *)&d, (void *)&h};
+    k.launch((const void *)k_mc_cond_phase, 1, 1, ah);
 }
 
 void launch_mcm_store(const Work *d, const Shape &sh, Sink &k)

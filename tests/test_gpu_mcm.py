@@ -78,3 +78,23 @@ def test_bad_start(ctx, torch):
         mcm_gpu(ctx, g, m, torch, host=True)
     assert ei.value.name == "NOT_PERFECT"
     check(ctx, g, torch)
+
+
+def test_graph_and_host_loop_agree(torch):
+    """The search as one graph launch (loops on the device) and with levels and
+    phases driven from the host (AWPM_FLAG_TIME_SEARCH): same matching, same
+    phase and level counts, twice in a row on one context (the cached graph)."""
+    ch = awpm.awpm_create(device=0, flags=awpm.FLAG_TIME_SEARCH)
+    cg = awpm.awpm_create(device=0)
+    try:
+        for g in (gen.rmat(1 << 13, 8, 9400), pins.random_pattern(700, 2, 9401),
+                  gen.stencil_2d(50, 9402)):
+            a, sa = mcm_gpu(ch, g, None, torch)
+            for _ in range(2):
+                b, sb = mcm_gpu(cg, g, None, torch)
+                assert a.tolist() == b.tolist()
+                assert (sa["phases"], sa["levels"], sa["cardinality"]) == \
+                    (sb["phases"], sb["levels"], sb["cardinality"])
+    finally:
+        awpm.awpm_destroy(ch)
+        awpm.awpm_destroy(cg)
