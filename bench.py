@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-pool", type=int, default=16)
-    ap.add_argument("--lookup", default="auto", choices=["auto", "bsearch", "hash"],
+    ap.add_argument("--lookup", default="auto", choices=["auto", "bsearch", "hash", "rowmark"],
                     help="closing-edge lookup (auto: the library's autotuner picks)")
     ap.add_argument("--workload", default="rmat",
                     choices=["rmat", "stencil3d", "stencil2d", "rmat20", "rmat21"])
@@ -541,7 +541,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     # lookup AUTO: the warm-up solves are the autotuner's trials
     lookup_opt = {"auto": awpm.LOOKUP_AUTO, "bsearch": awpm.LOOKUP_BSEARCH,
-                  "hash": awpm.LOOKUP_HASH}[args.lookup]
+                  "hash": awpm.LOOKUP_HASH, "rowmark": awpm.LOOKUP_ROWMARK}[args.lookup]
     ctx = awpm.awpm_create(device=local, stream=stream.cuda_stream, lookup=lookup_opt)
     cp = torch.from_numpy(g.colptr).to(dev)
     ri = torch.from_numpy(g.rowidx).to(dev)

@@ -69,6 +69,14 @@ extern "C" {
 #define AWPM_LOOKUP_HASH 2    /* per-column open-addressing table built once per solve
                                  (nnz < 2^30; larger problems use the binary search,
                                  as awpm_stats.lookup_used reports)                    */
+#define AWPM_LOOKUP_ROWMARK 3 /* row marking (Section 4): the neighbourhood of row m_j
+                                 is marked once per solve (a 64-bit signature of its
+                                 columns) and confirmed in the transpose of the
+                                 pattern (built once per solve by a radix sort), so
+                                 every candidate of root j reads row m_j's data;
+                                 never picked by AWPM_LOOKUP_AUTO; the batched and
+                                 single paths only (awpm_search_noalloc: binary
+                                 search)                                              */
 
 /* awpm_options.select: how a pass turns its Step-C winners into the disjoint
  * cycles it flips.
@@ -133,7 +141,7 @@ typedef struct {
     double ms_total;         /* wall time of the call on the stream (CUDA events)      */
     double ms_search;        /* summed cycle-search kernel time, only with
                                 AWPM_FLAG_TIME_SEARCH (else 0)                         */
-    int32_t lookup_used;     /* AWPM_LOOKUP_BSEARCH or AWPM_LOOKUP_HASH                */
+    int32_t lookup_used;     /* AWPM_LOOKUP_BSEARCH, _HASH or _ROWMARK                 */
     int32_t reserved;
 } awpm_stats;
 

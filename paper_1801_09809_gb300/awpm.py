@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libawpm.so")
 AWPM_OK = 0
 ERRORS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_PERFECT", 3: "UNSORTED_OR_DUP", 4: "NONFINITE",
           5: "OOM", 6: "BUDGET", 7: "CUDA", 8: "TIMEOUT", 9: "NOT_FOUND", 10: "TOO_LARGE"}
-LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_HASH = 0, 1, 2
+LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_HASH, LOOKUP_ROWMARK = 0, 1, 2, 3
 SELECT_STEP_D, SELECT_GREEDY = 0, 1
 FLAG_TIME_SEARCH = 1
 PASS_CAP = 65536

@@ -142,6 +142,12 @@ int check_sink(const Sink &k)
     return AWPM_OK;
 }
 
+// Index of a lookup in the per-lookup tables: binary search, hash, row marking.
+int lookup_slot(int lookup)
+{
+    return lookup == AWPM_LOOKUP_HASH ? 1 : lookup == AWPM_LOOKUP_ROWMARK ? 2 : 0;
+}
+
 Shape shape_of(const awpm_ctx *c, bool batch, int lookup, bool wide, int32_t ntiles)
 {
     Shape sh;
@@ -149,7 +155,7 @@ Shape shape_of(const awpm_ctx *c, bool batch, int lookup, bool wide, int32_t nti
     sh.batch = batch;
     sh.lookup = lookup;
     sh.wide = wide;
-    sh.search_bps = c->search_bps[batch ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0][wide ? 1 : 0];
+    sh.search_bps = c->search_bps[batch ? 1 : 0][lookup_slot(lookup)][wide ? 1 : 0];
     sh.search_waves = search_waves(sh.num_sms, sh.search_bps, ntiles);
     sh.select = c->opt.select == AWPM_SELECT_GREEDY ? AWPM_SELECT_GREEDY : AWPM_SELECT_STEP_D;
     return sh;
@@ -525,8 +531,10 @@ size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup)
                4 * (Z / 32 + 1) + sizeof(Ctl) + 8 * kWsumBlocks;
     if (lookup != AWPM_LOOKUP_BSEARCH)  // hash tables (AUTO may pick them)
         b += 16 * Z;
-    if (lookup != AWPM_LOOKUP_HASH)  // Bloom filters of the binary search
+    if (lookup != AWPM_LOOKUP_HASH && lookup != AWPM_LOOKUP_ROWMARK)  // Bloom filters
         b += Z + 4;
+    if (lookup == AWPM_LOOKUP_ROWMARK)  // marks, transpose, radix-sort buffers
+        b += 12 * N + 4 + 16 * Z + 4 * (size_t)kRsBins * (Z / kRsTile + 1) + 4 * kRsBins;
     if (host_inputs)
         b += 4 * (N + 1) + 12 * Z + 8 * N;
     return b + b / 8;
@@ -543,7 +551,7 @@ int setup_ctx(awpm_ctx *c, const awpm_options *opt)
         c->opt = *opt;
     else
         awpm_default_options(&c->opt);
-    if (c->opt.max_iters < 0 || c->opt.lookup < 0 || c->opt.lookup > 2 || c->opt.slots < 0 ||
+    if (c->opt.max_iters < 0 || c->opt.lookup < 0 || c->opt.lookup > 3 || c->opt.slots < 0 ||
         c->opt.select < 0 || c->opt.select > 1)
         return AWPM_ERR_INVALID_ARG;
     int dev = c->opt.device;
@@ -557,6 +565,7 @@ int setup_ctx(awpm_ctx *c, const awpm_options *opt)
         for (int p = 0; p < 2; ++p) {
             c->search_bps[b][0][p] = search_blocks_per_sm(AWPM_LOOKUP_BSEARCH, b == 1, p == 1);
             c->search_bps[b][1][p] = search_blocks_per_sm(AWPM_LOOKUP_HASH, b == 1, p == 1);
+            c->search_bps[b][2][p] = search_blocks_per_sm(AWPM_LOOKUP_ROWMARK, b == 1, p == 1);
         }
     if (c->opt.stream) {
         c->stream = (cudaStream_t)c->opt.stream;
@@ -584,7 +593,7 @@ void teardown_ctx(awpm_ctx *c)
     if (c->stream)
         cudaStreamSynchronize(c->stream);
     for (int b = 0; b < 2; ++b)
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < 3; ++h)
             for (int p = 0; p < 2; ++p)
                 for (int v = 0; v < 2; ++v)
                     for (int q = 0; q < 2; ++q)
@@ -613,7 +622,8 @@ void teardown_ctx(awpm_ctx *c)
                       &c->wt_cmax, &c->wt_rmax,  &c->wt_stage,
                       &c->mroot,   &c->mrpar,    &c->mfront,   &c->mnext,    &c->mrkey,
                       &c->mrcol,   &c->mtkey,    &c->mtrow,    &c->mstage,   &c->mcolof,
-                      &c->mtiles};
+                      &c->mtiles,  &c->rowsig,   &c->trowptr,  &c->rs_k0,    &c->rs_k1,
+                      &c->rs_v0,   &c->rs_v1,    &c->rs_hist,  &c->rs_sums};
     for (DevBuf *b : bufs)
         release(c, *b);
     if (c->h_work)
@@ -648,7 +658,9 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
         (r.count > 0 && !r.n_off))
         return AWPM_ERR_INVALID_ARG;
     CUDA_TRY(cudaSetDevice(c->device));
-    pd.lookup = c->opt.lookup == AWPM_LOOKUP_HASH ? AWPM_LOOKUP_HASH : AWPM_LOOKUP_BSEARCH;
+    pd.lookup = (c->opt.lookup == AWPM_LOOKUP_HASH || c->opt.lookup == AWPM_LOOKUP_ROWMARK)
+                    ? c->opt.lookup
+                    : AWPM_LOOKUP_BSEARCH;
     pd.search_only = r.search_only;
     if (n == 0) {
         pd.active = true;
@@ -717,10 +729,25 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     AWPM_TRY(ensure(c, c->starts, sizeof(uint32_t) * (((size_t)nnz + 31) / 32 + 1)));
     AWPM_TRY(ensure(c, c->ctl, sizeof(Ctl)));
     AWPM_TRY(ensure(c, c->wpart, sizeof(double) * kWsumBlocks));
-    if (lookup == AWPM_LOOKUP_HASH)
+    const int32_t rs_tiles = (int32_t)(((int64_t)nnz + kRsTile - 1) / kRsTile);
+    int32_t rs_passes = 1;
+    while (rs_passes < 4 && ((int64_t)(n - 1) >> (8 * rs_passes)) > 0)
+        ++rs_passes;
+    if (lookup == AWPM_LOOKUP_HASH) {
         AWPM_TRY(ensure(c, c->htab, sizeof(unsigned long long) * 2 * (size_t)nnz));
-    else
+    } else if (lookup == AWPM_LOOKUP_ROWMARK) {
+        const size_t m = (size_t)kRsBins * (size_t)rs_tiles;
+        AWPM_TRY(ensure(c, c->rowsig, sizeof(unsigned long long) * n));
+        AWPM_TRY(ensure(c, c->trowptr, sizeof(int32_t) * ((size_t)n + 1)));
+        AWPM_TRY(ensure(c, c->rs_k0, sizeof(int32_t) * ((size_t)nnz + 1)));
+        AWPM_TRY(ensure(c, c->rs_k1, sizeof(int32_t) * ((size_t)nnz + 1)));
+        AWPM_TRY(ensure(c, c->rs_v0, sizeof(int32_t) * ((size_t)nnz + 1)));
+        AWPM_TRY(ensure(c, c->rs_v1, sizeof(int32_t) * ((size_t)nnz + 1)));
+        AWPM_TRY(ensure(c, c->rs_hist, sizeof(int32_t) * (m + 1)));
+        AWPM_TRY(ensure(c, c->rs_sums, sizeof(int32_t) * (m / kScanChunk + 2)));
+    } else {
         AWPM_TRY(ensure(c, c->bloom, sizeof(uint32_t) * ((size_t)nnz / 4 + 1)));
+    }
     const bool ps = c->opt.select == AWPM_SELECT_GREEDY && !r.search_only;
     if (ps) {
         AWPM_TRY(ensure(c, c->psel, sizeof(Sel) * n));
@@ -733,7 +760,7 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     const Shape sh = shape_of(c, count > 0, lookup, wide, ntiles);
     cudaGraphExec_t gexec = nullptr;
     if (!r.search_only && !timed) {
-        cudaGraphExec_t &g = c->g_exec[count > 0 ? 1 : 0][lookup == AWPM_LOOKUP_HASH ? 1 : 0]
+        cudaGraphExec_t &g = c->g_exec[count > 0 ? 1 : 0][lookup_slot(lookup)]
                                       [wide ? 1 : 0][sh.search_waves - 1][sh.select];
         if (!g)
             AWPM_TRY(build_graph(c, sh, &g));
@@ -758,7 +785,20 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     wk.wmr = (double *)c->wmr.p;
     wk.colsig = (unsigned long long *)c->colsig.p;
     wk.htab = lookup == AWPM_LOOKUP_HASH ? (unsigned long long *)c->htab.p : nullptr;
-    wk.bloom = lookup == AWPM_LOOKUP_HASH ? nullptr : (uint32_t *)c->bloom.p;
+    wk.bloom = lookup == AWPM_LOOKUP_BSEARCH ? (uint32_t *)c->bloom.p : nullptr;
+    if (lookup == AWPM_LOOKUP_ROWMARK) {
+        wk.rowsig = (unsigned long long *)c->rowsig.p;
+        wk.trowptr = (int32_t *)c->trowptr.p;
+        wk.rs_key[0] = (int32_t *)c->rs_k0.p;
+        wk.rs_key[1] = (int32_t *)c->rs_k1.p;
+        wk.rs_val[0] = (int32_t *)c->rs_v0.p;
+        wk.rs_val[1] = (int32_t *)c->rs_v1.p;
+        wk.rs_hist = (int32_t *)c->rs_hist.p;
+        wk.rs_sums = (int32_t *)c->rs_sums.p;
+        wk.rs_tiles = rs_tiles;
+        wk.rs_passes = rs_passes;
+        wk.tpos = wk.rs_val[(rs_passes - 1) & 1];
+    }
     if (ps) {
         wk.psel = (Sel *)c->psel.p;
         wk.pslive = (uint32_t *)c->pslive.p;

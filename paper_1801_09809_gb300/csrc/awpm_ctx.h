@@ -88,7 +88,7 @@ struct awpm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t held = 0;
-    int search_bps[2][2][2] = {};  // [batch][hash][wide]
+    int search_bps[2][3][2] = {};  // [batch][lookup slot][wide]
     bool search_wide = true;      // default when the lookup is given explicitly
     // per-solve device workspace
     awpm::DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
@@ -99,6 +99,7 @@ struct awpm_ctx {
     awpm::DevBuf wt_cmax, wt_rmax, wt_stage;     // weights from matrix values
     awpm::DevBuf mroot, mrpar, mfront, mnext, mrkey, mrcol, mtkey, mtrow, mstage,
         mcolof, mtiles;  // maximum matching
+    awpm::DevBuf rowsig, trowptr, rs_k0, rs_k1, rs_v0, rs_v1, rs_hist, rs_sums;  // row marking
     awpm::DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
     // staging of host-resident arrays
     awpm::DevBuf s_colptr, s_rowidx, s_w, s_mate, s_out, s_gain, s_row;
@@ -111,8 +112,8 @@ struct awpm_ctx {
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     std::vector<cudaEvent_t> tev;     // timing pairs of the timed loop
     std::vector<cudaEvent_t> flagev;  // ring of the timed loop
-    // one instantiated graph per [batch][hash][wide][search waves - 1][select]
-    cudaGraphExec_t g_exec[2][2][2][2][2] = {};
+    // one instantiated graph per [batch][lookup slot][wide][search waves - 1][select]
+    cudaGraphExec_t g_exec[2][3][2][2][2] = {};
     cudaGraphExec_t g_greedy[2] = {};  // greedy matching, [search waves - 1] of the shape
     cudaGraphExec_t g_mcm[2] = {};     // maximum matching, [search waves - 1] of the shape
     std::map<uint64_t, awpm::TuneEntry> tune;  // autotuner state per problem class

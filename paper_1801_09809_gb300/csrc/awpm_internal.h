@@ -98,7 +98,7 @@ struct Work {
     int32_t nnz;
     int32_t ntiles;
     int32_t max_passes;
-    int32_t lookup;     // AWPM_LOOKUP_BSEARCH or AWPM_LOOKUP_HASH
+    int32_t lookup;     // AWPM_LOOKUP_BSEARCH, _HASH or _ROWMARK
     int32_t pad;
     const int32_t *colptr;
     const int32_t *rowidx;
@@ -157,13 +157,34 @@ struct Work {
     int32_t *mmate;
     int32_t *mcolof;    // column of every entry
     int32_t *mtiles;    // tiles holding a frontier column, this level
+    // row marking: per row the mark of its columns (a signature), the
+    // transpose (row pointers; CSC positions row by row, ascending), the
+    // radix sort that builds it (keys and values in two buffers each, digit
+    // counts per block tile, then their offsets; sums per scan chunk)
+    unsigned long long *rowsig;
+    int32_t *trowptr;
+    int32_t *tpos;
+    int32_t *rs_key[2];
+    int32_t *rs_val[2];
+    int32_t *rs_hist;
+    int32_t *rs_sums;
+    int32_t rs_tiles;   // block tiles of kRsTile entries
+    int32_t rs_passes;  // 8-bit digits of the largest row index (at least 1)
 };
+
+// Radix sort of the transpose: 256 threads, 8 entries each per block tile,
+// 8-bit digits; scans run over chunks of 2048 counts.
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;
+constexpr int kRsBins = 256;
+constexpr int kScanChunk = kRsThreads * 8;
 
 // Launch shape of a context: fixed grids sized by the GPU, not the problem.
 struct Shape {
     int num_sms;
     int search_bps;     // resident blocks per SM of the chosen search kernel
-    int lookup;         // AWPM_LOOKUP_BSEARCH or AWPM_LOOKUP_HASH
+    int lookup;         // AWPM_LOOKUP_BSEARCH, _HASH or _ROWMARK
     bool batch;
     bool wide;          // search kernel takes four tiles per warp round (else one)
     int search_waves;   // search grid = search_waves full waves of resident blocks

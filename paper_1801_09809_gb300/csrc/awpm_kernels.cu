@@ -364,6 +364,9 @@ __global__ void k_reset(const Work *__restrict__ W)
     if (w.bloom)
         for (int64_t x = gtid(); x <= (int64_t)w.nnz / 4; x += gstride())
             w.bloom[x] = 0u;
+    if (w.rowsig)
+        for (int64_t x = gtid(); x < w.n; x += gstride())
+            w.rowsig[x] = 0ull;
     if (w.psel) {
         for (int64_t j = gtid(); j < w.n; j += gstride())
             w.psel[j] = Sel{0.0, 0, 0};
@@ -715,6 +718,336 @@ __global__ void k_batch_wsum(const Work *__restrict__ W, int out)
 }
 
 // ---------------------------------------------------------------------------
+// Row marking (Section 4): marks of the rows' neighbourhoods and the
+// transpose of the pattern, built once per solve for AWPM_LOOKUP_ROWMARK
+// ---------------------------------------------------------------------------
+
+// The mark of row i: the signature (see sig_mask) of the columns k with a
+// stored (i, k), each column named by its first position colptr[k] (the
+// search has that number at hand from the row record), OR-ed over the
+// entries with 64-bit atomics (skipped when the bits are already set).  Runs
+// after validation: no column is empty, so the start bitmap gives exact
+// columns and distinct first positions.
+__global__ void __launch_bounds__(kThreads) k_rm_marks(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err || !w.rowsig)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
+        const int32_t p = (int32_t)(t * kTile) + lane;
+        if (p >= w.nnz)
+            continue;
+        const int32_t j = lane_column(__ldg(w.tile_col + t), __ldg(w.starts + t), lane);
+        const int32_t i = __ldcs(w.rowidx + p);
+        const unsigned long long m = sig_mask(__ldg(w.colptr + j));
+        // bits only ever get set: a set bit in the (possibly stale) L1 copy
+        // is set; otherwise ask the L2 copy, where the atomics land
+        if ((w.rowsig[i] & m) != m && (__ldcg(w.rowsig + i) & m) != m)
+            atomicOr(w.rowsig + i, m);
+    }
+}
+
+// Exclusive prefix of one value per thread over a block of kRsThreads
+// threads; the block's total into *total.  Called by the whole block.
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *total)
+{
+    __shared__ int32_t s_w[kRsThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        s_w[warp] = x;
+    __syncthreads();
+    int32_t below = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < kRsThreads / 32; ++i) {
+        below += i < warp ? s_w[i] : 0;
+        tot += s_w[i];
+    }
+    __syncthreads();
+    *total = tot;
+    return below + x - v;
+}
+
+// The transpose is a stable LSD radix sort of the entries (in CSC order) by
+// row, 8 bits per pass: afterwards the CSC positions of each row's entries
+// are contiguous and ascending, i.e. in column order.  Pass `pass` reads the
+// keys of the previous pass (the row indices themselves first) and writes
+// buffer pass & 1; passes at or above rs_passes do nothing.
+
+// Digit counts of each block tile of kRsTile entries, stored digit-major
+// (rs_hist[digit * rs_tiles + tile]) so one scan gives every scatter offset.
+// A thread loads its 16 keys first; each warp counts into its own table.
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const Work *__restrict__ W, int pass)
+{
+    const Work &w = *W;
+    if (w.ctl->err || pass >= w.rs_passes)
+        return;
+    constexpr int kWarps = kRsThreads / 32;
+    __shared__ int32_t s_cnt[kWarps][kRsBins];
+    const int warp = threadIdx.x >> 5;
+    const int shift = 8 * pass;
+    const int32_t *key = pass == 0 ? w.rowidx : w.rs_key[(pass - 1) & 1];
+    for (int64_t tile = blockIdx.x; tile < w.rs_tiles; tile += gridDim.x) {
+#pragma unroll
+        for (int x = 0; x < kWarps; ++x)
+            s_cnt[x][threadIdx.x] = 0;
+        uint32_t k[kRsItems];
+#pragma unroll
+        for (int r = 0; r < kRsItems; ++r) {
+            const int64_t e = tile * kRsTile + r * kRsThreads + threadIdx.x;
+            k[r] = e < w.nnz ? (uint32_t)__ldcs(key + e) : 0xffffffffu;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kRsItems; ++r)
+            if (k[r] != 0xffffffffu)
+                atomicAdd(&s_cnt[warp][(k[r] >> shift) & 255u], 1);
+        __syncthreads();
+        int32_t c = 0;
+#pragma unroll
+        for (int x = 0; x < kWarps; ++x)
+            c += s_cnt[x][threadIdx.x];
+        w.rs_hist[(int64_t)threadIdx.x * w.rs_tiles + tile] = c;
+        __syncthreads();
+    }
+}
+
+// Scan of the digit counts, step 1: the total of every chunk of kScanChunk.
+__global__ void __launch_bounds__(kRsThreads) k_rs_scan_a(const Work *__restrict__ W, int pass)
+{
+    const Work &w = *W;
+    if (w.ctl->err || pass >= w.rs_passes)
+        return;
+    const int64_t m = (int64_t)kRsBins * w.rs_tiles;
+    const int64_t chunks = (m + kScanChunk - 1) / kScanChunk;
+    for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+        int32_t s = 0;
+        for (int k = 0; k < kScanChunk / kRsThreads; ++k) {
+            const int64_t x = c * kScanChunk + k * kRsThreads + threadIdx.x;
+            if (x < m)
+                s += w.rs_hist[x];
+        }
+        int32_t tot = 0;
+        block_excl_scan(s, &tot);
+        if (threadIdx.x == 0)
+            w.rs_sums[c] = tot;
+    }
+}
+
+// Step 2 (one block): exclusive prefix of the chunk totals, in place.
+__global__ void __launch_bounds__(kRsThreads) k_rs_scan_b(const Work *__restrict__ W, int pass)
+{
+    const Work &w = *W;
+    if (w.ctl->err || pass >= w.rs_passes)
+        return;
+    const int64_t m = (int64_t)kRsBins * w.rs_tiles;
+    const int64_t chunks = (m + kScanChunk - 1) / kScanChunk;
+    int32_t carry = 0;
+    for (int64_t b0 = 0; b0 < chunks; b0 += kRsThreads) {
+        const int64_t x = b0 + threadIdx.x;
+        const int32_t v = x < chunks ? w.rs_sums[x] : 0;
+        int32_t tot = 0;
+        const int32_t pre = block_excl_scan(v, &tot);
+        if (x < chunks)
+            w.rs_sums[x] = carry + pre;
+        carry += tot;
+    }
+}
+
+// Step 3: every chunk's exclusive prefix plus the chunk's offset, in place;
+// thread t takes the chunk's counts 8t .. 8t + 7.
+__global__ void __launch_bounds__(kRsThreads) k_rs_scan_c(const Work *__restrict__ W, int pass)
+{
+    const Work &w = *W;
+    if (w.ctl->err || pass >= w.rs_passes)
+        return;
+    constexpr int kPer = kScanChunk / kRsThreads;
+    const int64_t m = (int64_t)kRsBins * w.rs_tiles;
+    const int64_t chunks = (m + kScanChunk - 1) / kScanChunk;
+    for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+        const int64_t x0 = c * kScanChunk + (int64_t)threadIdx.x * kPer;
+        int32_t v[kPer];
+        int32_t s = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            v[k] = x0 + k < m ? w.rs_hist[x0 + k] : 0;
+            s += v[k];
+        }
+        int32_t tot = 0;
+        int32_t run = block_excl_scan(s, &tot) + w.rs_sums[c];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            if (x0 + k < m)
+                w.rs_hist[x0 + k] = run;
+            run += v[k];
+        }
+    }
+}
+
+// Stable scatter of one pass.  A thread loads its kRsItems entries of the
+// block tile; the tile is sorted by digit in shared memory (the entries
+// placed 256 at a time, in order: within a warp, entries of equal digit --
+// eight ballots -- are ranked by lane, and the warps' digit counts give each
+// warp's offset; counts and running offsets alternate between two tables, so
+// a round needs two barriers); then each digit's run is written to its
+// global offset with consecutive threads on consecutive positions.
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const Work *__restrict__ W, int pass)
+{
+    const Work &w = *W;
+    if (w.ctl->err || pass >= w.rs_passes)
+        return;
+    constexpr int kWarps = kRsThreads / 32;
+    __shared__ int32_t s_key[kRsTile];
+    __shared__ int32_t s_val[kRsTile];
+    __shared__ int32_t s_local[kRsBins];   // start of each digit's run in the tile
+    __shared__ int32_t s_global[kRsBins];  // its global offset
+    __shared__ int32_t s_base[2][kRsBins];
+    __shared__ int32_t s_wcnt[2][kWarps][kRsBins];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int shift = 8 * pass;
+    const int32_t *kin = pass == 0 ? w.rowidx : w.rs_key[(pass - 1) & 1];
+    const int32_t *vin = pass == 0 ? nullptr : w.rs_val[(pass - 1) & 1];
+    int32_t *kout = w.rs_key[pass & 1];
+    int32_t *vout = w.rs_val[pass & 1];
+    for (int64_t tile = blockIdx.x; tile < w.rs_tiles; tile += gridDim.x) {
+        const int64_t first = tile * kRsTile;
+        const int32_t count =
+            (int32_t)(w.nnz - first < kRsTile ? w.nnz - first : (int64_t)kRsTile);
+        int32_t kv[kRsItems], vv[kRsItems];
+#pragma unroll
+        for (int r = 0; r < kRsItems; ++r) {
+            const int32_t x = r * kRsThreads + threadIdx.x;
+            const bool valid = x < count;
+            kv[r] = valid ? __ldcs(kin + first + x) : -1;
+            vv[r] = valid ? (vin ? __ldcs(vin + first + x) : (int32_t)(first + x)) : 0;
+        }
+        s_base[0][threadIdx.x] = 0;  // digit counts of the tile first
+#pragma unroll
+        for (int x = 0; x < kWarps; ++x) {
+            s_wcnt[0][x][threadIdx.x] = 0;
+            s_wcnt[1][x][threadIdx.x] = 0;
+        }
+        s_global[threadIdx.x] = w.rs_hist[(int64_t)threadIdx.x * w.rs_tiles + tile];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kRsItems; ++r)
+            if (kv[r] >= 0)
+                atomicAdd(&s_base[0][((uint32_t)kv[r] >> shift) & 255u], 1);
+        __syncthreads();
+        int32_t tot = 0;
+        const int32_t start = block_excl_scan(s_base[0][threadIdx.x], &tot);
+        s_local[threadIdx.x] = start;
+        s_base[0][threadIdx.x] = start;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kRsItems; ++r) {
+            const int q = r & 1;
+            const bool valid = kv[r] >= 0;
+            const int d = valid ? (int)(((uint32_t)kv[r] >> shift) & 255u) : kRsBins;
+            // lanes with the same digit: agree on all 8 bits and on validity
+            const unsigned vm = __ballot_sync(FULL_MASK, valid);
+            unsigned peers = valid ? vm : ~vm;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const unsigned m = __ballot_sync(FULL_MASK, (d >> b) & 1);
+                peers &= ((d >> b) & 1) ? m : ~m;
+            }
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            if (valid && rank == 0)
+                s_wcnt[q][warp][d] = __popc(peers);
+            __syncthreads();
+            if (valid) {
+                int32_t off = s_base[q][d] + rank;
+                for (int x = 0; x < warp; ++x)
+                    off += s_wcnt[q][x][d];
+                s_key[off] = kv[r];
+                s_val[off] = vv[r];
+            }
+            int32_t add = 0;
+#pragma unroll
+            for (int x = 0; x < kWarps; ++x) {
+                add += s_wcnt[q][x][threadIdx.x];
+                s_wcnt[q ^ 1][x][threadIdx.x] = 0;
+            }
+            s_base[q ^ 1][threadIdx.x] = s_base[q][threadIdx.x] + add;
+            __syncthreads();
+        }
+        for (int32_t x = threadIdx.x; x < count; x += kRsThreads) {
+            const int32_t key = s_key[x];
+            const int d = (int)(((uint32_t)key >> shift) & 255u);
+            const int32_t g = s_global[d] + (x - s_local[d]);
+            if (g >= 0 && g < w.nnz) {
+                kout[g] = key;
+                vout[g] = s_val[x];
+            } else {
+                raise_err(w.ctl, kErrInternal);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Row pointers of the transpose from the sorted keys: row r starts at the
+// first entry whose row is >= r.
+__global__ void k_rm_rowptr(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err || !w.trowptr)
+        return;
+    const int64_t nnz = w.nnz;
+    if (nnz == 0) {
+        for (int64_t r = gtid(); r <= w.n; r += gstride())
+            w.trowptr[r] = 0;
+        return;
+    }
+    const int32_t *key = w.rs_key[(w.rs_passes - 1) & 1];
+    for (int64_t e = gtid(); e < nnz; e += gstride()) {
+        const int32_t k = key[e];
+        const int32_t prev = e > 0 ? key[e - 1] : -1;
+        if (k < 0 || k >= w.n || prev > k) {  // not sorted rows: no transpose
+            raise_err(w.ctl, kErrInternal);
+            continue;
+        }
+        for (int32_t r = prev + 1; r <= k; ++r)
+            w.trowptr[r] = (int32_t)e;
+        if (e == nnz - 1)
+            for (int64_t r = (int64_t)k + 1; r <= w.n; ++r)
+                w.trowptr[r] = (int32_t)nnz;
+    }
+}
+
+// Warp-cooperative search, in the ascending values arr[s, s+len), of the
+// last one below `key` for one lane's request (all 32 lanes take part, as in
+// coop_find).  Returns its index or -1.
+__device__ __forceinline__ int32_t coop_last_below(const int32_t *__restrict__ arr, int32_t s,
+                                                   int32_t len, int32_t key, int lane)
+{
+    while (len > 32) {
+        const int32_t step = (len + 31) >> 5;
+        const int32_t off = lane * step;
+        const int32_t v = off < len ? __ldg(arr + s + off) : 0x7fffffff;
+        const unsigned lt = __ballot_sync(FULL_MASK, v < key);
+        if (lt == 0)
+            return -1;
+        const int c = 31 - __clz(lt);
+        s += c * step;
+        const int32_t rest = len - c * step;
+        len = rest < step ? rest : step;
+    }
+    const int32_t v = lane < len ? __ldg(arr + s + lane) : 0x7fffffff;
+    const unsigned lt = __ballot_sync(FULL_MASK, v < key);
+    return lt ? s + 31 - __clz(lt) : -1;
+}
+
+// ---------------------------------------------------------------------------
 // Steps A + B + C (Algorithms 3, 4, 5): fused edge-parallel cycle search
 // ---------------------------------------------------------------------------
 
@@ -735,7 +1068,10 @@ struct LookupQueue {
 
 // Resolve the queued requests head .. head + k - 1 (k <= 32, lane x takes
 // request head + x): Bloom probe for long columns, then the column search
-// (per lane up to kCoopMin rows, warp-cooperative above) or the hash probe;
+// (per lane up to kCoopMin rows, warp-cooperative above), or the hash probe,
+// or with row marking the search of row m_j's entries (CSC positions,
+// ascending) for the one inside column m_i's positions [lo, lo + len) (per
+// lane, warp-cooperative above kCoopMin entries);
 // a closing entry found gives the gain in the fixed order
 // ((w_ij + w_q) - w(i, m_i)) - w(m_j, j), and a positive gain goes into the
 // root's Step-C record (maximum gain, then lowest position; Algorithm 5).
@@ -745,7 +1081,8 @@ __device__ __forceinline__ void resolve_lookups(
     const LookupQueue &qu, int head, int k, int lane, const int32_t *__restrict__ rowidx,
     const double *__restrict__ wv, const double *__restrict__ wm, const double *__restrict__ wmr,
     const unsigned long long *__restrict__ htab, const uint32_t *__restrict__ bloom,
-    Rec *__restrict__ best, uint32_t *winbits, Ctl *ctl, uint32_t &n_found, uint32_t &n_pos)
+    const int32_t *__restrict__ trowptr, const int32_t *__restrict__ tpos, int32_t nnz, Rec *__restrict__ best, uint32_t *winbits,
+    Ctl *ctl, uint32_t &n_found, uint32_t &n_pos)
 {
     const int x = (head + lane) & (kQueue - 1);
     const bool act = lane < k;
@@ -767,6 +1104,47 @@ __device__ __forceinline__ void resolve_lookups(
                 break;
             if (++pos == hbase + hsize)
                 pos = hbase;
+        }
+    } else if (kLookup == AWPM_LOOKUP_ROWMARK) {
+        // column m_i's positions are [a, b); row m_j's entries tpos[lo, lo + len)
+        const int32_t a = lo, b = lo + len;
+        if (act) {
+            lo = __ldg(trowptr + mj);
+            len = __ldg(trowptr + mj + 1) - lo;
+            if (lo < 0 || len < 0 || len > nnz - lo) {
+                lo = 0;
+                len = 0;
+                raise_err(ctl, kErrInternal);
+            }
+        }
+        unsigned longm = __ballot_sync(FULL_MASK, len > kCoopMin);
+        while (longm) {
+            const int src = __ffs(longm) - 1;
+            longm &= longm - 1;
+            const int32_t ss = __shfl_sync(FULL_MASK, lo, src);
+            const int32_t sl = __shfl_sync(FULL_MASK, len, src);
+            const int32_t sb = __shfl_sync(FULL_MASK, b, src);
+            const int32_t f = coop_last_below(tpos, ss, sl, sb, lane);
+            if (lane == src) {
+                const int32_t v = f >= 0 ? __ldg(tpos + f) : -1;
+                q = v >= a ? v : -1;
+                len = 0;
+            }
+        }
+        // short rows: the last entry below column m_i's end, per lane
+        const int32_t s0 = lo;
+        int32_t hi = lo + len;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (__ldg(tpos + mid) < b)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        if (len > 0 && lo > s0) {
+            const int32_t v = __ldg(tpos + lo - 1);
+            if (v >= a)
+                q = v;
         }
     } else {
         if (bloom && len > kBloomMin) {
@@ -858,6 +1236,9 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
     const double *__restrict__ wmr = W->wmr;
     const unsigned long long *__restrict__ htab = W->htab;
     const uint32_t *__restrict__ bloom = W->bloom;
+    const unsigned long long *__restrict__ rowsig = W->rowsig;
+    const int32_t *__restrict__ trowptr = W->trowptr;
+    const int32_t *__restrict__ tpos = W->tpos;
     Rec *__restrict__ best = W->best;
     uint32_t *winbits = W->winbits;
     Ctl *ctl = W->ctl;
@@ -876,8 +1257,8 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
 
     auto flush = [&](int k) {
         __syncwarp();
-        resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, wmr, htab, bloom, best,
-                                 winbits, ctl, n_found, n_pos);
+        resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, wmr, htab, bloom, trowptr,
+                                 tpos, nnz, best, winbits, ctl, n_found, n_pos);
         __syncwarp();
         qhead = (qhead + k) & (kQueue - 1);
         qn -= k;
@@ -956,11 +1337,17 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
                 if (cand[u]) {
                     ++n_cand;
                     rec[u] = ld_rowrec(rr + iv[u], pol);
+                    if (kLookup == AWPM_LOOKUP_ROWMARK)
+                        rec[u].sig = __ldg(rowsig + mjv[u]);  // the mark of row m_j
                 }
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const bool pass = cand[u] && sig_has(rec[u].sig, mjv[u]);
+                // column m_i (first position rec.s) marked by row m_j, or row
+                // m_j in column m_i's signature
+                const bool pass = cand[u] && (kLookup == AWPM_LOOKUP_ROWMARK
+                                                  ? sig_has(rec[u].sig, rec[u].s)
+                                                  : sig_has(rec[u].sig, mjv[u]));
                 const unsigned need = __ballot_sync(FULL_MASK, pass);
                 if (pass) {
                     const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
@@ -2098,6 +2485,22 @@ void launch_init(const Work *d, const Shape &sh, Sink &k)
         k.launch((const void *)k_batch_check, init_tile_grid(sh), kThreads, a);
     if (sh.lookup == AWPM_LOOKUP_HASH)
         k.launch((const void *)k_hash_build, init_tile_grid(sh), kThreads, a);
+    if (sh.lookup == AWPM_LOOKUP_ROWMARK) {
+        k.launch((const void *)k_rm_marks, init_tile_grid(sh), kThreads, a);
+        // four passes cover every row index; the unneeded ones return at once.
+        // Grids: the resident blocks (scatter: 48 registers, 36 KB shared)
+        const unsigned rs_grid = (unsigned)sh.num_sms * 8;
+        const unsigned sc_grid = (unsigned)sh.num_sms * 5;
+        for (int pass = 0; pass < 4; ++pass) {
+            void *ap[] = {(void *)&d, (void *)&pass};
+            k.launch((const void *)k_rs_hist, rs_grid, kRsThreads, ap);
+            k.launch((const void *)k_rs_scan_a, rs_grid, kRsThreads, ap);
+            k.launch((const void *)k_rs_scan_b, 1, kRsThreads, ap);
+            k.launch((const void *)k_rs_scan_c, rs_grid, kRsThreads, ap);
+            k.launch((const void *)k_rs_scatter, sc_grid, kRsThreads, ap);
+        }
+        k.launch((const void *)k_rm_rowptr, init_grid(sh), kThreads, a);
+    }
 }
 
 void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k)
@@ -2126,6 +2529,9 @@ static int bps_of()
 template <bool kWide>
 static const void *search_fn(int lookup, bool batch)
 {
+    if (lookup == AWPM_LOOKUP_ROWMARK)
+        return batch ? (const void *)k_search<AWPM_LOOKUP_ROWMARK, true, kWide>
+                     : (const void *)k_search<AWPM_LOOKUP_ROWMARK, false, kWide>;
     if (lookup == AWPM_LOOKUP_HASH)
         return batch ? (const void *)k_search<AWPM_LOOKUP_HASH, true, kWide>
                      : (const void *)k_search<AWPM_LOOKUP_HASH, false, kWide>;
@@ -2135,6 +2541,13 @@ static const void *search_fn(int lookup, bool batch)
 
 int search_blocks_per_sm(int lookup, bool batch, bool wide)
 {
+    if (lookup == AWPM_LOOKUP_ROWMARK) {
+        if (wide)
+            return batch ? bps_of<AWPM_LOOKUP_ROWMARK, true, true>()
+                         : bps_of<AWPM_LOOKUP_ROWMARK, false, true>();
+        return batch ? bps_of<AWPM_LOOKUP_ROWMARK, true, false>()
+                     : bps_of<AWPM_LOOKUP_ROWMARK, false, false>();
+    }
     if (wide) {
         if (lookup == AWPM_LOOKUP_HASH)
             return batch ? bps_of<AWPM_LOOKUP_HASH, true, true>()

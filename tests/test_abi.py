@@ -75,3 +75,18 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(awpm, "_lib_handle", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         awpm.lib()
+
+
+def test_constants_match_header():
+    """Every #define of the header has the same value in the binding (the
+    error codes through the ERRORS table)."""
+    from paper_1801_09809_gb300 import awpm
+    defines = dict(re.findall(r"#define AWPM_(\w+) +(\d+)u?\b", open(HEADER).read()))
+    assert defines
+    for name, value in defines.items():
+        if name.startswith("ERR_"):
+            assert awpm.ERRORS[int(value)] == name[4:], name
+        elif name == "OK":
+            assert awpm.AWPM_OK == int(value)
+        else:
+            assert getattr(awpm, name) == int(value), name

@@ -55,7 +55,7 @@ def check_batch(ctx, graphs, torch, max_iters=0, host=False, select=0):
 def test_batch_mixed_structures(torch):
     specs = gen.batch_spec(48, seed=424242)
     graphs = [gen.build_spec(sp) for sp in specs]
-    for lookup in (awpm.LOOKUP_BSEARCH, awpm.LOOKUP_HASH):
+    for lookup in (awpm.LOOKUP_BSEARCH, awpm.LOOKUP_HASH, awpm.LOOKUP_ROWMARK):
         ctx = awpm.awpm_create(device=0, lookup=lookup)
         try:
             check_batch(ctx, graphs, torch)

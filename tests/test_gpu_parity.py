@@ -329,10 +329,11 @@ def test_context_reuse_across_sizes(ctx, orc, torch):
         check(ctx, orc, g, torch)
 
 
-@pytest.mark.parametrize("lookup", [awpm.LOOKUP_BSEARCH, awpm.LOOKUP_HASH], ids=["bsearch", "hash"])
+@pytest.mark.parametrize("lookup", [awpm.LOOKUP_BSEARCH, awpm.LOOKUP_HASH, awpm.LOOKUP_ROWMARK],
+                         ids=["bsearch", "hash", "rowmark"])
 def test_lookup_strategies(torch, orc, lookup):
-    """Both closing-edge lookups (binary search, per-column hash table) give
-    the oracle's result, ties and dense columns included."""
+    """The three closing-edge lookups (binary search, per-column hash table,
+    row marking) give the oracle's result, ties and dense columns included."""
     c = awpm.awpm_create(device=0, lookup=lookup)
     try:
         graphs = [gen.stencil_3d(14, 141), gen.rmat(1 << 14, 16, 142), gen.config1(),
@@ -398,3 +399,38 @@ def test_greedy_selection(torch, orc, flags):
     finally:
         awpm.awpm_destroy(c)
 
+
+
+def arrow_graph(n, seed):
+    """Planted diagonal plus a full row 0 and a full column 0: row 0's
+    neighbourhood is long (warp-cooperative search) and every other row is
+    short."""
+    rng = np.random.default_rng(seed)
+    rows = np.concatenate([np.arange(n), np.zeros(n, dtype=np.int64), np.arange(n)])
+    cols = np.concatenate([np.arange(n), np.arange(n), np.zeros(n, dtype=np.int64)])
+    colptr, rowidx = gen._csc_from_coo(n, rows, cols)
+    w = rng.standard_normal(len(rowidx))
+    return gen.Graph(n, colptr, rowidx, w, np.arange(n, dtype=np.int32), f"arrow_{n}")
+
+
+@pytest.mark.parametrize("flags", [0, awpm.FLAG_TIME_SEARCH], ids=["graph", "timed"])
+def test_row_marking_transpose_and_selections(torch, orc, flags):
+    """Row marking (Section 4) on the shapes its transpose must handle: one,
+    two and three radix passes (n up to 256, up to 65,536, above), a row with
+    thousands of entries, hub rows, empty-free ragged tails; under Step D
+    and the Pettie-Sanders selection; every result equals the oracle's row
+    marking mode and its column-search mode."""
+    graphs = [gen.random_small(200, 0.05, 161), gen.stencil_2d(300, 162),
+              gen.rmat(1 << 17, 8, 163), arrow_graph(3000, 164), gen.banded(70001, 7, 165)]
+    for sel in (awpm.SELECT_STEP_D, awpm.SELECT_GREEDY):
+        c = awpm.awpm_create(device=0, lookup=awpm.LOOKUP_ROWMARK, select=sel, flags=flags)
+        try:
+            for g in graphs:
+                ref, rst, _ = orc.improve(g, select=sel, row_marking=True)
+                ref2, _, _ = orc.improve(g, select=sel)
+                assert ref.tolist() == ref2.tolist()
+                got, st = run_gpu(c, g, torch=torch)
+                assert_same_as_oracle(g, got, st, ref, rst, f"{g.name} rowmark sel={sel}")
+                assert st["lookup_used"] == awpm.LOOKUP_ROWMARK
+        finally:
+            awpm.awpm_destroy(c)
