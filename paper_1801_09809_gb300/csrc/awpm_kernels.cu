@@ -1326,6 +1326,7 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
                 mjv[u] = valid[u] ? ld_i32_last(mc + jv[u], pol) : 0x7fffffff;
             }
             RowRec rec[kU];
+            unsigned long long mark[kU];
             bool cand[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
@@ -1334,20 +1335,20 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
                 cand[u] = valid[u] && iv[u] > mjv[u];
                 rec[u].s = rec[u].e = 0;
                 rec[u].sig = 0ull;
+                mark[u] = 0ull;
                 if (cand[u]) {
                     ++n_cand;
                     rec[u] = ld_rowrec(rr + iv[u], pol);
                     if (kLookup == AWPM_LOOKUP_ROWMARK)
-                        rec[u].sig = __ldg(rowsig + mjv[u]);  // the mark of row m_j
+                        mark[u] = __ldg(rowsig + mjv[u]);  // the mark of row m_j
                 }
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                // column m_i (first position rec.s) marked by row m_j, or row
-                // m_j in column m_i's signature
-                const bool pass = cand[u] && (kLookup == AWPM_LOOKUP_ROWMARK
-                                                  ? sig_has(rec[u].sig, rec[u].s)
-                                                  : sig_has(rec[u].sig, mjv[u]));
+                // row m_j in column m_i's signature; with row marking also
+                // column m_i (first position rec.s) marked by row m_j
+                const bool pass = cand[u] && sig_has(rec[u].sig, mjv[u]) &&
+                                  (kLookup != AWPM_LOOKUP_ROWMARK || sig_has(mark[u], rec[u].s));
                 const unsigned need = __ballot_sync(FULL_MASK, pass);
                 if (pass) {
                     const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
