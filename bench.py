@@ -398,6 +398,31 @@ def bench_selection(awpm, torch, dev, reps=3):
     return res
 
 
+def bench_lookups(awpm, torch, dev, g, reps=3):
+    """The three closing-entry lookups on the bench graph (inputs resident):
+    column search with Bloom filters, per-column hash tables, and the
+    paper's row marking (row marks plus a radix-sorted transpose, Section 4):
+    solve time, and whether each gives the column search's matching."""
+    t = [torch.from_numpy(a).to(dev) for a in (g.colptr, g.rowidx, g.weight, g.mate)]
+    res, first = {}, None
+    for name, lk in (("bsearch", awpm.LOOKUP_BSEARCH), ("hash", awpm.LOOKUP_HASH),
+                     ("rowmark", awpm.LOOKUP_ROWMARK)):
+        out = torch.empty_like(t[3])
+        ctx = awpm.awpm_create(device=dev.index or 0, lookup=lk)
+        st = awpm.awpm_improve_ctx(ctx, g.n, *t, out)
+        ms = []
+        for _ in range(reps):
+            st = awpm.awpm_improve_ctx(ctx, g.n, *t, out)
+            ms.append(st["ms_total"])
+        awpm.awpm_destroy(ctx)
+        m = out.cpu().numpy()
+        first = m if first is None else first
+        res[name] = {"ms": statistics.median(ms), "passes": st["iterations"],
+                     "lookup_used": st["lookup_used"],
+                     "same_matching": bool(np.array_equal(m, first))}
+    return res
+
+
 def bench_batched(awpm, torch, dev, count):
     """4,096 matrices (n log-uniform in [200, 20000], random sparse / 2D 5-point /
     banded): one batched graph launch vs one launch per matrix, same GPU,
@@ -690,6 +715,7 @@ def main():
         line["greedy"] = bench_greedy(awpm, torch, dev, g)
         line["selection"] = bench_selection(awpm, torch, dev)
         line["pipeline"] = bench_pipeline(awpm, torch, dev, g)
+        line["lookups"] = bench_lookups(awpm, torch, dev, g)
     if not args.no_batched:
         line["batched"] = bench_batched(awpm, torch, dev, args.batch_count)
     if not args.no_served:
