@@ -536,6 +536,12 @@ def bench_served(awpm, torch, dev, requests, pool_size, budget=100 * 10**9):
     same_b = all(np.array_equal(outs[r].numpy(), refs[pick[r]]) for r in range(requests))
     awpm.awpm_destroy(solo)
     ms = lambda a, q: float(1e3 * np.percentile(a, q))
+    # the served form across offered loads (fractions of its capacity)
+    sweep = []
+    for load in (0.3, 0.5, 0.9):
+        lat_x, tot_x = serve(gen.poisson_arrivals(requests, load * capacity))
+        sweep.append({"load": load, "rate_per_s": load * capacity, "p50_ms": ms(lat_x, 50),
+                      "p99_ms": ms(lat_x, 99), "solves_per_s": requests / tot_x})
     return {"workload": f"{requests} requests from a pool of {pool_size} generated problems "
                         "(n log-uniform [1e3, 1e6]; random sparse, 2D, 3D, R-MAT; degree 4-27), "
                         "pinned host inputs, Poisson arrivals",
@@ -544,6 +550,7 @@ def bench_served(awpm, torch, dev, requests, pool_size, budget=100 * 10**9):
                        "solves_per_s": requests / tot_s},
             "one_launch_per_matrix": {"p50_ms": ms(lat_b, 50), "p99_ms": ms(lat_b, 99),
                                       "solves_per_s": requests / tot_b},
+            "served_load_sweep": sweep,
             "slots": 4, "budget_bytes": budget,
             "identical_outputs": bool(same_s and same_b)}
 
