@@ -522,15 +522,15 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
 // mc = mate_in, mr = its inverse, and the row record and matched weight of
 // every row; checks that mate_in is a permutation over stored entries (the
 // entry pass left wm[j] = NaN where (mate_in[j], j) is not stored).  Each
-// thread takes four columns per round and issues their loads together: the
+// thread takes eight columns per round and issues their loads together: the
 // scattered writes by row and the inverse's compare-and-swap are latency
-// bound, so the rounds overlap four of them.
+// bound, so the rounds overlap eight of them.
 __global__ void k_init_mates(const Work *__restrict__ W)
 {
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    constexpr int kU = 4;
+    constexpr int kU = 8;
     const int64_t stride = gstride();
     const int32_t n = w.n;
     for (int64_t j0 = gtid(); j0 < n; j0 += kU * stride) {
