@@ -359,6 +359,15 @@ def bench_pipeline(awpm, torch, dev, g, reps=3):
     awpm.awpm_destroy(ctx)
     rows = rows[1:]
     med = [statistics.median(r[k] for r in rows) for k in range(4)]
+    # the maximum matching with its phases and levels driven from the host
+    # (one launch per kernel, a synchronisation per level): what the graph
+    # form saves, and launches a profiler can list
+    ctx = awpm.awpm_create(device=dev.index or 0, lookup=awpm.LOOKUP_BSEARCH,
+                           flags=awpm.FLAG_TIME_SEARCH)
+    awpm.awpm_greedy(ctx, g.n, cp, ri, w, m)
+    mh = awpm.awpm_mcm(ctx, g.n, cp, ri, w, m)
+    same_host = bool(np.array_equal(m.cpu().numpy(), mcm_out))
+    awpm.awpm_destroy(ctx)
     orc = oracle.get()
     gm, _ = orc.greedy(g)
     t0 = time.perf_counter()
@@ -370,6 +379,7 @@ def bench_pipeline(awpm, torch, dev, g, reps=3):
             "mcm_cardinality": ms["cardinality"], "passes": st["iterations"],
             "greedy_ms": med[0], "mcm_ms": med[1], "improve_ms": med[2],
             "pipeline_ms_host_clock": med[3],
+            "mcm_host_loop_ms": mh["ms_total"], "mcm_host_loop_identical": same_host,
             "mcm_identical_to_oracle": bool(np.array_equal(om, mcm_out)),
             "mcm_cpu_oracle_s": cpu_s, "mcm_speedup_vs_cpu_oracle": cpu_s / (med[1] * 1e-3)}
 

@@ -12,6 +12,7 @@
 // graph serves every problem of the context.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -1372,7 +1373,9 @@ int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *row
     AWPM_TRY(ensure(c, c->mfront, sizeof(uint32_t) * words));
     AWPM_TRY(ensure(c, c->mcolof, sizeof(int32_t) * ((size_t)nnz + 1)));
     AWPM_TRY(ensure(c, c->mnext, sizeof(uint32_t) * words));
-    AWPM_TRY(ensure(c, c->mtiles, sizeof(int32_t) * ((size_t)ntiles + 1)));
+    // the level's tile list: at most min(nnz, nnz/32 + 2n) entries
+    const size_t tiles_cap = std::min((size_t)nnz, (size_t)ntiles + 2 * (size_t)n);
+    AWPM_TRY(ensure(c, c->mtiles, sizeof(int32_t) * (tiles_cap + 1)));
     AWPM_TRY(ensure(c, c->tile_col, sizeof(int32_t) * ((size_t)ntiles + 1)));
     AWPM_TRY(ensure(c, c->starts, sizeof(uint32_t) * (((size_t)nnz + 31) / 32 + 1)));
     AWPM_TRY(ensure(c, c->ctl, sizeof(Ctl)));

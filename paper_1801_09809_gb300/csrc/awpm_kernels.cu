@@ -2179,41 +2179,53 @@ __global__ void k_mc_phase(const Work *__restrict__ W)
     warp_add_i32(live, &w.ctl->live);
 }
 
-// Level, step 0: list the 32-entry tiles that hold an entry of a frontier
-// column.  A tile covers the columns from its first entry's column to the
-// next tile's first column (a superset: the lanes check their own column).
-// The list's order is free: every level step below takes the same decisions
-// in any order of its tiles.
+// Level, step 0: list the 32-entry tiles holding an entry of a frontier
+// column: every frontier column (a set bit of the frontier bitmap, a thread
+// per bitmap word) appends the tiles its entries span, one atomic per warp.
+// A tile shared by two frontier columns is listed twice: the level steps
+// below take the same decisions however often, and in whatever order, a
+// tile comes (maxima, minima and writes of equal values), so the list needs
+// neither order nor uniqueness.  It holds at most min(nnz, nnz/32 + 2n)
+// entries (a column spans at most len/32 + 2 tiles, and at most len).
 __global__ void k_mc_tiles(const Work *__restrict__ W)
 {
     const Work &w = *W;
     if (w.ctl->err)
         return;
     const int lane = threadIdx.x & 31;
-    for (int64_t t0 = gtid() - lane; t0 < w.ntiles; t0 += gstride()) {
-        const int64_t t = t0 + lane;
-        bool act = false;
-        if (t < w.ntiles) {
-            const int32_t c0 = __ldg(w.tile_col + t);
-            const int32_t c1 = t + 1 < w.ntiles ? __ldg(w.tile_col + t + 1) : w.n - 1;
-            for (int32_t x = c0 >> 5; x <= (c1 >> 5) && !act; ++x) {
-                uint32_t bits = w.mfront[x];
-                if (x == (c0 >> 5))
-                    bits &= ~0u << (c0 & 31);
-                if (x == (c1 >> 5) && (c1 & 31) != 31)
-                    bits &= (2u << (c1 & 31)) - 1u;
-                act = bits != 0u;
-            }
+    const int64_t words = (int64_t)w.n / 32 + 1;
+    for (int64_t x0 = gtid() - lane; x0 < words; x0 += gstride()) {
+        const int64_t x = x0 + lane;
+        const uint32_t front = x < words ? w.mfront[x] : 0u;
+        // tiles this lane's columns span
+        int32_t mine = 0;
+        for (uint32_t bits = front; bits; bits &= bits - 1) {
+            const int64_t c = x * 32 + __ffs(bits) - 1;
+            const int32_t s = __ldg(w.colptr + c), e = __ldg(w.colptr + c + 1);
+            if (e > s)
+                mine += ((e - 1) >> 5) - (s >> 5) + 1;
         }
-        const unsigned m = __ballot_sync(FULL_MASK, act);
-        if (!m)
+        int32_t incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        const int32_t total = __shfl_sync(FULL_MASK, incl, 31);
+        if (total == 0)
             continue;
-        int base = 0;
+        int32_t base = 0;
         if (lane == 0)
-            base = atomicAdd(&w.ctl->level_tiles, __popc(m));
-        base = __shfl_sync(FULL_MASK, base, 0);
-        if (act)
-            w.mtiles[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)t;
+            base = atomicAdd(&w.ctl->level_tiles, total);
+        int32_t at = __shfl_sync(FULL_MASK, base, 0) + incl - mine;
+        for (uint32_t bits = front; bits; bits &= bits - 1) {
+            const int64_t c = x * 32 + __ffs(bits) - 1;
+            const int32_t s = __ldg(w.colptr + c), e = __ldg(w.colptr + c + 1);
+            if (e > s)
+                for (int32_t t = s >> 5; t <= ((e - 1) >> 5); ++t)
+                    w.mtiles[at++] = t;
+        }
     }
 }
 
@@ -2693,11 +2705,13 @@ void launch_mcm_phase(const Work *d, const Shape &sh, Sink &k)
 void launch_mcm_level(const Work *d, const Shape &sh, Sink &k)
 {
     void *a[] = {(void *)&d};
-    k.launch((const void *)k_mc_tiles, init_tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_mc_offer_max, init_tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_mc_offer_min, init_tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_mc_join, init_tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_mc_end, init_tile_grid(sh), kThreads, a);
+    // one wave of blocks: a level's work follows its frontier, and a small
+    // frontier should not pay for launching idle blocks
+    k.launch((const void *)k_mc_tiles, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_offer_max, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_offer_min, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_join, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_end, tile_grid(sh), kThreads, a);
     k.launch((const void *)k_mc_advance, util_grid(sh), kThreads, a);
 }
 
