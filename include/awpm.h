@@ -290,12 +290,16 @@ int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
  * lower column); a tree ends at the free row with the heaviest last edge
  * (equal weights: lower row) and stops growing; all trees with an end are
  * augmented; a phase that augments nothing ends the search.  Columns
- * without entries are allowed (they stay unmatched).
+ * without entries are allowed (they stay unmatched).  The phase and level
+ * loops run on the device in one graph launch (nested conditional WHILE
+ * nodes); with AWPM_FLAG_TIME_SEARCH the host drives them instead, one
+ * launch per kernel (same result).
  *   stats (may be NULL): phases (the last, augmenting nothing, included),
  *     cardinality, elapsed milliseconds, search levels.
  * Errors: AWPM_ERR_INVALID_ARG, _UNSORTED_OR_DUP, _NONFINITE as for
  * awpm_improve; AWPM_ERR_NOT_PERFECT when mate is not a matching over
- * stored entries.
+ * stored entries; AWPM_ERR_TIMEOUT if a search phase exceeded n + 1 levels
+ * (a bound no correct search reaches).
  */
 typedef struct {
     int32_t phases;
