@@ -1383,18 +1383,27 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
 // second matched edge at column k = m_i: drop it if column k is itself the
 // root of a Step-C winner, otherwise compete for key k (maximum gain, then
 // lowest root j).  The winner's key (or -1) is kept for the flip.
+// A warp loads 32 bitmap words at a time and takes their nonzero words one
+// by one, lane b handling the winner at bit b, so the winners of a word are
+// handled side by side rather than one after another.
 __global__ void k_select(const Work *__restrict__ W)
 {
     const Work &w = *W;
     if (!gate(w.ctl))
         return;
+    const int lane = threadIdx.x & 31;
     const int64_t words = (int64_t)w.n / 32 + 1;
-    for (int64_t x = gtid(); x < words; x += gstride()) {
-        uint32_t bits = w.winbits[x];
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const int32_t j = (int32_t)(x * 32 + b);
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t x0 = (gtid() >> 5) * 32; x0 < words; x0 += nwarps * 32) {
+        const uint32_t mine = x0 + lane < words ? w.winbits[x0 + lane] : 0u;
+        unsigned nz = __ballot_sync(FULL_MASK, mine != 0u);
+        while (nz) {
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1;
+            const uint32_t bits = __shfl_sync(FULL_MASK, mine, src);
+            if (!((bits >> lane) & 1u))
+                continue;
+            const int32_t j = (int32_t)((x0 + src) * 32 + lane);
             const Rec r = w.best[j];
             const int32_t i = __ldg(w.rowidx + r.p);
             const int32_t k = w.mr[i];
@@ -1403,69 +1412,80 @@ __global__ void k_select(const Work *__restrict__ W)
                 continue;
             }
             w.wkey[j] = k;
-            Sel s;
-            s.g = r.g;
-            s.j = j;
-            s.pad = 0;
-            sel_combine(w.dsel + k, s, w.ctl);
+            Sel sl;
+            sl.g = r.g;
+            sl.j = j;
+            sl.pad = 0;
+            sel_combine(w.dsel + k, sl, w.ctl);
         }
     }
 }
 
 // Flip every selected cycle: column j takes row i, key column k takes m_j;
 // the row records of rows i and m_j follow their new mates.  The selected
-// cycles are vertex-disjoint, so each thread owns its four vertices.  Each
-// thread also clears the Step-C records and winner bits it visited, which
-// leaves them empty for the next pass.
+// cycles are vertex-disjoint, so each lane owns its four vertices.  The
+// Step-C records and winner bits visited are cleared, which leaves them
+// empty for the next pass.  Words of the winner bitmap are taken as in
+// k_select; in a batched solve the flips of a word are counted per matrix
+// with one atomic per matrix (the word's columns are consecutive).
 __global__ void k_flip(const Work *__restrict__ W)
 {
     const Work &w = *W;
     unsigned long long flips = 0;
     if (gate(w.ctl)) {
+        const int lane = threadIdx.x & 31;
         const int64_t words = (int64_t)w.n / 32 + 1;
-        for (int64_t x = gtid(); x < words; x += gstride()) {
-            uint32_t bits = w.winbits[x];
-            if (!bits)
-                continue;
-            w.winbits[x] = 0u;
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int32_t j = (int32_t)(x * 32 + b);
-                const Rec r = w.best[j];
-                w.best[j] = Rec{0.0, 0, 0};
-                const int32_t k = w.wkey[j];
-                if (k < 0)
-                    continue;
-                const Sel s = w.dsel[k];
-                if (gbits(s.g) <= 0ll || s.j != j)
-                    continue;  // another root won key k
-                w.dsel[k] = Sel{0.0, 0, 0};
-                const int32_t i = w.rowidx[r.p];
-                const int32_t mj = w.mc[j];
-                const double wij = w.w[r.p];
-                const double wq = w.w[r.q];
-                w.mc[j] = i;
-                w.mr[i] = j;
-                w.mc[k] = mj;
-                w.mr[mj] = k;
-                w.wm[j] = wij;
-                w.wm[k] = wq;
-                RowRec a;
-                a.s = w.colptr[j];
-                a.e = w.colptr[j + 1];
-                a.sig = w.colsig[j];
-                w.rr[i] = a;
-                w.wmr[i] = wij;
-                RowRec c;
-                c.s = w.colptr[k];
-                c.e = w.colptr[k + 1];
-                c.sig = w.colsig[k];
-                w.rr[mj] = c;
-                w.wmr[mj] = wq;
-                ++flips;
-                if (w.bw.count > 0)
-                    atomicAdd(w.bw.mflips + w.bw.colmat[k], 1ull);
+        const int64_t nwarps = gstride() >> 5;
+        for (int64_t x0 = (gtid() >> 5) * 32; x0 < words; x0 += nwarps * 32) {
+            const uint32_t mine = x0 + lane < words ? w.winbits[x0 + lane] : 0u;
+            if (mine)
+                w.winbits[x0 + lane] = 0u;
+            unsigned nz = __ballot_sync(FULL_MASK, mine != 0u);
+            while (nz) {
+                const int src = __ffs(nz) - 1;
+                nz &= nz - 1;
+                const uint32_t bits = __shfl_sync(FULL_MASK, mine, src);
+                int32_t mat = -1;  // matrix of a flipped cycle (batched solve)
+                if ((bits >> lane) & 1u) {
+                    const int32_t j = (int32_t)((x0 + src) * 32 + lane);
+                    const Rec r = w.best[j];
+                    w.best[j] = Rec{0.0, 0, 0};
+                    const int32_t k = w.wkey[j];
+                    const Sel sl = k >= 0 ? w.dsel[k] : Sel{0.0, 0, 0};
+                    if (k >= 0 && gbits(sl.g) > 0ll && sl.j == j) {
+                        w.dsel[k] = Sel{0.0, 0, 0};
+                        const int32_t i = w.rowidx[r.p];
+                        const int32_t mj = w.mc[j];
+                        const double wij = w.w[r.p];
+                        const double wq = w.w[r.q];
+                        w.mc[j] = i;
+                        w.mr[i] = j;
+                        w.mc[k] = mj;
+                        w.mr[mj] = k;
+                        w.wm[j] = wij;
+                        w.wm[k] = wq;
+                        RowRec a;
+                        a.s = w.colptr[j];
+                        a.e = w.colptr[j + 1];
+                        a.sig = w.colsig[j];
+                        w.rr[i] = a;
+                        w.wmr[i] = wij;
+                        RowRec c;
+                        c.s = w.colptr[k];
+                        c.e = w.colptr[k + 1];
+                        c.sig = w.colsig[k];
+                        w.rr[mj] = c;
+                        w.wmr[mj] = wq;
+                        ++flips;
+                        if (w.bw.count > 0)
+                            mat = w.bw.colmat[k];
+                    }
+                }
+                if (w.bw.count > 0) {
+                    const unsigned peers = __match_any_sync(FULL_MASK, mat);
+                    if (mat >= 0 && (peers & ((1u << lane) - 1u)) == 0u)
+                        atomicAdd(w.bw.mflips + mat, (unsigned long long)__popc(peers));
+                }
             }
         }
     }
