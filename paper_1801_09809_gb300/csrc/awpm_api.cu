@@ -615,7 +615,7 @@ void teardown_ctx(awpm_ctx *c)
     DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->wmr,
                       &c->colsig,  &c->best,     &c->dsel,     &c->tile_col, &c->starts,
                       &c->ctl,     &c->wpart,    &c->htab,     &c->b_noff,   &c->b_colmat,
-                      &c->b_tilemat, &c->b_i32,  &c->b_u64,    &c->b_f64,    &c->s_colptr,
+                      &c->b_tilemat, &c->b_tlist, &c->b_i32,  &c->b_u64,    &c->b_f64,    &c->s_colptr,
                       &c->s_rowidx, &c->s_w,     &c->s_mate,   &c->s_out,    &c->s_gain,
                       &c->s_row,   &c->d_work,   &c->winbits,  &c->wkey,     &c->bloom,    &c->gckey,
                       &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate,
@@ -820,7 +820,8 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
         AWPM_TRY(stage_in(c, c->b_noff, r.n_off, (size_t)count + 1, l_off, &bw.n_off));
         AWPM_TRY(ensure(c, c->b_colmat, sizeof(int32_t) * n));
         AWPM_TRY(ensure(c, c->b_tilemat, sizeof(int32_t) * ((size_t)ntiles + 1)));
-        AWPM_TRY(ensure(c, c->b_i32, sizeof(int32_t) * (5 * (size_t)count + 1)));
+        AWPM_TRY(ensure(c, c->b_i32, sizeof(int32_t) * (5 * (size_t)count + 2)));
+        AWPM_TRY(ensure(c, c->b_tlist, sizeof(int32_t) * ((size_t)ntiles + 1)));
         AWPM_TRY(ensure(c, c->b_u64, sizeof(unsigned long long) * 2 * (size_t)count));
         AWPM_TRY(ensure(c, c->b_f64, sizeof(double) * 2 * (size_t)count));
         bw.colmat = (int32_t *)c->b_colmat.p;
@@ -831,6 +832,8 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
         bw.mconv = i32 + 2 * (size_t)count;
         bw.mnnz = i32 + 3 * (size_t)count;
         bw.active = i32 + 5 * (size_t)count;
+        bw.tlist_n = i32 + 5 * (size_t)count + 1;
+        bw.tlist = (int32_t *)c->b_tlist.p;
         unsigned long long *u64 = (unsigned long long *)c->b_u64.p;
         bw.mflips = u64;
         bw.mcycles = u64 + count;

@@ -100,7 +100,7 @@ struct awpm_ctx {
     awpm::DevBuf mroot, mrpar, mfront, mnext, mrkey, mrcol, mtkey, mtrow, mstage,
         mcolof, mtiles;  // maximum matching
     awpm::DevBuf rowsig, trowptr, rs_k0, rs_k1, rs_v0, rs_v1, rs_hist, rs_sums;  // row marking
-    awpm::DevBuf b_noff, b_colmat, b_tilemat, b_i32, b_u64, b_f64;
+    awpm::DevBuf b_noff, b_colmat, b_tilemat, b_tlist, b_i32, b_u64, b_f64;
     // staging of host-resident arrays
     awpm::DevBuf s_colptr, s_rowidx, s_w, s_mate, s_out, s_gain, s_row;
     awpm::DevBuf d_work;             // device copy of the Work descriptor

@@ -84,6 +84,9 @@ struct BatchWork {
     double *mw_in;
     double *mw_out;
     int32_t *active;        // matrices still running after a pass
+    int32_t *tlist;         // tiles the next pass searches (running matrices,
+                            // and every tile spanning two matrices)
+    int32_t *tlist_n;       // their number
 };
 
 // Tile whose nonzeros all belong to one matrix.

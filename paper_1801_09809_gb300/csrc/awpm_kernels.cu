@@ -343,8 +343,10 @@ __global__ void k_reset(const Work *__restrict__ W)
         c->positive = 0ull;
         c->weight_in = 0.0;
         c->weight_out = 0.0;
-        if (w.bw.count > 0)
+        if (w.bw.count > 0) {
             *w.bw.active = 0;
+            *w.bw.tlist_n = 0;
+        }
     }
     for (int64_t j = gtid(); j < w.n; j += gstride()) {
         w.mr[j] = -1;
@@ -698,6 +700,38 @@ __global__ void __launch_bounds__(kThreads) k_batch_check(const Work *__restrict
         raise_err(w.ctl, kErrInvalid);
     for (int64_t b = gtid(); b < bw.count; b += gstride())
         bw.mnnz[b] = w.colptr[bw.n_off[b + 1]] - w.colptr[bw.n_off[b]];
+}
+
+// The tiles the next pass of a batched solve searches: those of matrices
+// still running, and every tile spanning two matrices (its lanes of a
+// finished matrix are skipped in the search).  Each tile at most once; the
+// list's order (warp-aggregated appends) does not change any result, since
+// the search's records and counters are order-free.  The count was zeroed
+// by the reset (first pass) or the end-of-pass control.
+__global__ void k_batch_list(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    const BatchWork &bw = w.bw;
+    const int lane = threadIdx.x & 31;
+    for (int64_t t0 = gtid() - lane; t0 < w.ntiles; t0 += gstride()) {
+        const int64_t t = t0 + lane;
+        bool keep = false;
+        if (t < w.ntiles) {
+            const int32_t tm = __ldg(bw.tilemat + t);
+            keep = !(tm & kTileSingle) || !bw.mdone[tm & ~kTileSingle];
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, keep);
+        if (!m)
+            continue;
+        int32_t base = 0;
+        if (lane == 0)
+            base = atomicAdd(bw.tlist_n, __popc(m));
+        base = __shfl_sync(FULL_MASK, base, 0);
+        if (keep)
+            bw.tlist[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)t;
+    }
 }
 
 // One block per matrix (grid-stride over matrices): deterministic sum of its
@@ -1268,16 +1302,24 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
     // of the kU tiles overlap; the tiles of the next round have their first
     // column, start bits and row indices loaded (prefetched) meanwhile.
     constexpr int kU = kWide ? 4 : 1;
-    int64_t t = s_go ? (gtid() >> 5) : (int64_t)ntiles;
-    int32_t pf_c0[kU], pf_i[kU];
+    // a batched solve walks the list of the running matrices' tiles (built
+    // after every pass); a single solve walks every tile
+    const int64_t steps = kBatch ? (int64_t)*W->bw.tlist_n : (int64_t)ntiles;
+    const int32_t *__restrict__ tlist = W->bw.tlist;
+    int64_t t = s_go ? (gtid() >> 5) : steps;
+    int32_t pf_c0[kU], pf_i[kU], pf_t[kU];
     uint32_t pf_mask[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
-        const int64_t tu = t + u * nwarps;
+        const int64_t xu = t + u * nwarps;
         pf_c0[u] = 0;
         pf_i[u] = 0;
         pf_mask[u] = 1u;
-        if (tu < ntiles) {
+        pf_t[u] = 0;
+        if (xu < steps) {
+            const int64_t tu = kBatch ? (int64_t)__ldg(tlist + xu) : xu;
+            if (kBatch)
+                pf_t[u] = (int32_t)tu;
             pf_c0[u] = __ldg(tile_col + tu);
             pf_mask[u] = __ldg(starts + tu);
             const int32_t pp = (int32_t)(tu * kTile) + lane;
@@ -1285,21 +1327,22 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
         }
     }
     for (;;) {
-        const bool more = t < ntiles;
+        const bool more = t < steps;
         if (more) {
             int32_t c0[kU], iv[kU], jv[kU], mjv[kU], pv[kU];
             uint32_t mask[kU];
             bool valid[kU], mixed[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int64_t tu = t + u * nwarps;
+                const int64_t xu = t + u * nwarps;
+                const int64_t tu = kBatch ? (int64_t)pf_t[u] : xu;
                 pv[u] = (int32_t)(tu * kTile) + lane;
-                valid[u] = tu < ntiles && pv[u] < nnz;
+                valid[u] = xu < steps && pv[u] < nnz;
                 mixed[u] = false;
                 c0[u] = pf_c0[u];
                 mask[u] = pf_mask[u];
                 iv[u] = pf_i[u];
-                if (kBatch && tu < ntiles) {
+                if (kBatch && xu < steps) {
                     const int32_t tm = __ldg(tilemat + tu);
                     if (tm & kTileSingle) {
                         if (__ldg(mdone + (tm & ~kTileSingle)))
@@ -1311,12 +1354,27 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int64_t tn = t + (kU + u) * nwarps;
-                if (tn < ntiles) {
+                const int64_t xn = t + (kU + u) * nwarps;
+                if (xn < steps) {
+                    const int64_t tn = kBatch ? (int64_t)__ldg(tlist + xn) : xn;
+                    if (kBatch)
+                        pf_t[u] = (int32_t)tn;
                     pf_c0[u] = __ldg(tile_col + tn);
                     pf_mask[u] = __ldg(starts + tn);
                     const int32_t pn = (int32_t)(tn * kTile) + lane;
                     pf_i[u] = pn < nnz ? __ldcs(rowidx + pn) : 0;
+                }
+            }
+            if (kBatch) {
+                // every tile of the round belongs to finished matrices: on
+                // to the next round (its loads are already in flight)
+                bool any = false;
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    any |= valid[u];
+                if (!__any_sync(FULL_MASK, any)) {
+                    t += kU * nwarps;
+                    continue;
                 }
             }
 #pragma unroll
@@ -1554,6 +1612,8 @@ __global__ void k_batch_control(const Work *__restrict__ W)
         if (threadIdx.x == 0 && still)
             atomicAdd(bw.active, still);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *bw.tlist_n = 0;  // the list of the next pass is built after this
 }
 
 // Pass counter of the whole batch; another pass runs while any matrix runs.
@@ -2514,8 +2574,10 @@ void launch_init(const Work *d, const Shape &sh, Sink &k)
     if (sh.batch)
         k.launch((const void *)k_batch_cols, init_grid(sh), kThreads, a);
     k.launch((const void *)k_init_mates, init_grid(sh), kThreads, a);
-    if (sh.batch)
+    if (sh.batch) {
         k.launch((const void *)k_batch_check, init_tile_grid(sh), kThreads, a);
+        k.launch((const void *)k_batch_list, init_grid(sh), kThreads, a);
+    }
     if (sh.lookup == AWPM_LOOKUP_HASH)
         k.launch((const void *)k_hash_build, init_tile_grid(sh), kThreads, a);
     if (sh.lookup == AWPM_LOOKUP_ROWMARK) {
@@ -2662,6 +2724,7 @@ void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditi
     void *ah[] = {(void *)&d, (void *)&h};
     if (sh.batch) {
         k.launch((const void *)k_batch_control, util_grid(sh), kThreads, a);
+        k.launch((const void *)k_batch_list, init_grid(sh), kThreads, a);
         if (graph)
             k.launch((const void *)k_batch_step_graph, 1, 1, ah);
         else
