@@ -180,17 +180,27 @@ def test_default_context_entry_point(orc, torch):
     assert np.array_equal(out.cpu().numpy(), ref) and st["iterations"] == rst["iterations"]
 
 
-def test_degenerate_sizes(ctx, orc, torch):
-    # n = 0
-    out = np.empty(0, dtype=np.int32)
-    st = awpm.awpm_improve_ctx(ctx, 0, np.zeros(1, np.int32), np.zeros(0, np.int32),
-                               np.zeros(0), np.zeros(0, np.int32), out)
-    assert st["iterations"] == 1 and st["converged"] == 1
-    # n = 1, and a diagonal-only matrix (no candidate at all)
-    for n in (1, 7, 1000):
-        W = np.diag(np.arange(n, dtype=np.float64) * -0.5)
-        g = gen.from_dense(W, np.eye(n, dtype=bool), np.arange(n))
-        check(ctx, orc, g, torch, what=f"diag n={n}")
+@pytest.mark.parametrize("lookup", [awpm.LOOKUP_AUTO, awpm.LOOKUP_ROWMARK], ids=["auto", "rowmark"])
+def test_degenerate_sizes(orc, torch, lookup):
+    """n = 0, n = 1, and diagonal-only matrices (no candidate at all), also
+    through row marking (a transpose of one entry; 1 to 2 radix passes)."""
+    ctx = awpm.awpm_create(device=0, lookup=lookup)
+    try:
+        out = np.empty(0, dtype=np.int32)
+        st = awpm.awpm_improve_ctx(ctx, 0, np.zeros(1, np.int32), np.zeros(0, np.int32),
+                                   np.zeros(0), np.zeros(0, np.int32), out)
+        assert st["iterations"] == 1 and st["converged"] == 1
+        for n in (1, 2, 7, 257, 1000):
+            W = np.diag(np.arange(n, dtype=np.float64) * -0.5)
+            g = gen.from_dense(W, np.eye(n, dtype=bool), np.arange(n))
+            check(ctx, orc, g, torch, what=f"diag n={n}")
+        # a full 2 x 2 (one flip) and a full 3 x 3
+        for n in (2, 3):
+            W = np.arange(n * n, dtype=np.float64).reshape(n, n) % 5 - 2.0
+            g = gen.from_dense(W, np.ones((n, n), dtype=bool), np.arange(n))
+            check(ctx, orc, g, torch, what=f"full n={n}")
+    finally:
+        awpm.awpm_destroy(ctx)
 
 
 def test_skewed_columns(ctx, orc, torch):
