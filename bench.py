@@ -452,6 +452,13 @@ def bench_batched(awpm, torch, dev, count):
         tot, _ = awpm.awpm_improve_batch(ctx, count, *t, out, per_matrix=False)
     batched_s = (time.perf_counter() - t0) / reps
     batched = out.cpu().numpy()
+    # the same batch with its passes driven from the host: the summed
+    # search-kernel time (CUDA events), and launches a profiler can list
+    tctx = awpm.awpm_create(device=dev.index or 0, flags=awpm.FLAG_TIME_SEARCH)
+    awpm.awpm_improve_batch(tctx, count, *t, out, per_matrix=False)
+    ttot, _ = awpm.awpm_improve_batch(tctx, count, *t, out, per_matrix=False)
+    awpm.awpm_destroy(tctx)
+    same_timed = bool(np.array_equal(out.cpu().numpy(), batched))
     # one launch (one awpm_improve call) per matrix, device-resident inputs
     per = []
     for g in graphs:
@@ -473,7 +480,8 @@ def bench_batched(awpm, torch, dev, count):
             "solves_per_s": count / batched_s, "ms_per_batch": 1e3 * batched_s,
             "one_launch_per_matrix_solves_per_s": count / single_s,
             "speedup_vs_one_launch_per_matrix": single_s / batched_s,
-            "identical_outputs": bool(same)}
+            "host_loop_ms": ttot["ms_total"], "host_loop_search_ms": ttot["ms_search"],
+            "identical_outputs": bool(same and same_timed)}
 
 
 def bench_served(awpm, torch, dev, requests, pool_size, budget=100 * 10**9):
