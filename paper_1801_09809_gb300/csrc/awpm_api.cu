@@ -1415,6 +1415,7 @@ int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *row
     wk.mmate = dmate;
     wk.mcolof = (int32_t *)c->mcolof.p;
     wk.mtiles = (int32_t *)c->mtiles.p;
+    wk.mtiles_cap = (int64_t)tiles_cap + 1;
     CUDA_TRY(cudaMemcpyAsync(c->d_work.p, c->h_work, sizeof(Work), cudaMemcpyHostToDevice,
                              c->stream));
     const Work *d = (const Work *)c->d_work.p;

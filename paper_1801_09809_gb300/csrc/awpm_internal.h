@@ -56,7 +56,8 @@ struct Ctl {
     int32_t live;                // greedy selection: winners still undecided
     int32_t nonempty;            // maximum matching: no column is empty
     int32_t phase_levels;        // maximum matching: levels of the running phase
-    int32_t level_tiles;         // maximum matching: tiles listed for this level
+    int32_t level_tiles;         // maximum matching: tiles listed for the next level
+    int32_t level_listed;        // maximum matching: tiles listed for this level
     unsigned long long levels;   // maximum matching: search levels run
     unsigned long long pass_flips;   // cycles flipped in the running pass
     unsigned long long cycles;       // cycles flipped in total
@@ -160,6 +161,7 @@ struct Work {
     int32_t *mmate;
     int32_t *mcolof;    // column of every entry
     int32_t *mtiles;    // tiles holding a frontier column, this level
+    int64_t mtiles_cap; // capacity of mtiles
     // row marking: per row the mark of its columns (a signature), the
     // transpose (row pointers; CSC positions row by row, ascending), the
     // radix sort that builds it (keys and values in two buffers each, digit

@@ -2172,6 +2172,8 @@ __global__ void k_mc_reset(const Work *__restrict__ W)
         c->levels = 0ull;
         c->pass_flips = 0ull;
         c->cycles = 0ull;
+        c->level_tiles = 0;
+        c->level_listed = 0;
     }
     for (int64_t x = gtid(); x < w.n; x += gstride())
         w.mr[x] = -1;
@@ -2223,6 +2225,54 @@ __global__ void k_mc_load(const Work *__restrict__ W)
     block_add_u64(have, &w.ctl->cycles);
 }
 
+// The list of 32-entry tiles holding an entry of a frontier column, built
+// where the frontier is made (the phase start and the end of each level):
+// every frontier column appends the tiles its entries span, one atomic per
+// warp.  A tile shared by two frontier columns is listed twice: the level
+// steps take the same decisions however often, and in whatever order, a
+// tile comes (maxima, minima and writes of equal values), so the list needs
+// neither order nor uniqueness.  It holds at most min(nnz, nnz/32 + 2n)
+// entries (a column spans at most len/32 + 2 tiles, and at most len); an
+// append past the capacity is refused with an internal error.  Called by a
+// whole warp, lane l holding the frontier bits `front` of bitmap word x.
+__device__ __forceinline__ void mc_list_tiles(const Work &w, int64_t x, uint32_t front, int lane)
+{
+    int32_t mine = 0;
+    for (uint32_t bits = front; bits; bits &= bits - 1) {
+        const int64_t c = x * 32 + __ffs(bits) - 1;
+        const int32_t s = __ldg(w.colptr + c), e = __ldg(w.colptr + c + 1);
+        if (e > s)
+            mine += ((e - 1) >> 5) - (s >> 5) + 1;
+    }
+    int32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    const int32_t total = __shfl_sync(FULL_MASK, incl, 31);
+    if (total == 0)
+        return;
+    int32_t base = 0;
+    if (lane == 0)
+        base = atomicAdd(&w.ctl->level_tiles, total);
+    base = __shfl_sync(FULL_MASK, base, 0);
+    if ((int64_t)base + total > w.mtiles_cap) {
+        if (lane == 0)
+            raise_err(w.ctl, kErrInternal);
+        return;
+    }
+    int32_t at = base + incl - mine;
+    for (uint32_t bits = front; bits; bits &= bits - 1) {
+        const int64_t c = x * 32 + __ffs(bits) - 1;
+        const int32_t s = __ldg(w.colptr + c), e = __ldg(w.colptr + c + 1);
+        if (e > s)
+            for (int32_t t = s >> 5; t <= ((e - 1) >> 5); ++t)
+                w.mtiles[at++] = t;
+    }
+}
+
 // A phase: every free column roots a tree and forms the frontier; rows
 // unreached; offers and tree ends cleared.
 __global__ void k_mc_phase(const Work *__restrict__ W)
@@ -2239,74 +2289,30 @@ __global__ void k_mc_phase(const Work *__restrict__ W)
             if (w.mc[x] < 0)
                 w.mroot[x] = (int32_t)x;
         }
+        // the frontier and its tile list (the list's count is zero here:
+        // the reset, or the last level of the previous phase, which kept no
+        // column)
+        const int lane = threadIdx.x & 31;
         const int64_t words = (int64_t)w.n / 32 + 1;
-        for (int64_t x = gtid(); x < words; x += gstride()) {
+        for (int64_t x0 = gtid() - lane; x0 < words; x0 += gstride()) {
+            const int64_t x = x0 + lane;
             uint32_t bits = 0u;
-            for (int b = 0; b < 32; ++b) {
-                const int64_t j = x * 32 + b;
-                if (j < w.n && w.mc[j] < 0)
-                    bits |= 1u << b;
+            if (x < words) {
+                for (int b = 0; b < 32; ++b) {
+                    const int64_t j = x * 32 + b;
+                    if (j < w.n && w.mc[j] < 0)
+                        bits |= 1u << b;
+                }
+                w.mfront[x] = bits;
+                w.mnext[x] = 0u;
+                live += __popc(bits);
             }
-            w.mfront[x] = bits;
-            w.mnext[x] = 0u;
-            live += __popc(bits);
+            mc_list_tiles(w, x, bits, lane);
         }
     }
-    if (gtid() == 0) {
+    if (gtid() == 0)
         w.ctl->phase_levels = 0;
-        w.ctl->level_tiles = 0;
-    }
     warp_add_i32(live, &w.ctl->live);
-}
-
-// Level, step 0: list the 32-entry tiles holding an entry of a frontier
-// column: every frontier column (a set bit of the frontier bitmap, a thread
-// per bitmap word) appends the tiles its entries span, one atomic per warp.
-// A tile shared by two frontier columns is listed twice: the level steps
-// below take the same decisions however often, and in whatever order, a
-// tile comes (maxima, minima and writes of equal values), so the list needs
-// neither order nor uniqueness.  It holds at most min(nnz, nnz/32 + 2n)
-// entries (a column spans at most len/32 + 2 tiles, and at most len).
-__global__ void k_mc_tiles(const Work *__restrict__ W)
-{
-    const Work &w = *W;
-    if (w.ctl->err)
-        return;
-    const int lane = threadIdx.x & 31;
-    const int64_t words = (int64_t)w.n / 32 + 1;
-    for (int64_t x0 = gtid() - lane; x0 < words; x0 += gstride()) {
-        const int64_t x = x0 + lane;
-        const uint32_t front = x < words ? w.mfront[x] : 0u;
-        // tiles this lane's columns span
-        int32_t mine = 0;
-        for (uint32_t bits = front; bits; bits &= bits - 1) {
-            const int64_t c = x * 32 + __ffs(bits) - 1;
-            const int32_t s = __ldg(w.colptr + c), e = __ldg(w.colptr + c + 1);
-            if (e > s)
-                mine += ((e - 1) >> 5) - (s >> 5) + 1;
-        }
-        int32_t incl = mine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(FULL_MASK, incl, o);
-            if (lane >= o)
-                incl += y;
-        }
-        const int32_t total = __shfl_sync(FULL_MASK, incl, 31);
-        if (total == 0)
-            continue;
-        int32_t base = 0;
-        if (lane == 0)
-            base = atomicAdd(&w.ctl->level_tiles, total);
-        int32_t at = __shfl_sync(FULL_MASK, base, 0) + incl - mine;
-        for (uint32_t bits = front; bits; bits &= bits - 1) {
-            const int64_t c = x * 32 + __ffs(bits) - 1;
-            const int32_t s = __ldg(w.colptr + c), e = __ldg(w.colptr + c + 1);
-            if (e > s)
-                for (int32_t t = s >> 5; t <= ((e - 1) >> 5); ++t)
-                    w.mtiles[at++] = t;
-        }
-    }
 }
 
 // Level steps 1-4 run over the listed tiles (one warp per tile): a column of
@@ -2314,11 +2320,11 @@ __global__ void k_mc_tiles(const Work *__restrict__ W)
 // level follows the size of its frontier.  The column of an entry comes from
 // the tile's first column and start bits when no column is empty, else from
 // the colof array.
-#define MC_TILE_LOOP_BEGIN                                                          \
+#define MC_TILE_LOOP_BEGIN(COUNT)                                                   \
     const int lane = threadIdx.x & 31;                                              \
     const int64_t nwarps = gstride() >> 5;                                          \
     const bool exact = w.ctl->nonempty != 0;                                        \
-    const int64_t listed = w.ctl->level_tiles;                                      \
+    const int64_t listed = (COUNT);                                                 \
     for (int64_t x = gtid() >> 5; x < listed; x += nwarps) {                        \
         const int64_t t = w.mtiles[x];                                              \
         const int32_t p = (int32_t)(t * kTile) + lane;                              \
@@ -2340,7 +2346,10 @@ __global__ void k_mc_offer_max(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    MC_TILE_LOOP_BEGIN
+    // the list's count, kept for the level's later steps
+    if (gtid() == 0)
+        w.ctl->level_listed = w.ctl->level_tiles;
+    MC_TILE_LOOP_BEGIN(w.ctl->level_tiles)
     if (r == w.mc[c] || w.mrpar[r] != -1)
         continue;
     const long long key = order_key(w.w[p]);
@@ -2355,7 +2364,10 @@ __global__ void k_mc_offer_min(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    MC_TILE_LOOP_BEGIN
+    // the next level's list starts empty (filled by k_mc_advance)
+    if (gtid() == 0)
+        w.ctl->level_tiles = 0;
+    MC_TILE_LOOP_BEGIN(w.ctl->level_listed)
     if (r == w.mc[c] || w.mrpar[r] != -1)
         continue;
     if (order_key(w.w[p]) == w.mrkey[r] && c < *(volatile const int32_t *)(w.mrcol + r))
@@ -2371,7 +2383,7 @@ __global__ void k_mc_join(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    MC_TILE_LOOP_BEGIN
+    MC_TILE_LOOP_BEGIN(w.ctl->level_listed)
     if (r == w.mc[c] || w.mrcol[r] != c || w.mrpar[r] != -1)
         continue;
     w.mrpar[r] = c;
@@ -2397,7 +2409,7 @@ __global__ void k_mc_end(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    MC_TILE_LOOP_BEGIN
+    MC_TILE_LOOP_BEGIN(w.ctl->level_listed)
     if (w.mrpar[r] != c || w.mr[r] >= 0)
         continue;
     const int32_t t_root = w.mroot[c];
@@ -2429,24 +2441,29 @@ __global__ void k_mc_advance(const Work *__restrict__ W)
     const Work &w = *W;
     int live = 0;
     if (!w.ctl->err) {
+        // the next frontier and its tile list (the list's count was zeroed
+        // by k_mc_offer_min of this level)
+        const int lane = threadIdx.x & 31;
         const int64_t words = (int64_t)w.n / 32 + 1;
-        for (int64_t x = gtid(); x < words; x += gstride()) {
-            uint32_t bits = w.mnext[x];
+        for (int64_t x0 = gtid() - lane; x0 < words; x0 += gstride()) {
+            const int64_t x = x0 + lane;
             uint32_t keep = 0u;
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int32_t c = (int32_t)(x * 32 + b);
-                if (w.mtkey[w.mroot[c]] == kKeyNone)
-                    keep |= 1u << b;
+            if (x < words) {
+                uint32_t bits = w.mnext[x];
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int32_t c = (int32_t)(x * 32 + b);
+                    if (w.mtkey[w.mroot[c]] == kKeyNone)
+                        keep |= 1u << b;
+                }
+                w.mfront[x] = keep;
+                w.mnext[x] = 0u;
+                live += __popc(keep);
             }
-            w.mfront[x] = keep;
-            w.mnext[x] = 0u;
-            live += __popc(keep);
+            mc_list_tiles(w, x, keep, lane);
         }
     }
-    if (gtid() == 0)
-        w.ctl->level_tiles = 0;
     warp_add_i32(live, &w.ctl->live);
 }
 
@@ -2790,7 +2807,6 @@ void launch_mcm_level(const Work *d, const Shape &sh, Sink &k)
     void *a[] = {(void *)&d};
     // one wave of blocks: a level's work follows its frontier, and a small
     // frontier should not pay for launching idle blocks
-    k.launch((const void *)k_mc_tiles, tile_grid(sh), kThreads, a);
     k.launch((const void *)k_mc_offer_max, tile_grid(sh), kThreads, a);
     k.launch((const void *)k_mc_offer_min, tile_grid(sh), kThreads, a);
     k.launch((const void *)k_mc_join, tile_grid(sh), kThreads, a);
