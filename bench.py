@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served comparison")
     ap.add_argument("--no-greedy", action="store_true", help="skip the greedy matching line")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the CPU baselines (profiling runs of the GPU path)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-pool", type=int, default=16)
@@ -746,8 +748,9 @@ def main():
     if not args.no_served:
         line["served"] = bench_served(awpm, torch, dev, args.serve_requests, args.serve_pool)
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(g) if world == 1 else None
-        line["cpu_baseline_parallel"] = cpu_baseline_parallel(g) if world == 1 else None
+        cpu = world == 1 and not args.no_cpu
+        line["cpu_baseline"] = cpu_baseline(g) if cpu else None
+        line["cpu_baseline_parallel"] = cpu_baseline_parallel(g) if cpu else None
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

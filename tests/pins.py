@@ -42,7 +42,7 @@ def load_hand_cases(path=os.path.join(GOLDEN, "hand_cases.txt")):
             cur["entries"].append((int(r), int(c), float(w)))
         elif key == "expect_mate":
             cur["expect_mate"] = [int(x) for x in rest.split()]
-        elif key in ("expect_iterations", "expect_cycles"):
+        elif key in ("expect_iterations", "expect_cycles", "expect_phases", "expect_cardinality"):
             cur[key] = int(rest)
         elif key == "expect_weight":
             cur[key] = float(rest)
@@ -465,6 +465,20 @@ def pin_mcm(orc):
     assert m.tolist() == [-1, 0]
 
 
+def pin_mcm_hand_cases(orc):
+    """Hand-derived maximum matchings (tests/golden/mcm_cases.txt): equal
+    offers go to the lower column, equal tree ends to the lower row, and a
+    tree that found its end stops growing (the readings of Section 5.2)."""
+    cases = load_hand_cases(os.path.join(GOLDEN, "mcm_cases.txt"))
+    assert len(cases) >= 3
+    for c in cases:
+        g = graph_of_case(c)
+        m, st = orc.mcm(g, np.asarray(c["mate"], dtype=np.int32))
+        assert m.tolist() == c["expect_mate"], (c["name"], m)
+        assert st["phases"] == c["expect_phases"], (c["name"], st)
+        assert st["cardinality"] == c["expect_cardinality"], (c["name"], st)
+
+
 def pin_validation(orc):
     """Input checks: error classes for malformed inputs."""
     g = gen.random_small(5, 0.6, 3)
@@ -526,4 +540,4 @@ PINS = [pin_hand_cases, pin_2x2_closed_form, pin_block_diagonal, pin_six_cycle,
         pin_bruteforce_small, pin_one_pass_bruteforce, pin_rank_simulation,
         pin_local_optimality_midsize, pin_validation, pin_resume, pin_paper_maxiters,
         pin_pettie_sanders_selection, pin_row_marking, pin_greedy_matching, pin_weights,
-        pin_mcm]
+        pin_mcm, pin_mcm_hand_cases]

@@ -98,3 +98,17 @@ def test_graph_and_host_loop_agree(torch):
     finally:
         awpm.awpm_destroy(ch)
         awpm.awpm_destroy(cg)
+
+
+def test_hand_cases_equal_weights(ctx, torch):
+    """The hand-derived cases of tests/golden/mcm_cases.txt (equal offers to
+    the lower column, equal ends to the lower row, a tree with an end stops
+    growing): the GPU gives the expected matchings and phase counts."""
+    import os
+    for c in pins.load_hand_cases(os.path.join(pins.GOLDEN, "mcm_cases.txt")):
+        g = pins.graph_of_case(c)
+        for host in (False, True):
+            got, st = mcm_gpu(ctx, g, c["mate"], torch, host=host)
+            assert got.tolist() == c["expect_mate"], (c["name"], got)
+            assert st["phases"] == c["expect_phases"], (c["name"], st)
+            assert st["cardinality"] == c["expect_cardinality"], (c["name"], st)

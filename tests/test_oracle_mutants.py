@@ -66,6 +66,15 @@ MUTANTS = [
     ("maximum matching ends at the lowest free row",
      "if (tend[t] < 0 || w[p] > tw[t] || (w[p] == tw[t] && r < tend[t])) {",
      "if (tend[t] < 0 || r < tend[t]) {"),
+    ("maximum matching equal offers to the higher column",
+     "if (bestc[r] < 0 || w[p] > bestw[r] || (w[p] == bestw[r] && c < bestc[r])) {",
+     "if (bestc[r] < 0 || w[p] > bestw[r] || (w[p] == bestw[r] && c > bestc[r])) {"),
+    ("maximum matching equal ends to the higher row",
+     "if (tend[t] < 0 || w[p] > tw[t] || (w[p] == tw[t] && r < tend[t])) {",
+     "if (tend[t] < 0 || w[p] > tw[t] || (w[p] == tw[t] && r > tend[t])) {"),
+    ("maximum matching trees with an end keep growing",
+     "if (tend[root[next[f]]] < 0)\n                    front[nf++] = next[f];",
+     "front[nf++] = next[f];"),
     ("maximum matching stops after one phase", "        if (aug == 0)\n            break;",
      "        break;"),
     ("greedy column keeps the lightest", "if (cbest[j] < 0 || w[p] > w[cbest[j]])",
