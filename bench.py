@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "AWPM edge-checks/s and HBM GB/s at 1 GB300"
 UNIT = "edge-checks/s"
-PROFILE = os.path.join(ROOT, "profiles", "k_search_rmat_s22.md")
+PROFILE = os.path.join(ROOT, "profiles", "k_search_rmat_s22.json")
 KERNEL_SRC = os.path.join(ROOT, "paper_1801_09809_gb300", "csrc", "awpm_kernels.cu")
 
 
@@ -98,24 +98,25 @@ def search_kernel_hash():
     return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 
 
-def profile_traffic():
-    """DRAM bytes per search launch from the committed ncu summary, or None
-    when the kernel source changed since the capture."""
+def profile_record(path=None):
+    """The committed ncu record of one search launch on the bench graph (DRAM
+    bytes, L2 hit rate), or None when the kernel source changed since the
+    capture (its hash no longer matches) or the record is missing."""
     try:
-        text = open(PROFILE).read()
-    except OSError:
+        rec = json.load(open(path or PROFILE))
+    except (OSError, ValueError):
         return None
-    src_hash = search_kernel_hash()
-    vals = {}
-    for line in text.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, _, v = line.strip()[2:].partition(":")
-            vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != src_hash:
+    if rec.get("kernel_source_sha256_16") != search_kernel_hash():
         return None
+    return rec
+
+
+def profile_traffic(path=None):
+    """DRAM bytes per search launch from the committed ncu record, or None."""
+    rec = profile_record(path)
     try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        return float(rec["dram_bytes_per_launch"]) if rec else None
+    except (KeyError, TypeError, ValueError):
         return None
 
 
@@ -651,11 +652,17 @@ def main():
     alg_bytes = launches * (12.0 * nnz + 4.0 * (n + 1) + 12.0 * n + 20.0 * n) + 32.0 * cand
     avg_ms = search_ms / max(launches, 1)
     achieved = alg_bytes / launches / (avg_ms / 1e3) / 1e9
-    traffic = profile_traffic()
+    prof = profile_record() if args.workload == "rmat" else None
+    traffic = profile_traffic() if prof else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
                 "kernel": "k_search (Steps A+B+C)", "avg_launch_ms": avg_ms,
-                "alg_bytes_per_launch": alg_bytes / launches, "peak_kind": pk_kind}
+                "alg_bytes_per_launch": alg_bytes / launches, "peak_kind": pk_kind,
+                # measured DRAM bytes (ncu, one launch on this graph) over the
+                # live launch time: the fraction of peak the kernel really moves
+                "dram_frac": (traffic / (avg_ms / 1e3) / 1e9 / pk["hbm_gbs"]) if traffic else None,
+                "l2_hit_rate_pct": prof.get("l2_sector_hit_rate_pct") if prof else None,
+                "traffic_source": "profiles/k_search_rmat_s22.json" if prof else None}
 
     # timed region 3: end to end through host (pinned) buffers, every step
     # one solve with its host->device input copies and the device->host

@@ -25,13 +25,13 @@ def test_search_kernel_hash_is_stable(bench):
 
 
 def write_profile(path, sha, traffic):
-    path.write_text("# profile\n\n"
-                    f"- kernel_source_sha256_16: `{sha}`\n"
-                    f"- dram_bytes_per_launch: `{traffic}`\n")
+    import json
+    path.write_text(json.dumps({"kernel_source_sha256_16": sha, "dram_bytes_per_launch": traffic,
+                                "l2_sector_hit_rate_pct": 59.0}))
 
 
 def test_profile_traffic_follows_the_source_hash(bench, tmp_path, monkeypatch):
-    prof = tmp_path / "p.md"
+    prof = tmp_path / "p.json"
     monkeypatch.setattr(bench, "PROFILE", str(prof))
     write_profile(prof, bench.search_kernel_hash(), 123456789)
     assert bench.profile_traffic() == 123456789.0
@@ -39,12 +39,29 @@ def test_profile_traffic_follows_the_source_hash(bench, tmp_path, monkeypatch):
     write_profile(prof, "0" * 16, 123456789)
     assert bench.profile_traffic() is None
     # no profile at all
-    monkeypatch.setattr(bench, "PROFILE", str(tmp_path / "missing.md"))
+    monkeypatch.setattr(bench, "PROFILE", str(tmp_path / "missing.json"))
     assert bench.profile_traffic() is None
 
 
 def test_profile_traffic_rejects_malformed_values(bench, tmp_path, monkeypatch):
-    prof = tmp_path / "p.md"
+    prof = tmp_path / "p.json"
     monkeypatch.setattr(bench, "PROFILE", str(prof))
     write_profile(prof, bench.search_kernel_hash(), "n/a")
     assert bench.profile_traffic() is None
+
+
+def test_committed_profile_record_is_well_formed(bench):
+    import json
+    rec = json.load(open(bench.PROFILE))
+    for k in ("kernel_source_sha256_16", "dram_bytes_read", "dram_bytes_write",
+              "dram_bytes_per_launch", "l2_sector_hit_rate_pct", "gpu_time_ns", "command"):
+        assert k in rec, k
+    assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    assert "--clock-control none" in rec["command"] and "-c 1" in rec["command"]
+
+
+def test_profile_record_garbage_is_none(bench, tmp_path, monkeypatch):
+    prof = tmp_path / "p.json"
+    prof.write_text("not json")
+    monkeypatch.setattr(bench, "PROFILE", str(prof))
+    assert bench.profile_record() is None and bench.profile_traffic() is None
