@@ -90,10 +90,11 @@ def peaks():
 
 
 def search_kernel_hash():
-    """sha256 (16 hex digits) of the search kernel's source text, from its
-    template line to the Step D section."""
+    """sha256 (16 hex digits) of the search kernels' source text: the Steps
+    A+B+C section (lookup queue, lookups, both search kernels) up to the Step D
+    section."""
     text = open(KERNEL_SRC).read()
-    a = text.index("template <int kLookup, bool kBatch, bool kWide>")
+    a = text.index("// Steps A + B + C (Algorithms 3, 4, 5)")
     b = text.index("// Step D (Algorithm 6)")
     return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 

@@ -59,9 +59,14 @@ extern "C" {
 #define AWPM_ERR_OOM 5             /* device or pinned host allocation failed         */
 #define AWPM_ERR_BUDGET 6          /* the context's device-memory budget is exceeded  */
 #define AWPM_ERR_CUDA 7            /* a CUDA call failed (message: awpm_last_error)   */
-#define AWPM_ERR_TIMEOUT 8         /* a bounded device-side wait gave up              */
+#define AWPM_ERR_TIMEOUT 8         /* a bounded device-side retry or loop gave up     */
 #define AWPM_ERR_NOT_FOUND 9       /* unknown ticket                                  */
 #define AWPM_ERR_TOO_LARGE 10      /* problem exceeds awpm_search_noalloc's scratch   */
+#define AWPM_ERR_INTERNAL 11       /* a device-side consistency check of the library's
+                                      own state failed (a full hash table, a broken
+                                      transpose or search tree): a library bug, not an
+                                      input error; the context stays usable           */
+#define AWPM_ERR_CANCELLED 12      /* the request was cancelled before it started     */
 
 /* Closing-edge lookup strategy of the cycle search (Step B). */
 #define AWPM_LOOKUP_AUTO 0    /* the library picks (per matrix)                         */
@@ -232,7 +237,14 @@ int awpm_improve_batch(awpm_ctx *ctx, int32_t count, const int32_t *n_off, const
  * concurrently, each on its own stream and workspace, and admits the next
  * queued request as soon as a slot is free and the device bytes held by all
  * slots stay within opt.mem_budget_bytes (a request that could never fit
- * finishes with AWPM_ERR_BUDGET).  Every request is solved exactly as by
+ * finishes with AWPM_ERR_BUDGET).  A request's need is estimated from n and
+ * nnz (nnz read from colptr[n] at admission when the caller passes -1 with a
+ * device colptr); each slot solves under a budget of what the other slots
+ * leave, so the slots together never hold more than opt.mem_budget_bytes,
+ * and idle slots give their workspace back when a waiting request needs the
+ * room.  Admission looks up to 8 requests past the head for one that fits;
+ * a head overtaken 16 times is then admitted before any other request.
+ * Every request is solved exactly as by
  * awpm_improve alone: the same matching, passes and statistics, whatever else
  * runs beside it.  The problem's arrays are borrowed until the request is
  * reported done; mate_out is written then.  Device arrays must hold their
@@ -248,6 +260,45 @@ int awpm_improve_batch(awpm_ctx *ctx, int32_t count, const int32_t *n_off, const
 int awpm_submit(awpm_ctx *ctx, const awpm_problem *p, uint64_t *ticket);
 int awpm_poll(awpm_ctx *ctx, uint64_t ticket, int *done, awpm_stats *stats);
 int awpm_wait(awpm_ctx *ctx, uint64_t ticket, awpm_stats *stats);
+
+/*
+ * Cancel a request of the request server (a serving concern; the paper has
+ * no counterpart).  A request still queued is removed at once: its arrays are
+ * no longer borrowed, *cancelled = 1, and awpm_poll / awpm_wait report it
+ * done with AWPM_ERR_CANCELLED (releasing the ticket).  A request already
+ * started runs to completion and is reported as usual (*cancelled = 0).
+ * Errors: AWPM_ERR_INVALID_ARG (NULL argument), AWPM_ERR_NOT_FOUND (unknown
+ * or released ticket).
+ */
+int awpm_cancel(awpm_ctx *ctx, uint64_t ticket, int *cancelled);
+
+/*
+ * Device memory of a context (host memory is not counted): *held = the bytes
+ * it holds now, its request server's slots included; *peak = the most it has
+ * held at once since creation (for the server: the most all slots held
+ * together, which never exceeds opt.mem_budget_bytes when a budget is set).
+ * Errors: AWPM_ERR_INVALID_ARG.
+ */
+int awpm_memory_held(awpm_ctx *ctx, size_t *held, size_t *peak);
+
+/*
+ * Test hook for allocation failures (the paper has no counterpart): after
+ * `after` more successful device allocations of this context's own
+ * workspace, the next one fails as if cudaMalloc had (AWPM_ERR_OOM), once;
+ * -1 switches it off.  The context stays usable: a later call allocates
+ * again.  Errors: AWPM_ERR_INVALID_ARG (ctx NULL or after < -1).
+ */
+int awpm_inject_alloc_failure(awpm_ctx *ctx, int32_t after);
+
+/*
+ * The device bytes one solve of an n x n problem with nnz stored entries may
+ * need on this context's options (lookup, selection): the request server's
+ * admission estimate, an upper bound of the workspace the solve allocates.
+ * host_inputs != 0 adds the staging copies of host arrays.  For planning
+ * opt.mem_budget_bytes.  Errors: AWPM_ERR_INVALID_ARG (NULL, n < 0, nnz < 0).
+ */
+int awpm_bytes_needed(awpm_ctx *ctx, int32_t n, int32_t nnz, int32_t host_inputs,
+                      size_t *bytes);
 
 /*
  * Heavy-weight greedy maximal matching (Section 5.1: the maximal matching
@@ -367,11 +418,13 @@ int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
  *     AWPM_ERR_TOO_LARGE.
  *   - colptr, rowidx, weight, mate, stepc_gain and stepc_row must be device
  *     memory of the current device (AWPM_ERR_INVALID_ARG otherwise); the
- *     caller owns them.  stream is a cudaStream_t (NULL = the default stream);
- *     the call waits on it before returning.  stats may be NULL (host).
- *   - The first call on a device looks up the device address of the scratch
- *     array (once per device, with that device current); make that first
- *     call before any stream capture on the device.
+ *     caller owns them.  stream is a cudaStream_t (NULL = the default stream).
+ *     stats may be NULL (host).
+ *   - Every call looks up the device address of the scratch array on the
+ *     current device (cudaGetSymbolAddress), so a context re-created after
+ *     cudaDeviceReset gets the right address.  The call reads colptr[n] and
+ *     the search's counters back to the host and synchronises `stream`
+ *     before it returns, so it cannot be captured into a CUDA graph.
  *   - Every call on a device shares the one scratch array, which keeps the
  *     contents of the last call; each call clears what must start at zero.
  *     Calls whose work overlaps on the GPU (other threads, other streams)

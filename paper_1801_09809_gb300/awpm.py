@@ -13,11 +13,14 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libawpm.so")
+# AWPM_LIBRARY names another build of the same library (for example one
+# compiled with AWPM_DEBUG_BOUNDS); the default is the in-tree libawpm.so.
+LIB_PATH = os.environ.get("AWPM_LIBRARY") or os.path.join(HERE, "libawpm.so")
 
 AWPM_OK = 0
 ERRORS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_PERFECT", 3: "UNSORTED_OR_DUP", 4: "NONFINITE",
-          5: "OOM", 6: "BUDGET", 7: "CUDA", 8: "TIMEOUT", 9: "NOT_FOUND", 10: "TOO_LARGE"}
+          5: "OOM", 6: "BUDGET", 7: "CUDA", 8: "TIMEOUT", 9: "NOT_FOUND", 10: "TOO_LARGE",
+          11: "INTERNAL", 12: "CANCELLED"}
 LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_HASH, LOOKUP_ROWMARK = 0, 1, 2, 3
 SELECT_STEP_D, SELECT_GREEDY = 0, 1
 FLAG_TIME_SEARCH = 1
@@ -97,6 +100,12 @@ SIGNATURES = [
     ("awpm_poll", ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(Stats)]),
     ("awpm_wait", ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(Stats)]),
+    ("awpm_cancel", ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+    ("awpm_memory_held", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t),
+                                        ctypes.POINTER(ctypes.c_size_t)]),
+    ("awpm_inject_alloc_failure", ctypes.c_int, [_VP, ctypes.c_int32]),
+    ("awpm_bytes_needed", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_size_t)]),
     ("awpm_search_noalloc", ctypes.c_int, [ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                            ctypes.POINTER(Stats)]),
     ("awpm_greedy", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP,
@@ -292,6 +301,36 @@ def awpm_wait(ctx: Context, ticket: int) -> dict:
     st = Stats()
     _check(lib().awpm_wait(ctx.handle, ctypes.c_uint64(ticket), ctypes.byref(st)))
     return st.as_dict()
+
+
+def awpm_cancel(ctx: Context, ticket: int) -> bool:
+    """Cancel a queued request; True if it had not started (it is then
+    reported done with CANCELLED), False if it runs to completion."""
+    c = ctypes.c_int(0)
+    _check(lib().awpm_cancel(ctx.handle, ctypes.c_uint64(ticket), ctypes.byref(c)))
+    return bool(c.value)
+
+
+def awpm_memory_held(ctx: Context):
+    """(device bytes held now, most held at once) by the context and its
+    request server's slots."""
+    h, p = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(lib().awpm_memory_held(ctx.handle, ctypes.byref(h), ctypes.byref(p)))
+    return h.value, p.value
+
+
+def awpm_inject_alloc_failure(ctx: Context, after: int) -> None:
+    """Test hook: the context's next device allocation after `after`
+    successful ones fails (OOM), once; -1 switches it off."""
+    _check(lib().awpm_inject_alloc_failure(ctx.handle, int(after)))
+
+
+def awpm_bytes_needed(ctx: Context, n: int, nnz: int, host_inputs: bool = False) -> int:
+    """Admission estimate of one solve's device workspace on this context."""
+    b = ctypes.c_size_t(0)
+    _check(lib().awpm_bytes_needed(ctx.handle, int(n), int(nnz), int(bool(host_inputs)),
+                                   ctypes.byref(b)))
+    return b.value
 
 
 def awpm_strerror(code: int) -> str:

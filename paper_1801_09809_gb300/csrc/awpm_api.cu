@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -87,6 +88,13 @@ int ensure(awpm_ctx *c, DevBuf &b, size_t bytes)
         if (c->held + want > c->opt.mem_budget_bytes)
             return AWPM_ERR_BUDGET;
     }
+    if (c->fail_after >= 0) {  // injected failure (awpm_inject_alloc_failure)
+        if (c->fail_after == 0) {
+            c->fail_after = -1;
+            return AWPM_ERR_OOM;
+        }
+        --c->fail_after;
+    }
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, want);
     if (e != cudaSuccess) {
@@ -97,6 +105,8 @@ int ensure(awpm_ctx *c, DevBuf &b, size_t bytes)
     b.p = p;
     b.bytes = want;
     c->held += want;
+    if (c->held > c->peak)
+        c->peak = c->held;
     return AWPM_OK;
 }
 
@@ -118,19 +128,21 @@ int where(const awpm_ctx *c, const void *p)
     return 0;
 }
 
+// Bloom filters of the long columns with the binary-search lookup (default
+// on; the environment variable AWPM_BLOOM=0 switches them off, a tuning knob:
+// results are the same either way).
+bool bloom_enabled()
+{
+    static const bool on = [] {
+        const char *v = getenv("AWPM_BLOOM");
+        return !(v && v[0] == '0' && v[1] == 0);
+    }();
+    return on;
+}
+
 int code_of(unsigned err)
 {
-    if (err & kErrInvalid)
-        return AWPM_ERR_INVALID_ARG;
-    if (err & kErrUnsorted)
-        return AWPM_ERR_UNSORTED_OR_DUP;
-    if (err & kErrNonfinite)
-        return AWPM_ERR_NONFINITE;
-    if (err & kErrNotPerfect)
-        return AWPM_ERR_NOT_PERFECT;
-    if (err)
-        return AWPM_ERR_TIMEOUT;
-    return AWPM_OK;
+    return awpm_code_of_bits(err);
 }
 
 int check_sink(const Sink &k)
@@ -524,7 +536,7 @@ std::map<int, awpm_ctx *> g_default;
 
 namespace awpm {
 
-size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup)
+size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup, int select)
 {
     const size_t N = (size_t)n, Z = (size_t)nnz, T = Z / kTile + 1;
     size_t b = N * (4 + 4 + 8 + sizeof(RowRec) + 8 + 8 + sizeof(Rec) + sizeof(Sel) + 4) + N / 8 +
@@ -538,12 +550,36 @@ size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup)
         b += 12 * N + 4 + 16 * Z + 4 * (size_t)kRsBins * (Z / kRsTile + 1) + 4 * kRsBins;
     if (host_inputs)
         b += 4 * (N + 1) + 12 * Z + 8 * N;
+    if (select == AWPM_SELECT_GREEDY)  // selection records and three bitmaps
+        b += sizeof(Sel) * N + 3 * 4 * (N / 32 + 1);
     return b + b / 8;
 }
 
 size_t ctx_bytes_held(const awpm_ctx *c)
 {
     return c->held;
+}
+
+void ctx_trim(awpm_ctx *c)
+{
+    DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->wmr,
+                      &c->colsig,  &c->best,     &c->dsel,     &c->tile_col, &c->starts,
+                      &c->wpart,   &c->htab,     &c->b_noff,   &c->b_colmat, &c->b_tilemat,
+                      &c->b_tlist, &c->b_i32,    &c->b_u64,    &c->b_f64,    &c->s_colptr,
+                      &c->s_rowidx, &c->s_w,     &c->s_mate,   &c->s_out,    &c->s_gain,
+                      &c->s_row,   &c->winbits,  &c->wkey,     &c->bloom,    &c->gckey,
+                      &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate,    &c->gtdead,
+                      &c->psel,    &c->pslive,   &c->pstaken,  &c->psused,   &c->wt_cmax,
+                      &c->wt_rmax, &c->wt_stage, &c->mroot,    &c->mrpar,    &c->mfront,
+                      &c->mnext,   &c->mrkey,    &c->mrcol,    &c->mtkey,    &c->mtrow,
+                      &c->mstage,  &c->mcolof,   &c->mtiles,   &c->rowsig,   &c->trowptr,
+                      &c->rs_k0,   &c->rs_k1,    &c->rs_v0,    &c->rs_v1,    &c->rs_hist,
+                      &c->rs_sums};
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    for (DevBuf *b : bufs)
+        release(c, *b);
+    cudaGetLastError();
 }
 
 int setup_ctx(awpm_ctx *c, const awpm_options *opt)
@@ -783,10 +819,12 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     wk.mr = (int32_t *)c->mr.p;
     wk.wm = (double *)c->wm.p;
     wk.rr = (RowRec *)c->rr.p;
+    wk.rsig = (unsigned long long *)c->rr.p;
+    wk.rrange = (int2 *)(wk.rsig + n);
     wk.wmr = (double *)c->wmr.p;
     wk.colsig = (unsigned long long *)c->colsig.p;
     wk.htab = lookup == AWPM_LOOKUP_HASH ? (unsigned long long *)c->htab.p : nullptr;
-    wk.bloom = lookup == AWPM_LOOKUP_BSEARCH ? (uint32_t *)c->bloom.p : nullptr;
+    wk.bloom = lookup == AWPM_LOOKUP_BSEARCH && bloom_enabled() ? (uint32_t *)c->bloom.p : nullptr;
     if (lookup == AWPM_LOOKUP_ROWMARK) {
         wk.rowsig = (unsigned long long *)c->rowsig.p;
         wk.trowptr = (int32_t *)c->trowptr.p;
@@ -1018,9 +1056,11 @@ const char *awpm_strerror(int code)
     case AWPM_ERR_OOM: return "out of memory";
     case AWPM_ERR_BUDGET: return "device memory budget exceeded";
     case AWPM_ERR_CUDA: return "CUDA error";
-    case AWPM_ERR_TIMEOUT: return "bounded device wait gave up";
+    case AWPM_ERR_TIMEOUT: return "a bounded device-side retry or loop gave up";
     case AWPM_ERR_NOT_FOUND: return "unknown ticket";
     case AWPM_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of awpm_search_noalloc";
+    case AWPM_ERR_INTERNAL: return "internal consistency check failed (library bug)";
+    case AWPM_ERR_CANCELLED: return "request cancelled before it started";
     default: return "unknown error";
     }
 }
@@ -1076,6 +1116,42 @@ int awpm_destroy(awpm_ctx *ctx)
         teardown_ctx(ctx);
     }
     delete ctx;
+    return AWPM_OK;
+}
+
+int awpm_inject_alloc_failure(awpm_ctx *ctx, int32_t after)
+{
+    if (!ctx || after < -1)
+        return AWPM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->fail_after = after;
+    return AWPM_OK;
+}
+
+void awpm_server_memory(awpm_ctx *ctx, size_t *held, size_t *peak);
+
+int awpm_bytes_needed(awpm_ctx *ctx, int32_t n, int32_t nnz, int32_t host_inputs, size_t *bytes)
+{
+    if (!ctx || !bytes || n < 0 || nnz < 0)
+        return AWPM_ERR_INVALID_ARG;
+    *bytes = ctx_bytes_needed(n, nnz, host_inputs != 0, ctx->opt.lookup, ctx->opt.select);
+    return AWPM_OK;
+}
+
+int awpm_memory_held(awpm_ctx *ctx, size_t *held, size_t *peak)
+{
+    if (!ctx || !held || !peak)
+        return AWPM_ERR_INVALID_ARG;
+    size_t h, p;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        h = ctx->held;
+        p = ctx->peak;
+    }
+    size_t sh = 0, sp = 0;
+    awpm_server_memory(ctx, &sh, &sp);
+    *held = h + sh;
+    *peak = p > sp ? p : sp;
     return AWPM_OK;
 }
 

@@ -74,8 +74,11 @@ int ctx_enqueue(struct ::awpm_ctx *c, const Request &r);
 // statistics (per_matrix: count entries for a batch, may be null).
 int ctx_finish(struct ::awpm_ctx *c, awpm_stats *st, awpm_stats *per_matrix);
 // Device bytes a context needs to solve a problem of this size.
-size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup);
+size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup, int select);
 size_t ctx_bytes_held(const struct ::awpm_ctx *c);
+// Free the per-solve workspace of an idle context (its descriptor and graphs
+// stay; the next solve allocates again).
+void ctx_trim(struct ::awpm_ctx *c);
 void note_cuda_error(cudaError_t e, const char *what, int line);
 
 }  // namespace awpm
@@ -88,6 +91,8 @@ struct awpm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t held = 0;
+    size_t peak = 0;        // most device bytes held at once
+    int32_t fail_after = -1;  // test hook: allocations left before one fails (-1: off)
     int search_bps[2][3][2] = {};  // [batch][lookup slot][wide]
     bool search_wide = true;      // default when the lookup is given explicitly
     // per-solve device workspace

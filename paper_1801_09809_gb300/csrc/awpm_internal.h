@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "awpm.h"
+
 namespace awpm {
 
 // Nonzeros handled by one warp per tile of the edge-parallel kernels; tiles
@@ -11,13 +13,35 @@ namespace awpm {
 // bitmap.
 constexpr int kTile = 32;
 
-// Error bits raised by the device-side validation; the host maps them to the
-// public code (priority INVALID > UNSORTED > NONFINITE > NOTPERF).
+// Error bits raised on the device; the host maps them to the public code
+// (priority INVALID > UNSORTED > NONFINITE > NOTPERF > INTERNAL > TIMEOUT).
 constexpr unsigned kErrInvalid = 1u;
 constexpr unsigned kErrUnsorted = 2u;
 constexpr unsigned kErrNonfinite = 4u;
 constexpr unsigned kErrNotPerfect = 8u;
-constexpr unsigned kErrInternal = 16u;  // a bounded retry loop gave up
+constexpr unsigned kErrInternal = 16u;  // a consistency check of the library's own state failed
+constexpr unsigned kErrTimeout = 32u;   // a bounded retry loop or level loop gave up
+constexpr unsigned kErrBounds = 64u;    // AWPM_DEBUG_BOUNDS builds: an index check failed
+
+// Public code of a set of device error bits (host side).
+inline int awpm_code_of_bits(unsigned err)
+{
+    if (err & kErrInvalid)
+        return AWPM_ERR_INVALID_ARG;
+    if (err & kErrUnsorted)
+        return AWPM_ERR_UNSORTED_OR_DUP;
+    if (err & kErrNonfinite)
+        return AWPM_ERR_NONFINITE;
+    if (err & kErrNotPerfect)
+        return AWPM_ERR_NOT_PERFECT;
+    if (err & (kErrInternal | kErrBounds))
+        return AWPM_ERR_INTERNAL;
+    if (err & kErrTimeout)
+        return AWPM_ERR_TIMEOUT;
+    if (err)
+        return AWPM_ERR_INTERNAL;
+    return AWPM_OK;
+}
 
 // Step-C record of a root column j (Algorithm 5): best positive gain, the
 // position p of (i, j) in column j and the position q of the closing entry
@@ -111,7 +135,9 @@ struct Work {
     int32_t *mc;        // row matched to column j
     int32_t *mr;        // column matched to row i
     double *wm;         // w(mc[j], j)
-    RowRec *rr;         // per row i: rows of column mr[i] (range + signature)
+    RowRec *rr;         // the row-record buffer (16 B per row), split into:
+    unsigned long long *rsig;  // per row i: signature of the rows of column mr[i]
+    int2 *rrange;              // per row i: that column's range {colptr[m_i], colptr[m_i+1]}
     double *wmr;        // per row i: wm[mr[i]] = w(i, mr[i])
     unsigned long long *colsig;  // per column: signature of its rows
     unsigned long long *htab;    // per-column hash tables (2 slots per nonzero), or null
@@ -256,5 +282,8 @@ int search_waves(int num_sms, int search_bps, int32_t ntiles);
 // Whether the search kernel takes four tiles per warp round (default on; the
 // environment variable AWPM_SEARCH_WIDE=0/1 overrides it, a tuning knob).
 bool default_search_wide();
+// Whether single-problem searches use the pipelined kernel (default on; the
+// environment variable AWPM_SEARCH_PIPE=0/1 overrides it, a tuning knob).
+bool search_pipe();
 
 }  // namespace awpm

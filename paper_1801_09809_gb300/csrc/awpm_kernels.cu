@@ -239,7 +239,7 @@ __device__ void rec_combine(Rec *addr, Rec mine, Ctl *ctl)
             return;
         cur = old;
     }
-    raise_err(ctl, kErrInternal);
+    raise_err(ctl, kErrTimeout);
 }
 
 // (g, j) beats (cg, cj): larger gain, then lower root (gains >= +0).
@@ -262,7 +262,7 @@ __device__ void sel_combine(Sel *addr, Sel mine, Ctl *ctl)
             return;
         cur = old;
     }
-    raise_err(ctl, kErrInternal);
+    raise_err(ctl, kErrTimeout);
 }
 
 // ---- cache-policy loads -------------------------------------------------------
@@ -274,18 +274,21 @@ __device__ __forceinline__ unsigned long long policy_evict_last()
     return pol;
 }
 
-// 16-byte row record through the read-only path, kept in L2 (evict last).
-__device__ __forceinline__ RowRec ld_rowrec(const RowRec *ptr, unsigned long long pol)
+// Row record of `row` (the column matched to it: range and signature), kept as
+// two arrays so that the signature test gathers 8 bytes per candidate.
+__device__ __forceinline__ void put_rowrec(const Work &w, int32_t row, int32_t s, int32_t e,
+                                           unsigned long long sig)
 {
-    uint32_t a, b, c, d;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-                 : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
-                 : "l"(ptr), "l"(pol));
-    RowRec r;
-    r.s = (int32_t)a;
-    r.e = (int32_t)b;
-    r.sig = ((unsigned long long)d << 32) | c;
-    return r;
+    w.rsig[row] = sig;
+    w.rrange[row] = make_int2(s, e);
+}
+
+__device__ __forceinline__ unsigned long long ld_u64_last(const unsigned long long *ptr,
+                                                          unsigned long long pol)
+{
+    unsigned long long v;
+    asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+    return v;
 }
 
 __device__ __forceinline__ int32_t ld_i32_last(const int32_t *ptr, unsigned long long pol)
@@ -565,11 +568,7 @@ __global__ void k_init_mates(const Work *__restrict__ W)
                 raise_err(w.ctl, kErrNotPerfect);
                 continue;
             }
-            RowRec rec;
-            rec.s = s[u];
-            rec.e = e[u];
-            rec.sig = sig[u];
-            w.rr[r[u]] = rec;
+            put_rowrec(w, r[u], s[u], e[u], sig[u]);
             w.wmr[r[u]] = x[u];
         }
 #pragma unroll
@@ -1115,14 +1114,26 @@ __device__ __forceinline__ void resolve_lookups(
     const LookupQueue &qu, int head, int k, int lane, const int32_t *__restrict__ rowidx,
     const double *__restrict__ wv, const double *__restrict__ wm, const double *__restrict__ wmr,
     const unsigned long long *__restrict__ htab, const uint32_t *__restrict__ bloom,
-    const int32_t *__restrict__ trowptr, const int32_t *__restrict__ tpos, int32_t nnz, Rec *__restrict__ best, uint32_t *winbits,
+    const int32_t *__restrict__ trowptr, const int32_t *__restrict__ tpos,
+    const int2 *__restrict__ rrange, int32_t nnz, Rec *__restrict__ best, uint32_t *winbits,
     Ctl *ctl, uint32_t &n_found, uint32_t &n_pos)
 {
     const int x = (head + lane) & (kQueue - 1);
     const bool act = lane < k;
     const int32_t mj = act ? qu.mj[x] : 0;
-    int32_t lo = act ? qu.lo[x] : 0;
-    int32_t len = act ? qu.len[x] : 0;
+    // column m_i's rows rowidx[lo, lo + len): queued with row marking (the
+    // filter needed them), else read here from the row record of i
+    int32_t lo = 0, len = 0;
+    if (act) {
+        if (kLookup == AWPM_LOOKUP_ROWMARK) {
+            lo = qu.lo[x];
+            len = qu.len[x];
+        } else {
+            const int2 rg = __ldg(rrange + qu.i[x]);
+            lo = rg.x;
+            len = rg.y - rg.x;
+        }
+    }
     int32_t q = -1;
     if (kLookup == AWPM_LOOKUP_HASH) {
         const int32_t hbase = 2 * lo;
@@ -1250,8 +1261,12 @@ __device__ __forceinline__ void resolve_lookups(
 // resolve_lookups).  Step-C records (Algorithm 5) are combined by a 128-bit
 // compare-and-swap; `best` must be zero on entry: only positive records are
 // written.  In a batched solve, tiles of finished matrices are skipped.
+#ifndef AWPM_SEARCH_MINB_WIDE
+#define AWPM_SEARCH_MINB_WIDE 4
+#endif
 template <int kLookup, bool kBatch, bool kWide>
-__global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *__restrict__ W)
+__global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
+    k_search(const Work *__restrict__ W)
 {
     __shared__ int s_go;
     __shared__ LookupQueue s_queue[kThreads / 32];
@@ -1266,7 +1281,8 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
     const uint32_t *__restrict__ starts = W->starts;
     const int32_t *__restrict__ mc = W->mc;
     const double *__restrict__ wm = W->wm;
-    const RowRec *__restrict__ rr = W->rr;
+    const unsigned long long *__restrict__ rsig = W->rsig;
+    const int2 *__restrict__ rrange = W->rrange;
     const double *__restrict__ wmr = W->wmr;
     const unsigned long long *__restrict__ htab = W->htab;
     const uint32_t *__restrict__ bloom = W->bloom;
@@ -1292,7 +1308,7 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
     auto flush = [&](int k) {
         __syncwarp();
         resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, wmr, htab, bloom, trowptr,
-                                 tpos, nnz, best, winbits, ctl, n_found, n_pos);
+                                 tpos, rrange, nnz, best, winbits, ctl, n_found, n_pos);
         __syncwarp();
         qhead = (qhead + k) & (kQueue - 1);
         qn -= k;
@@ -1383,30 +1399,32 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
                 jv[u] = valid[u] ? lane_column(c0[u], mask[u], lane) : -1 - lane;
                 mjv[u] = valid[u] ? ld_i32_last(mc + jv[u], pol) : 0x7fffffff;
             }
-            RowRec rec[kU];
-            unsigned long long mark[kU];
+            unsigned long long sig[kU], mark[kU];
+            int2 rg[kU];
             bool cand[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 if (kBatch && mixed[u] && valid[u] && __ldg(mdone + __ldg(colmat + jv[u])))
                     mjv[u] = 0x7fffffff;  // finished matrix: no candidate
                 cand[u] = valid[u] && iv[u] > mjv[u];
-                rec[u].s = rec[u].e = 0;
-                rec[u].sig = 0ull;
+                sig[u] = 0ull;
                 mark[u] = 0ull;
+                rg[u] = make_int2(0, 0);
                 if (cand[u]) {
                     ++n_cand;
-                    rec[u] = ld_rowrec(rr + iv[u], pol);
-                    if (kLookup == AWPM_LOOKUP_ROWMARK)
+                    sig[u] = ld_u64_last(rsig + iv[u], pol);
+                    if (kLookup == AWPM_LOOKUP_ROWMARK) {
+                        rg[u] = __ldg(rrange + iv[u]);
                         mark[u] = __ldg(rowsig + mjv[u]);  // the mark of row m_j
+                    }
                 }
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 // row m_j in column m_i's signature; with row marking also
-                // column m_i (first position rec.s) marked by row m_j
-                const bool pass = cand[u] && sig_has(rec[u].sig, mjv[u]) &&
-                                  (kLookup != AWPM_LOOKUP_ROWMARK || sig_has(mark[u], rec[u].s));
+                // column m_i (first position rg.x) marked by row m_j
+                const bool pass = cand[u] && sig_has(sig[u], mjv[u]) &&
+                                  (kLookup != AWPM_LOOKUP_ROWMARK || sig_has(mark[u], rg[u].x));
                 const unsigned need = __ballot_sync(FULL_MASK, pass);
                 if (pass) {
                     const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
@@ -1414,8 +1432,10 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
                     qu.p[x] = pv[u];
                     qu.i[x] = iv[u];
                     qu.mj[x] = mjv[u];
-                    qu.lo[x] = rec[u].s;
-                    qu.len[x] = rec[u].e - rec[u].s;
+                    if (kLookup == AWPM_LOOKUP_ROWMARK) {
+                        qu.lo[x] = rg[u].x;
+                        qu.len[x] = rg[u].y - rg[u].x;
+                    }
                 }
                 qn += __popc(need);
                 if (qn >= 32)
@@ -1428,6 +1448,185 @@ __global__ void __launch_bounds__(kThreads, kWide ? 4 : 6) k_search(const Work *
         if (!more)
             break;
     }
+    block_add_u64((unsigned long long)n_cand, &ctl->candidates);
+    block_add_u64((unsigned long long)n_found, &ctl->found);
+    block_add_u64((unsigned long long)n_pos, &ctl->positive);
+}
+
+// Pipelined form of the single-problem search (same work, same results as
+// k_search<kLookup, false, ...>).  A warp's tiles are taken kU at a time
+// (tiles t, t + nwarps, ...), and each round advances three stages at once,
+// each on loads issued one round earlier:
+//   R: the row records of round r-1 arrived: signature test, queue;
+//   M: the matched rows m_j of round r arrived: candidate test (i > m_j),
+//      row-record loads of the candidates issued;
+//   P: first column, start bits and row indices of round r+1 arrived: the
+//      lanes' columns, loads of m_j issued; loads of round r+2 issued.
+// So the two dependent gathers of a nonzero (m_j, then the row record of i)
+// are each hidden behind a round of other work instead of being waited for
+// back to back.  All tile arithmetic is 32-bit (ntiles < 2^26).
+#ifndef AWPM_PIPE_U_WIDE
+#define AWPM_PIPE_U_WIDE 2
+#endif
+#ifndef AWPM_PIPE_U_NARROW
+#define AWPM_PIPE_U_NARROW 1
+#endif
+#ifndef AWPM_PIPE_MINB_WIDE
+#define AWPM_PIPE_MINB_WIDE 4
+#endif
+#ifndef AWPM_PIPE_MINB_NARROW
+#define AWPM_PIPE_MINB_NARROW 5
+#endif
+template <bool kWide>
+struct PipeCfg {
+    static constexpr int kU = kWide ? AWPM_PIPE_U_WIDE : AWPM_PIPE_U_NARROW;
+    static constexpr int kMinBlocks = kWide ? AWPM_PIPE_MINB_WIDE : AWPM_PIPE_MINB_NARROW;
+};
+
+template <int kLookup, bool kWide>
+__global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
+    k_search_pipe(const Work *__restrict__ W)
+{
+    constexpr int kU = PipeCfg<kWide>::kU;
+    __shared__ int s_go;
+    __shared__ LookupQueue s_queue[kThreads / 32];
+    if (threadIdx.x == 0)
+        s_go = gate(W->ctl) ? 1 : 0;
+    __syncthreads();
+    const int32_t nnz = W->nnz;
+    const int32_t ntiles = W->ntiles;
+    const int32_t *__restrict__ rowidx = W->rowidx;
+    const double *__restrict__ wv = W->w;
+    const int32_t *__restrict__ tile_col = W->tile_col;
+    const uint32_t *__restrict__ starts = W->starts;
+    const int32_t *__restrict__ mc = W->mc;
+    const double *__restrict__ wm = W->wm;
+    const unsigned long long *__restrict__ rsig = W->rsig;
+    const int2 *__restrict__ rrange = W->rrange;
+    const double *__restrict__ wmr = W->wmr;
+    const unsigned long long *__restrict__ htab = W->htab;
+    const uint32_t *__restrict__ bloom = W->bloom;
+    const unsigned long long *__restrict__ rowsig = W->rowsig;
+    const int32_t *__restrict__ trowptr = W->trowptr;
+    const int32_t *__restrict__ tpos = W->tpos;
+    Rec *__restrict__ best = W->best;
+    uint32_t *winbits = W->winbits;
+    Ctl *ctl = W->ctl;
+    LookupQueue &qu = s_queue[threadIdx.x >> 5];
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    const int32_t nwarps = (int32_t)(gstride() >> 5);
+    const int32_t stride = kU * nwarps;
+    const unsigned long long pol = policy_evict_last();
+    uint32_t n_cand = 0, n_found = 0, n_pos = 0;
+    int qhead = 0, qn = 0;  // the warp's queue (warp-uniform)
+
+    auto flush = [&](int k) {
+        __syncwarp();
+        resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, wmr, htab, bloom, trowptr,
+                                 tpos, rrange, nnz, best, winbits, ctl, n_found, n_pos);
+        __syncwarp();
+        qhead = (qhead + k) & (kQueue - 1);
+        qn -= k;
+    };
+
+    const int32_t t0 = s_go ? (int32_t)(gtid() >> 5) : ntiles;
+    // stage P: loads of a round's tiles (first column, start bits, row index)
+    int32_t pc0[kU], pi[kU];
+    uint32_t pmask[kU];
+    // stage M: columns, rows and the loads of m_j in flight
+    int32_t mj_[kU], mi_[kU], mm_[kU];
+    // stage R: the row records in flight (and, with row marking, the mark of m_j)
+    int32_t rj[kU], ri[kU], rm[kU];
+    unsigned long long rsg[kU], rmark[kU];
+    int2 rrg[kU];
+    bool rcand[kU];
+
+    auto load_p = [&](int32_t tr) {
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int32_t tu = tr + u * nwarps;
+            pc0[u] = 0;
+            pmask[u] = 1u;
+            pi[u] = 0;
+            if (tu < ntiles) {
+                pc0[u] = __ldg(tile_col + tu);
+                pmask[u] = __ldg(starts + tu);
+                const int32_t pp = tu * kTile + lane;
+                pi[u] = pp < nnz ? __ldcs(rowidx + pp) : 0;
+            }
+        }
+    };
+    auto p_to_m = [&](int32_t tr) {
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int32_t tu = tr + u * nwarps;
+            const bool valid = tu < ntiles && tu * kTile + lane < nnz;
+            mi_[u] = valid ? pi[u] : 0;
+            mj_[u] = valid ? lane_column(pc0[u], pmask[u], lane) : -1;
+            mm_[u] = valid ? ld_i32_last(mc + mj_[u], pol) : 0x7fffffff;
+        }
+    };
+
+    load_p(t0);
+    p_to_m(t0);
+    load_p(t0 + stride);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        rcand[u] = false;
+        rj[u] = ri[u] = rm[u] = 0;
+        rsg[u] = 0ull;
+        rrg[u] = make_int2(0, 0);
+        rmark[u] = 0ull;
+    }
+    for (int32_t tr = t0;; tr += stride) {
+        // R: signature tests of the previous round, passing requests queued
+        const int32_t tprev = tr - stride;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const bool pass = rcand[u] && sig_has(rsg[u], rm[u]) &&
+                              (kLookup != AWPM_LOOKUP_ROWMARK || sig_has(rmark[u], rrg[u].x));
+            const unsigned need = __ballot_sync(FULL_MASK, pass);
+            if (pass) {
+                const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
+                qu.j[x] = rj[u];
+                qu.p[x] = (tprev + u * nwarps) * kTile + lane;
+                qu.i[x] = ri[u];
+                qu.mj[x] = rm[u];
+                if (kLookup == AWPM_LOOKUP_ROWMARK) {
+                    qu.lo[x] = rrg[u].x;
+                    qu.len[x] = rrg[u].y - rrg[u].x;
+                }
+            }
+            qn += __popc(need);
+            if (qn >= 32)
+                flush(32);
+        }
+        if (tr >= ntiles)
+            break;
+        // M: candidates of this round, their row records requested
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            rj[u] = mj_[u];
+            ri[u] = mi_[u];
+            rm[u] = mm_[u];
+            rcand[u] = mj_[u] >= 0 && mi_[u] > mm_[u];
+            if (rcand[u]) {
+                ++n_cand;
+                rsg[u] = ld_u64_last(rsig + mi_[u], pol);
+                if (kLookup == AWPM_LOOKUP_ROWMARK) {
+                    rrg[u] = __ldg(rrange + mi_[u]);
+                    rmark[u] = __ldg(rowsig + mm_[u]);
+                }
+            }
+        }
+        // P -> M for the next round, then the loads of the round after it
+        p_to_m(tr + stride);
+        load_p(tr + 2 * stride);
+    }
+    if (qn > 0)
+        flush(qn);
     block_add_u64((unsigned long long)n_cand, &ctl->candidates);
     block_add_u64((unsigned long long)n_found, &ctl->found);
     block_add_u64((unsigned long long)n_pos, &ctl->positive);
@@ -1522,17 +1721,9 @@ __global__ void k_flip(const Work *__restrict__ W)
                         w.mr[mj] = k;
                         w.wm[j] = wij;
                         w.wm[k] = wq;
-                        RowRec a;
-                        a.s = w.colptr[j];
-                        a.e = w.colptr[j + 1];
-                        a.sig = w.colsig[j];
-                        w.rr[i] = a;
+                        put_rowrec(w, i, w.colptr[j], w.colptr[j + 1], w.colsig[j]);
                         w.wmr[i] = wij;
-                        RowRec c;
-                        c.s = w.colptr[k];
-                        c.e = w.colptr[k + 1];
-                        c.sig = w.colsig[k];
-                        w.rr[mj] = c;
+                        put_rowrec(w, mj, w.colptr[k], w.colptr[k + 1], w.colsig[k]);
                         w.wmr[mj] = wq;
                         ++flips;
                         if (w.bw.count > 0)
@@ -2477,7 +2668,7 @@ __global__ void k_mc_cond_level(const Work *__restrict__ W, cudaGraphConditional
         c->levels += 1;
         // every level adds at least one row to the search forest
         if (++c->phase_levels > W->n + 1)
-            raise_err(c, kErrInternal);
+            raise_err(c, kErrTimeout);
     }
     cudaGraphSetConditional(h, (live > 0 && c->err == 0u) ? 1u : 0u);
 }
@@ -2626,12 +2817,18 @@ void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k)
         k.launch((const void *)k_batch_wsum, util_grid(sh), kThreads, ao);
 }
 
-template <int kLookup, bool kBatch, bool kWide>
-static int bps_of()
+bool search_pipe()
+{
+    const char *v = getenv("AWPM_SEARCH_PIPE");
+    if (v && (v[0] == '0' || v[0] == '1') && v[1] == 0)
+        return v[0] == '1';
+    return true;
+}
+
+static int bps_clamp(const void *f)
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<kLookup, kBatch, kWide>,
-                                                      kThreads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kThreads, 0) != cudaSuccess) {
         cudaGetLastError();
         b = 1;
     }
@@ -2641,6 +2838,13 @@ static int bps_of()
 template <bool kWide>
 static const void *search_fn(int lookup, bool batch)
 {
+    if (!batch && search_pipe()) {
+        if (lookup == AWPM_LOOKUP_ROWMARK)
+            return (const void *)k_search_pipe<AWPM_LOOKUP_ROWMARK, kWide>;
+        if (lookup == AWPM_LOOKUP_HASH)
+            return (const void *)k_search_pipe<AWPM_LOOKUP_HASH, kWide>;
+        return (const void *)k_search_pipe<AWPM_LOOKUP_BSEARCH, kWide>;
+    }
     if (lookup == AWPM_LOOKUP_ROWMARK)
         return batch ? (const void *)k_search<AWPM_LOOKUP_ROWMARK, true, kWide>
                      : (const void *)k_search<AWPM_LOOKUP_ROWMARK, false, kWide>;
@@ -2653,25 +2857,7 @@ static const void *search_fn(int lookup, bool batch)
 
 int search_blocks_per_sm(int lookup, bool batch, bool wide)
 {
-    if (lookup == AWPM_LOOKUP_ROWMARK) {
-        if (wide)
-            return batch ? bps_of<AWPM_LOOKUP_ROWMARK, true, true>()
-                         : bps_of<AWPM_LOOKUP_ROWMARK, false, true>();
-        return batch ? bps_of<AWPM_LOOKUP_ROWMARK, true, false>()
-                     : bps_of<AWPM_LOOKUP_ROWMARK, false, false>();
-    }
-    if (wide) {
-        if (lookup == AWPM_LOOKUP_HASH)
-            return batch ? bps_of<AWPM_LOOKUP_HASH, true, true>()
-                         : bps_of<AWPM_LOOKUP_HASH, false, true>();
-        return batch ? bps_of<AWPM_LOOKUP_BSEARCH, true, true>()
-                     : bps_of<AWPM_LOOKUP_BSEARCH, false, true>();
-    }
-    if (lookup == AWPM_LOOKUP_HASH)
-        return batch ? bps_of<AWPM_LOOKUP_HASH, true, false>()
-                     : bps_of<AWPM_LOOKUP_HASH, false, false>();
-    return batch ? bps_of<AWPM_LOOKUP_BSEARCH, true, false>()
-                 : bps_of<AWPM_LOOKUP_BSEARCH, false, false>();
+    return bps_clamp(wide ? search_fn<true>(lookup, batch) : search_fn<false>(lookup, batch));
 }
 
 bool default_search_wide()

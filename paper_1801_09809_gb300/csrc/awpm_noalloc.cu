@@ -11,9 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "awpm.h"
 #include "awpm_internal.h"
@@ -51,30 +49,20 @@ constexpr size_t kScratchBytes = kOffWpart + up(sizeof(double) * kWsumBlocks);
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch per device.  In host code the name g_scratch
-// is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, taken once per device with that device current.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
-
-thread_local char g_msg[256] = "";
-
-int scratch_address(int device, unsigned char **out)
+// Device address of g_scratch on the current device.  In host code the name
+// g_scratch is only a host-side stand-in, so the address comes from
+// cudaGetSymbolAddress with the device current.  It is looked up on every
+// call (a table lookup once the module is loaded), so a context re-created
+// after cudaDeviceReset never sees a stale address.
+int scratch_address(unsigned char **out)
 {
-    if (device < 0 || device >= kMaxDevices)
-        return AWPM_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
-            std::snprintf(g_msg, sizeof(g_msg), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            return AWPM_ERR_CUDA;
-        }
-        g_addr[device] = p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return AWPM_ERR_CUDA;
     }
-    *out = (unsigned char *)g_addr[device];
+    *out = (unsigned char *)p;
     return AWPM_OK;
 }
 
@@ -130,7 +118,7 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
         return AWPM_ERR_TOO_LARGE;
 
     unsigned char *base = nullptr;
-    int rc = scratch_address(device, &base);
+    int rc = scratch_address(&base);
     if (rc != AWPM_OK)
         return rc;
     int num_sms = 1;
@@ -156,6 +144,8 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     wk.mr = (int32_t *)(base + kOffMr);
     wk.wm = (double *)(base + kOffWm);
     wk.rr = (RowRec *)(base + kOffRr);
+    wk.rsig = (unsigned long long *)(base + kOffRr);
+    wk.rrange = (int2 *)(wk.rsig + n);
     wk.wmr = (double *)(base + kOffWmr);
     wk.colsig = (unsigned long long *)(base + kOffSig);
     wk.best = (Rec *)(base + kOffBest);
@@ -199,16 +189,8 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
         cudaGetLastError();
         return AWPM_ERR_CUDA;
     }
-    if (h.err & kErrInvalid)
-        return AWPM_ERR_INVALID_ARG;
-    if (h.err & kErrUnsorted)
-        return AWPM_ERR_UNSORTED_OR_DUP;
-    if (h.err & kErrNonfinite)
-        return AWPM_ERR_NONFINITE;
-    if (h.err & kErrNotPerfect)
-        return AWPM_ERR_NOT_PERFECT;
     if (h.err)
-        return AWPM_ERR_TIMEOUT;
+        return awpm_code_of_bits(h.err);
     S.iterations = 0;
     S.converged = 0;
     S.edge_checks = (int64_t)nnz - n;

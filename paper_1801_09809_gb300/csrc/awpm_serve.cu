@@ -12,6 +12,14 @@
 // one frees its slot; completion is detected by polling each slot's event.
 // Each request is solved exactly as by awpm_improve on its own, so its
 // result does not depend on what else is running.
+//
+// Memory: a request's need is estimated from n and nnz (nnz read from a
+// device colptr at admission when the caller did not give it); a slot is
+// given, for the solve it starts, a budget of what the other slots leave,
+// so its workspace can never push the total past the context's budget;
+// idle slots give their workspaces back when that lets a waiting request
+// in.  Fairness: a request that later ones have overtaken kMaxPassed times
+// is the only one admitted until it fits.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -32,6 +40,7 @@ namespace {
 
 constexpr int kDefaultSlots = 4;
 constexpr int kAdmitLookahead = 8;
+constexpr int kMaxPassed = 16;
 
 struct Item {
     uint64_t ticket = 0;
@@ -40,6 +49,9 @@ struct Item {
     int rc = AWPM_OK;
     awpm_stats st{};
     size_t need = 0;
+    bool sized = false;  // nnz known (given, or read from colptr[n])
+    bool host_in = true;
+    int passed = 0;      // times a later request was admitted before this one
 };
 
 }  // namespace
@@ -56,6 +68,8 @@ struct awpm_server_impl {
     uint64_t next_ticket = 1;
     bool stop = false;
     size_t budget = 0;
+    size_t peak = 0;               // most device bytes all slots held at once
+    cudaStream_t aux = nullptr;    // reads colptr[n] of device inputs at admission
     std::thread th;
 };
 
@@ -87,8 +101,9 @@ void finish_item(awpm_server_impl *s, Item *it, int rc)
 }
 
 // Start `it` on free slot k (server lock held by the caller; released around
-// the CUDA calls).
-void start(awpm_server_impl *s, std::unique_lock<std::mutex> &lk, int k, Item *it)
+// the CUDA calls).  cap: the device bytes the slot may hold for this solve
+// (0 = no limit).
+void start(awpm_server_impl *s, std::unique_lock<std::mutex> &lk, int k, Item *it, size_t cap)
 {
     it->state = 1;
     s->running[k] = it;
@@ -105,18 +120,112 @@ void start(awpm_server_impl *s, std::unique_lock<std::mutex> &lk, int k, Item *i
     int rc;
     {
         std::lock_guard<std::mutex> cl(c->mu);
+        c->opt.mem_budget_bytes = cap;
         rc = ctx_enqueue(c, r);
         if (rc != AWPM_OK) {
             cudaStreamSynchronize(c->stream);
             cudaGetLastError();
             c->pend.active = false;
         }
+        if (rc == AWPM_ERR_BUDGET && cap) {
+            // buffers kept from earlier, differently shaped problems can
+            // leave too little room: start again from an empty workspace
+            // (the request's estimate fits the cap)
+            ctx_trim(c);
+            rc = ctx_enqueue(c, r);
+            if (rc != AWPM_OK) {
+                cudaStreamSynchronize(c->stream);
+                cudaGetLastError();
+                c->pend.active = false;
+            }
+        }
     }
     lk.lock();
+    const size_t h = held_total(s);
+    if (h > s->peak)
+        s->peak = h;
     if (rc != AWPM_OK) {
         s->running[k] = nullptr;
         finish_item(s, it, rc);
     }
+}
+
+// Make the request's need exact: with nnz not given and colptr in device
+// memory, read colptr[n] (a 4-byte copy on the server's own stream).
+void size_item(awpm_server_impl *s, Item *it)
+{
+    if (it->sized)
+        return;
+    it->sized = true;
+    int32_t nnz = it->p.nnz;
+    if (nnz < 0 && it->p.n > 0 && it->p.colptr) {
+        int32_t v = -1;
+        if (cudaMemcpyAsync(&v, it->p.colptr + it->p.n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            s->aux) == cudaSuccess &&
+            cudaStreamSynchronize(s->aux) == cudaSuccess) {
+            nnz = v;
+            it->p.nnz = v;
+        } else {
+            cudaGetLastError();  // the solve itself reports the bad pointer
+        }
+    }
+    it->need = ctx_bytes_needed(it->p.n, nnz > 0 ? nnz : 0, it->host_in, s->owner->opt.lookup,
+                                s->owner->opt.select);
+}
+
+// Pick the queued request to start on free slot k, or -1.  Requests that can
+// never fit the budget are finished with AWPM_ERR_BUDGET on the way.
+int pick_request(awpm_server_impl *s, int k, bool *progress)
+{
+    for (;;) {
+        const int look = (int)s->queue.size() < kAdmitLookahead ? (int)s->queue.size()
+                                                                 : kAdmitLookahead;
+        bool failed = false;
+        for (int x = 0; x < look; ++x) {
+            Item *it = s->queue[x];
+            size_item(s, it);
+            if (s->budget && it->need > s->budget) {
+                s->queue.erase(s->queue.begin() + x);
+                finish_item(s, it, AWPM_ERR_BUDGET);
+                *progress = true;
+                failed = true;
+                break;
+            }
+        }
+        if (!failed)
+            break;
+    }
+    if (s->queue.empty())
+        return -1;
+    if (!s->budget)
+        return 0;
+    // a head overtaken often enough goes next, alone
+    const int look = s->queue.front()->passed >= kMaxPassed
+                         ? 1
+                         : ((int)s->queue.size() < kAdmitLookahead ? (int)s->queue.size()
+                                                                   : kAdmitLookahead);
+    const size_t held = held_total(s);
+    const size_t mine = ctx_bytes_held(s->slots[k]);
+    size_t idle = 0;  // workspace of the other idle slots (can be given back)
+    for (size_t q = 0; q < s->slots.size(); ++q)
+        if ((int)q != k && !s->running[q])
+            idle += ctx_bytes_held(s->slots[q]);
+    for (int x = 0; x < look; ++x) {
+        const Item *it = s->queue[x];
+        const size_t grow = it->need > mine ? it->need - mine : 0;
+        if (held + grow <= s->budget)
+            return x;
+        if (held - idle + grow <= s->budget) {
+            // it fits once the idle slots free their workspaces
+            for (size_t q = 0; q < s->slots.size(); ++q)
+                if ((int)q != k && !s->running[q] && ctx_bytes_held(s->slots[q])) {
+                    std::lock_guard<std::mutex> cl(s->slots[q]->mu);
+                    ctx_trim(s->slots[q]);
+                }
+            return x;
+        }
+    }
+    return -1;
 }
 
 void scheduler(awpm_server_impl *s)
@@ -149,31 +258,17 @@ void scheduler(awpm_server_impl *s)
         for (size_t k = 0; k < s->slots.size() && !s->queue.empty(); ++k) {
             if (s->running[k])
                 continue;
-            const size_t held = held_total(s);
-            const size_t mine = ctx_bytes_held(s->slots[k]);
-            int pick = -1;
-            const int look = (int)s->queue.size() < kAdmitLookahead ? (int)s->queue.size()
-                                                                     : kAdmitLookahead;
-            for (int x = 0; x < look; ++x) {
-                Item *it = s->queue[x];
-                const size_t grow = it->need > mine ? it->need - mine : 0;
-                if (!s->budget || held + grow <= s->budget) {
-                    pick = x;
-                    break;
-                }
-                if (s->budget && it->need > s->budget) {
-                    // can never fit: fail it instead of blocking the queue
-                    s->queue.erase(s->queue.begin() + x);
-                    finish_item(s, it, AWPM_ERR_BUDGET);
-                    progress = true;
-                    break;
-                }
-            }
+            const int pick = pick_request(s, (int)k, &progress);
             if (pick < 0)
                 continue;
             Item *it = s->queue[pick];
+            if (pick > 0)
+                s->queue.front()->passed += 1;
             s->queue.erase(s->queue.begin() + pick);
-            start(s, lk, (int)k, it);
+            // the slot may hold what the other slots leave of the budget
+            const size_t others = held_total(s) - ctx_bytes_held(s->slots[k]);
+            const size_t cap = s->budget ? (s->budget > others ? s->budget - others : 1) : 0;
+            start(s, lk, (int)k, it, cap);
             progress = true;
         }
         bool busy = false;
@@ -206,6 +301,12 @@ awpm_server_impl *server_of(awpm_ctx *ctx, int *rc)
     s->budget = ctx->opt.mem_budget_bytes;
     const int nslots = ctx->opt.slots > 0 ? ctx->opt.slots : kDefaultSlots;
     cudaSetDevice(ctx->device);
+    if (cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        *rc = AWPM_ERR_CUDA;
+        return nullptr;
+    }
     for (int k = 0; k < nslots; ++k) {
         // slot streams do not synchronise with the legacy default stream:
         // requests run beside whatever the caller's threads do
@@ -216,6 +317,7 @@ awpm_server_impl *server_of(awpm_ctx *ctx, int *rc)
                 awpm_destroy(x);
             for (cudaStream_t y : s->streams)
                 cudaStreamDestroy(y);
+            cudaStreamDestroy(s->aux);
             delete s;
             *rc = AWPM_ERR_CUDA;
             return nullptr;
@@ -234,6 +336,7 @@ awpm_server_impl *server_of(awpm_ctx *ctx, int *rc)
                 awpm_destroy(x);
             for (cudaStream_t y : s->streams)
                 cudaStreamDestroy(y);
+            cudaStreamDestroy(s->aux);
             delete s;
             *rc = r;
             return nullptr;
@@ -274,9 +377,27 @@ void awpm_server_shutdown(awpm_ctx *ctx)
         awpm_destroy(c);
     for (cudaStream_t st : s->streams)
         cudaStreamDestroy(st);
+    if (s->aux)
+        cudaStreamDestroy(s->aux);
     for (auto &kv : s->items)
         delete kv.second;
     delete s;
+}
+
+void awpm_server_memory(awpm_ctx *ctx, size_t *held, size_t *peak)
+{
+    *held = 0;
+    *peak = 0;
+    awpm_server_impl *s;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        s = ctx->server;
+    }
+    if (!s)
+        return;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *held = held_total(s);
+    *peak = s->peak;
 }
 
 int awpm_submit(awpm_ctx *ctx, const awpm_problem *p, uint64_t *ticket)
@@ -291,11 +412,13 @@ int awpm_submit(awpm_ctx *ctx, const awpm_problem *p, uint64_t *ticket)
     if (!it)
         return AWPM_ERR_OOM;
     it->p = *p;
-    int32_t nnz = p->nnz;
-    const bool host_in = host_side(p->rowidx);
-    if (nnz < 0 && p->colptr && host_side(p->colptr))
-        nnz = p->colptr[p->n];
-    it->need = ctx_bytes_needed(p->n, nnz > 0 ? nnz : 0, host_in, ctx->opt.lookup);
+    it->host_in = host_side(p->rowidx);
+    if (it->p.nnz < 0 && p->colptr && host_side(p->colptr))
+        it->p.nnz = p->colptr[p->n];
+    // a device colptr without nnz is read at admission (size_item)
+    it->sized = it->p.nnz >= 0 || p->n == 0 || !p->colptr;
+    it->need = ctx_bytes_needed(p->n, it->p.nnz > 0 ? it->p.nnz : 0, it->host_in,
+                                ctx->opt.lookup, ctx->opt.select);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         it->ticket = s->next_ticket++;
@@ -334,6 +457,35 @@ int awpm_poll(awpm_ctx *ctx, uint64_t ticket, int *done, awpm_stats *stats)
     s->items.erase(f);
     delete it;
     return rc;
+}
+
+int awpm_cancel(awpm_ctx *ctx, uint64_t ticket, int *cancelled)
+{
+    if (!ctx || !cancelled)
+        return AWPM_ERR_INVALID_ARG;
+    *cancelled = 0;
+    awpm_server_impl *s;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        s = ctx->server;
+    }
+    if (!s)
+        return AWPM_ERR_NOT_FOUND;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto f = s->items.find(ticket);
+    if (f == s->items.end())
+        return AWPM_ERR_NOT_FOUND;
+    Item *it = f->second;
+    if (it->state == 0) {
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+            if (*q == it) {
+                s->queue.erase(q);
+                break;
+            }
+        finish_item(s, it, AWPM_ERR_CANCELLED);
+        *cancelled = 1;
+    }
+    return AWPM_OK;
 }
 
 int awpm_wait(awpm_ctx *ctx, uint64_t ticket, awpm_stats *stats)
