@@ -49,8 +49,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the CPU baselines (profiling runs of the GPU path)")
     ap.add_argument("--batch-count", type=int, default=4096)
-    ap.add_argument("--serve-requests", type=int, default=2000)
-    ap.add_argument("--serve-pool", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-pool", type=int, default=160)
+    ap.add_argument("--serve-low-requests", type=int, default=5000,
+                    help="requests of the low-load and sweep points of the served comparison")
     ap.add_argument("--lookup", default="auto", choices=["auto", "bsearch", "hash", "rowmark"],
                     help="closing-edge lookup (auto: the library's autotuner picks)")
     ap.add_argument("--workload", default="rmat",
@@ -488,93 +490,182 @@ def bench_batched(awpm, torch, dev, count):
             "identical_outputs": bool(same and same_timed)}
 
 
-def bench_served(awpm, torch, dev, requests, pool_size, budget=100 * 10**9):
+def _gen_spec(spec):
+    from paper_1801_09809_gb300 import gen
+    return gen.build_spec(spec)
+
+
+SERVE_ORACLE = os.path.join(ROOT, "tests", "golden", "serve_pool_oracle.json")
+
+
+def _digest(*arrays):
+    h = hashlib.sha256()
+    for a in arrays:
+        h.update(memoryview(np.ascontiguousarray(a)).cast("B"))
+    return h.hexdigest()[:32]
+
+
+def bench_served(awpm, torch, dev, requests, pool_size, low_requests, budget=100 * 10**9):
     """Poisson stream of matching requests (n log-uniform in [1e3, 1e6]; random
     sparse, 2D 5-point, 3D 27-point, R-MAT; degree 4-27) drawn from a pool of
     distinct generated problems with pinned host inputs.  Served: the request
     server (continuous batching over 4 slots, 100 GB budget).  Baseline: one
-    synchronous awpm_improve per request in arrival order.  Rate: 0.7 x the
-    served capacity measured on the same mix."""
+    synchronous awpm_improve per request in arrival order.  Points: all
+    requests at 0.7 x the served capacity (both forms); the first
+    `low_requests` at 0.5 x the baseline's own capacity (both forms, neither
+    saturated); the served form alone at 0.3 / 0.5 / 0.9 of its capacity.
+    Every request's passes, cycles and weight must equal those of the pool
+    problem solved alone, the last output of each problem its matching, and
+    each pool problem's matching the oracle's (stored digests, written by
+    tests/golden/make_serve_oracle.py)."""
+    import multiprocessing as mp
     from paper_1801_09809_gb300 import gen
     specs = gen.serve_spec(pool_size, seed=gen.SEED_BASE + 6)
-    pool = [gen.build_spec(sp) for sp in specs]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as gp:
+        pool = gp.map(_gen_spec, specs, chunksize=1)
     pin = [[torch.from_numpy(a).pin_memory() for a in (g.colptr, g.rowidx, g.weight, g.mate)]
            for g in pool]
     rng = np.random.default_rng(gen.SEED_BASE + 66)
     pick = rng.integers(0, pool_size, size=requests)
-    refs = {}
     solo = awpm.awpm_create(device=dev.index or 0)
+    refs, ref_st = {}, {}
     for k, g in enumerate(pool):
         o = torch.empty(g.n, dtype=torch.int32).pin_memory()
-        awpm.awpm_improve_ctx(solo, g.n, *pin[k], o)
+        st = awpm.awpm_improve_ctx(solo, g.n, *pin[k], o)
         refs[k] = o.numpy().copy()
-    outs = [torch.empty(pool[k].n, dtype=torch.int32).pin_memory() for k in pick]
+        ref_st[k] = (st["iterations"], st["cycles_applied"], st["weight_out"])
+    # the pool against the oracle's stored results (same generated inputs)
+    checked = agree = unverifiable = 0
+    try:
+        recs = json.load(open(SERVE_ORACLE))["records"]
+    except (OSError, ValueError, KeyError):
+        recs = []
+    for k, g in enumerate(pool[:len(recs)]):
+        r = recs[k]
+        if r["input"] != _digest(g.colptr, g.rowidx, g.weight, g.mate):
+            unverifiable += 1
+            continue
+        checked += 1
+        agree += int(r["mate"] == _digest(refs[k].astype(np.int32)) and
+                     r["iterations"] == ref_st[k][0] and r["cycles_applied"] == ref_st[k][1])
+    # output buffers: a ring per pool problem (a request whose ring slot is
+    # still in use writes to a spare and only its statistics are checked)
+    depth = 16
+    ring = [[torch.full((g.n,), -1, dtype=torch.int32).pin_memory() for _ in range(depth)]
+            for g in pool]
+    written = set()
+    spare = torch.empty(max(g.n for g in pool), dtype=torch.int32).pin_memory()
+    bad = [0]
 
-    def serve(arrivals):
+    def check_stats(r, st):
+        k = pick[r]
+        if (st["iterations"], st["cycles_applied"], st["weight_out"]) != ref_st[k]:
+            bad[0] += 1
+
+    def serve(arrivals, count, max_out=None):
         ctx = awpm.awpm_create(device=dev.index or 0, slots=4, mem_budget_bytes=budget)
-        lat = np.zeros(requests)
+        lat = np.zeros(count)
+        busy = [[False] * depth for _ in pool]
+        nxt_slot = [0] * pool_size
         t0 = time.perf_counter()
         tickets = {}
         nxt = 0
-        while nxt < requests or tickets:
+        while nxt < count or tickets:
             now = time.perf_counter() - t0
-            while nxt < requests and arrivals[nxt] <= now:
+            while nxt < count and arrivals[nxt] <= now and (max_out is None or
+                                                             len(tickets) < max_out):
                 k = pick[nxt]
-                g = pool[k]
-                tickets[nxt] = awpm.awpm_submit(ctx, g.n, *pin[k], outs[nxt], nnz=g.nnz)
+                c = nxt_slot[k]
+                if not busy[k][c]:
+                    busy[k][c] = True
+                    nxt_slot[k] = (c + 1) % depth
+                    out = ring[k][c]
+                else:
+                    c, out = -1, spare
+                tickets[nxt] = (awpm.awpm_submit(ctx, pool[k].n, *pin[k], out,
+                                                 nnz=pool[k].nnz), c)
                 nxt += 1
             for r in list(tickets):
-                done, _ = awpm.awpm_poll(ctx, tickets[r])
+                done, st = awpm.awpm_poll(ctx, tickets[r][0])
                 if done:
                     lat[r] = time.perf_counter() - t0 - arrivals[r]
+                    check_stats(r, st)
+                    if tickets[r][1] >= 0:
+                        busy[pick[r]][tickets[r][1]] = False
+                        written.add((int(pick[r]), tickets[r][1]))
                     del tickets[r]
-            if nxt < requests and not tickets:
+            if nxt < count and not tickets:
                 time.sleep(max(0.0, min(0.0005, arrivals[nxt] - (time.perf_counter() - t0))))
         total = time.perf_counter() - t0
         awpm.awpm_destroy(ctx)
         return lat, total
 
-    def one_by_one(arrivals):
-        lat = np.zeros(requests)
+    def one_by_one(arrivals, count):
+        lat = np.zeros(count)
+        service = 0.0
         t0 = time.perf_counter()
-        for r in range(requests):
+        for r in range(count):
             now = time.perf_counter() - t0
             if arrivals[r] > now:
                 time.sleep(arrivals[r] - now)
             k = pick[r]
-            g = pool[k]
-            awpm.awpm_improve_ctx(solo, g.n, *pin[k], outs[r])
+            s0 = time.perf_counter()
+            st = awpm.awpm_improve_ctx(solo, pool[k].n, *pin[k], ring[k][0])
+            service += time.perf_counter() - s0
+            written.add((int(k), 0))
             lat[r] = time.perf_counter() - t0 - arrivals[r]
-        return lat, time.perf_counter() - t0
+            check_stats(r, st)
+        return lat, time.perf_counter() - t0, service
 
-    # capacity of the served form on this mix (all requests at time 0)
-    lat0, total0 = serve(np.zeros(requests))
+    ms = lambda a, q: float(1e3 * np.percentile(a, q))
+
+    def point(lat, total, count):
+        return {"p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99), "solves_per_s": count / total}
+
+    # capacity of the served form on this mix (all requests waiting; at most
+    # 64 queued at a time)
+    lat0, total0 = serve(np.zeros(requests), requests, max_out=64)
     capacity = requests / total0
     rate = 0.7 * capacity
     arrivals = gen.poisson_arrivals(requests, rate)
-    lat_s, tot_s = serve(arrivals)
-    same_s = all(np.array_equal(outs[r].numpy(), refs[pick[r]]) for r in range(requests))
-    lat_b, tot_b = one_by_one(arrivals)
-    same_b = all(np.array_equal(outs[r].numpy(), refs[pick[r]]) for r in range(requests))
-    awpm.awpm_destroy(solo)
-    ms = lambda a, q: float(1e3 * np.percentile(a, q))
-    # the served form across offered loads (fractions of its capacity)
+    lat_s, tot_s = serve(arrivals, requests)
+    lat_b, tot_b, svc_b = one_by_one(arrivals, requests)
+    base_capacity = requests / svc_b
+    low_rate = 0.5 * base_capacity
+    low_arr = gen.poisson_arrivals(low_requests, low_rate, seed=gen.SEED_BASE + 67)
+    lat_sl, tot_sl = serve(low_arr, low_requests)
+    lat_bl, tot_bl, _ = one_by_one(low_arr, low_requests)
     sweep = []
     for load in (0.3, 0.5, 0.9):
-        lat_x, tot_x = serve(gen.poisson_arrivals(requests, load * capacity))
-        sweep.append({"load": load, "rate_per_s": load * capacity, "p50_ms": ms(lat_x, 50),
-                      "p99_ms": ms(lat_x, 99), "solves_per_s": requests / tot_x})
+        lat_x, tot_x = serve(gen.poisson_arrivals(low_requests, load * capacity,
+                                                  seed=gen.SEED_BASE + 68), low_requests)
+        sweep.append({"load": load, "rate_per_s": load * capacity, **point(lat_x, tot_x,
+                                                                             low_requests)})
+    awpm.awpm_destroy(solo)
+    # the last output written to each ring slot is that problem's matching
+    same_out = all(np.array_equal(ring[k][c].numpy(), refs[k]) for k, c in written)
     return {"workload": f"{requests} requests from a pool of {pool_size} generated problems "
                         "(n log-uniform [1e3, 1e6]; random sparse, 2D, 3D, R-MAT; degree 4-27), "
                         "pinned host inputs, Poisson arrivals",
-            "rate_per_s": rate, "served_capacity_solves_per_s": capacity,
-            "served": {"p50_ms": ms(lat_s, 50), "p99_ms": ms(lat_s, 99),
-                       "solves_per_s": requests / tot_s},
-            "one_launch_per_matrix": {"p50_ms": ms(lat_b, 50), "p99_ms": ms(lat_b, 99),
-                                      "solves_per_s": requests / tot_b},
+            "pool_size": pool_size, "pool_nnz_total": int(sum(g.nnz for g in pool)),
+            "pool_n_max": int(max(g.n for g in pool)),
+            "requests": requests, "rate_per_s": rate,
+            "served_capacity_solves_per_s": capacity,
+            "one_launch_per_matrix_capacity_solves_per_s": base_capacity,
+            "served": point(lat_s, tot_s, requests),
+            "one_launch_per_matrix": point(lat_b, tot_b, requests),
+            "low_load": {"requests": low_requests, "rate_per_s": low_rate,
+                         "load_of_one_launch_capacity": 0.5,
+                         "served": point(lat_sl, tot_sl, low_requests),
+                         "one_launch_per_matrix": point(lat_bl, tot_bl, low_requests)},
             "served_load_sweep": sweep,
             "slots": 4, "budget_bytes": budget,
-            "identical_outputs": bool(same_s and same_b)}
+            "oracle": {"pool_problems_checked": checked, "identical": bool(checked and
+                                                                          agree == checked),
+                       "unverifiable_inputs": unverifiable,
+                       "record": "tests/golden/serve_pool_oracle.json"},
+            "identical_outputs": bool(bad[0] == 0 and same_out),
+            "requests_with_other_statistics": bad[0]}
 
 
 def main():
@@ -754,7 +845,8 @@ def main():
     if not args.no_batched:
         line["batched"] = bench_batched(awpm, torch, dev, args.batch_count)
     if not args.no_served:
-        line["served"] = bench_served(awpm, torch, dev, args.serve_requests, args.serve_pool)
+        line["served"] = bench_served(awpm, torch, dev, args.serve_requests, args.serve_pool,
+                                      min(args.serve_low_requests, args.serve_requests))
     if rank == 0:
         cpu = world == 1 and not args.no_cpu
         line["cpu_baseline"] = cpu_baseline(g) if cpu else None

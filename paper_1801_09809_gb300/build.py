@@ -57,5 +57,26 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+def build_debug(lib: str, objdir: str) -> str:
+    """The same library compiled with AWPM_DEBUG_BOUNDS (device index checks
+    that report AWPM_ERR_INTERNAL instead of touching memory out of range),
+    written to `lib`; objects go to `objdir`.  Not part of build(): tests that
+    need it build it themselves and load it through AWPM_LIBRARY."""
+    os.makedirs(objdir, exist_ok=True)
+    procs, objs = [], []
+    for src in SOURCES:
+        o = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
+        objs.append(o)
+        cmd = [NVCC, *ARCH, *FLAGS, "-DAWPM_DEBUG_BOUNDS", "-c", os.path.join(CSRC, src), "-o", o]
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE,
+                                            stderr=subprocess.STDOUT)))
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("nvcc failed: " + " ".join(cmd) + "\n" + out.decode())
+    subprocess.check_call([NVCC, "-shared", *ARCH, *objs, "-o", lib])
+    return lib
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))

@@ -480,6 +480,7 @@ int run_timed(awpm_ctx *c, const Shape &sh, int max_passes, int *passes_enqueued
             if (!c->h_active[slot])
                 break;
         }
+        NvtxRange pass_range("pass");
         AWPM_TRY(ensure_timing_events(c, (size_t)t + 1));
         CUDA_TRY(cudaEventRecord(c->tev[2 * t], s));
         launch_search(d, sh, k);
@@ -539,7 +540,7 @@ namespace awpm {
 size_t ctx_bytes_needed(int32_t n, int32_t nnz, bool host_inputs, int lookup, int select)
 {
     const size_t N = (size_t)n, Z = (size_t)nnz, T = Z / kTile + 1;
-    size_t b = N * (4 + 4 + 8 + sizeof(RowRec) + 8 + 8 + sizeof(Rec) + sizeof(Sel) + 4) + N / 8 +
+    size_t b = N * (4 + 4 + 8 + sizeof(RowRange) + 8 + 8 + sizeof(Rec) + sizeof(Sel) + 4) + N / 8 +
                4 * T +
                4 * (Z / 32 + 1) + sizeof(Ctl) + 8 * kWsumBlocks;
     if (lookup != AWPM_LOOKUP_BSEARCH)  // hash tables (AUTO may pick them)
@@ -562,7 +563,7 @@ size_t ctx_bytes_held(const awpm_ctx *c)
 
 void ctx_trim(awpm_ctx *c)
 {
-    DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->wmr,
+    DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->rsig,
                       &c->colsig,  &c->best,     &c->dsel,     &c->tile_col, &c->starts,
                       &c->wpart,   &c->htab,     &c->b_noff,   &c->b_colmat, &c->b_tilemat,
                       &c->b_tlist, &c->b_i32,    &c->b_u64,    &c->b_f64,    &c->s_colptr,
@@ -571,7 +572,7 @@ void ctx_trim(awpm_ctx *c)
                       &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate,    &c->gtdead,
                       &c->psel,    &c->pslive,   &c->pstaken,  &c->psused,   &c->wt_cmax,
                       &c->wt_rmax, &c->wt_stage, &c->mroot,    &c->mrpar,    &c->mfront,
-                      &c->mnext,   &c->mrkey,    &c->mrcol,    &c->mtkey,    &c->mtrow,
+                      &c->mnext,   &c->mroff,    &c->mtend,
                       &c->mstage,  &c->mcolof,   &c->mtiles,   &c->rowsig,   &c->trowptr,
                       &c->rs_k0,   &c->rs_k1,    &c->rs_v0,    &c->rs_v1,    &c->rs_hist,
                       &c->rs_sums};
@@ -648,7 +649,7 @@ void teardown_ctx(awpm_ctx *c)
             c->g_mcm[v] = nullptr;
         }
     }
-    DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->wmr,
+    DevBuf *bufs[] = {&c->mc,      &c->mr,       &c->wm,       &c->rr,       &c->rsig,
                       &c->colsig,  &c->best,     &c->dsel,     &c->tile_col, &c->starts,
                       &c->ctl,     &c->wpart,    &c->htab,     &c->b_noff,   &c->b_colmat,
                       &c->b_tilemat, &c->b_tlist, &c->b_i32,  &c->b_u64,    &c->b_f64,    &c->s_colptr,
@@ -657,8 +658,8 @@ void teardown_ctx(awpm_ctx *c)
                       &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate,
                       &c->gtdead,  &c->psel,     &c->pslive,   &c->pstaken,  &c->psused,
                       &c->wt_cmax, &c->wt_rmax,  &c->wt_stage,
-                      &c->mroot,   &c->mrpar,    &c->mfront,   &c->mnext,    &c->mrkey,
-                      &c->mrcol,   &c->mtkey,    &c->mtrow,    &c->mstage,   &c->mcolof,
+                      &c->mroot,   &c->mrpar,    &c->mfront,   &c->mnext,    &c->mroff,
+                      &c->mtend,   &c->mstage,   &c->mcolof,
                       &c->mtiles,  &c->rowsig,   &c->trowptr,  &c->rs_k0,    &c->rs_k1,
                       &c->rs_v0,   &c->rs_v1,    &c->rs_hist,  &c->rs_sums};
     for (DevBuf *b : bufs)
@@ -686,6 +687,7 @@ void teardown_ctx(awpm_ctx *c)
 
 int ctx_enqueue(awpm_ctx *c, const Request &r)
 {
+    NvtxRange nvtx_range("enqueue");
     Pending &pd = c->pend;
     pd = Pending();
     const int32_t n = r.n;
@@ -755,8 +757,8 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     AWPM_TRY(ensure(c, c->mc, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->mr, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->wm, sizeof(double) * n));
-    AWPM_TRY(ensure(c, c->rr, sizeof(RowRec) * n));
-    AWPM_TRY(ensure(c, c->wmr, sizeof(double) * n));
+    AWPM_TRY(ensure(c, c->rr, sizeof(RowRange) * n));
+    AWPM_TRY(ensure(c, c->rsig, sizeof(unsigned long long) * n));
     AWPM_TRY(ensure(c, c->colsig, sizeof(unsigned long long) * n));
     AWPM_TRY(ensure(c, c->best, sizeof(Rec) * n));
     AWPM_TRY(ensure(c, c->dsel, sizeof(Sel) * n));
@@ -818,10 +820,8 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     wk.mc = (int32_t *)c->mc.p;
     wk.mr = (int32_t *)c->mr.p;
     wk.wm = (double *)c->wm.p;
-    wk.rr = (RowRec *)c->rr.p;
-    wk.rsig = (unsigned long long *)c->rr.p;
-    wk.rrange = (int2 *)(wk.rsig + n);
-    wk.wmr = (double *)c->wmr.p;
+    wk.rsig = (unsigned long long *)c->rsig.p;
+    wk.rrange = (RowRange *)c->rr.p;
     wk.colsig = (unsigned long long *)c->colsig.p;
     wk.htab = lookup == AWPM_LOOKUP_HASH ? (unsigned long long *)c->htab.p : nullptr;
     wk.bloom = lookup == AWPM_LOOKUP_BSEARCH && bloom_enabled() ? (uint32_t *)c->bloom.p : nullptr;
@@ -952,6 +952,7 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
 
 int ctx_finish(awpm_ctx *c, awpm_stats *st, awpm_stats *per_matrix)
 {
+    NvtxRange nvtx_range("finish");
     Pending &pd = c->pend;
     if (!pd.active)
         return AWPM_ERR_INVALID_ARG;
@@ -1173,6 +1174,7 @@ int awpm_improve_ctx(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int3
                      const double *weight, const int32_t *mate_in, int32_t *mate_out,
                      awpm_stats *stats)
 {
+    NvtxRange nvtx_range("awpm_improve");
     if (!ctx)
         return AWPM_ERR_INVALID_ARG;
     Request r;
@@ -1251,6 +1253,7 @@ int awpm_improve_batch(awpm_ctx *ctx, int32_t count, const int32_t *n_off, const
                        const int32_t *rowidx, const double *weight, const int32_t *mate_in,
                        int32_t *mate_out, awpm_stats *per_matrix, awpm_stats *total)
 {
+    NvtxRange nvtx_range("awpm_improve_batch");
     if (!ctx || count < 0 || (count > 0 && !n_off))
         return AWPM_ERR_INVALID_ARG;
     if (count == 0) {
@@ -1290,6 +1293,7 @@ int awpm_improve_batch(awpm_ctx *ctx, int32_t count, const int32_t *n_off, const
 int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
                 const double *weight, int32_t *mate_out, awpm_greedy_stats *stats)
 {
+    NvtxRange nvtx_range("awpm_greedy");
     if (!ctx || n < 0 || (n > 0 && (!colptr || !mate_out)))
         return AWPM_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1411,6 +1415,7 @@ int awpm_greedy(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
 int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
              const double *weight, int32_t *mate, awpm_mcm_stats *stats)
 {
+    NvtxRange nvtx_range("awpm_mcm");
     if (!ctx || n < 0 || (n > 0 && (!colptr || !mate)))
         return AWPM_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1445,10 +1450,8 @@ int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *row
     AWPM_TRY(ensure(c, c->mr, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->mroot, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->mrpar, sizeof(int32_t) * n));
-    AWPM_TRY(ensure(c, c->mrcol, sizeof(int32_t) * n));
-    AWPM_TRY(ensure(c, c->mtrow, sizeof(int32_t) * n));
-    AWPM_TRY(ensure(c, c->mrkey, sizeof(long long) * n));
-    AWPM_TRY(ensure(c, c->mtkey, sizeof(long long) * n));
+    AWPM_TRY(ensure(c, c->mroff, sizeof(Off) * n));
+    AWPM_TRY(ensure(c, c->mtend, sizeof(Off) * n));
     AWPM_TRY(ensure(c, c->mfront, sizeof(uint32_t) * words));
     AWPM_TRY(ensure(c, c->mcolof, sizeof(int32_t) * ((size_t)nnz + 1)));
     AWPM_TRY(ensure(c, c->mnext, sizeof(uint32_t) * words));
@@ -1484,10 +1487,8 @@ int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *row
     wk.mrpar = (int32_t *)c->mrpar.p;
     wk.mfront = (uint32_t *)c->mfront.p;
     wk.mnext = (uint32_t *)c->mnext.p;
-    wk.mrkey = (long long *)c->mrkey.p;
-    wk.mrcol = (int32_t *)c->mrcol.p;
-    wk.mtkey = (long long *)c->mtkey.p;
-    wk.mtrow = (int32_t *)c->mtrow.p;
+    wk.mroff = (Off *)c->mroff.p;
+    wk.mtend = (Off *)c->mtend.p;
     wk.mmate = dmate;
     wk.mcolof = (int32_t *)c->mcolof.p;
     wk.mtiles = (int32_t *)c->mtiles.p;
@@ -1579,6 +1580,7 @@ int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *row
 int awpm_weights(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *rowidx,
                  const double *values, int32_t mode, double *weight_out)
 {
+    NvtxRange nvtx_range("awpm_weights");
     if (!ctx || n < 0 || (n > 0 && !colptr) ||
         (mode != AWPM_WEIGHTS_SUM && mode != AWPM_WEIGHTS_PRODUCT))
         return AWPM_ERR_INVALID_ARG;
@@ -1644,6 +1646,7 @@ int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
                 const double *weight, const int32_t *mate, double *stepc_gain, int32_t *stepc_row,
                 awpm_stats *stats)
 {
+    NvtxRange nvtx_range("awpm_search");
     if (!ctx)
         return AWPM_ERR_INVALID_ARG;
     Request r;

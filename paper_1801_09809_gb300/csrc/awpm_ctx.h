@@ -10,10 +10,23 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "awpm.h"
 #include "awpm_internal.h"
 
 namespace awpm {
+
+// NVTX range of a host-side step (an entry point, the enqueue of a solve,
+// the wait for it, a pass of the host-driven loop): profilers show where the
+// host time goes; without a profiler attached a push/pop costs a few
+// nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct DevBuf {
     void *p = nullptr;
@@ -96,13 +109,13 @@ struct awpm_ctx {
     int search_bps[2][3][2] = {};  // [batch][lookup slot][wide]
     bool search_wide = true;      // default when the lookup is given explicitly
     // per-solve device workspace
-    awpm::DevBuf mc, mr, wm, rr, wmr, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
+    awpm::DevBuf mc, mr, wm, rr, rsig, colsig, best, dsel, tile_col, starts, ctl, wpart, htab;
     awpm::DevBuf winbits, wkey, bloom;
     awpm::DevBuf gckey, gcpos, grkey, grcol, gtdead;  // greedy matching records
     awpm::DevBuf gmate;                       // greedy start of awpm_improve_ctx
     awpm::DevBuf psel, pslive, pstaken, psused;  // greedy (Pettie-Sanders) selection
     awpm::DevBuf wt_cmax, wt_rmax, wt_stage;     // weights from matrix values
-    awpm::DevBuf mroot, mrpar, mfront, mnext, mrkey, mrcol, mtkey, mtrow, mstage,
+    awpm::DevBuf mroot, mrpar, mfront, mnext, mroff, mtend, mstage,
         mcolof, mtiles;  // maximum matching
     awpm::DevBuf rowsig, trowptr, rs_k0, rs_k1, rs_v0, rs_v1, rs_hist, rs_sums;  // row marking
     awpm::DevBuf b_noff, b_colmat, b_tilemat, b_tlist, b_i32, b_u64, b_f64;

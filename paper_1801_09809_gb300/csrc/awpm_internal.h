@@ -52,15 +52,28 @@ struct alignas(16) Rec {
     int32_t q;
 };
 
-// Per-row view of the column matched to row i (m_i): where its rows sit in
-// the CSC arrays and a 64-bit signature of those rows (the bits sig_mask(r)
-// set for every stored row r).  A clear bit proves that the closing entry
-// (m_j, m_i) is absent without touching the column; the record is rewritten
-// whenever row i changes mate.
-struct alignas(16) RowRec {
+// Per-row view of the column matched to row i (m_i), in two arrays:
+//   rsig[i]   a 64-bit signature of column m_i's rows (the bits sig_mask(r)
+//             set for every stored row r): a clear bit proves that the
+//             closing entry (m_j, m_i) is absent without touching the column;
+//             every candidate gathers these 8 bytes;
+//   rrange[i] where column m_i's rows sit in the CSC arrays and the matched
+//             weight w(i, m_i): read only for the candidates that pass.
+// Both are rewritten whenever row i changes mate.
+struct alignas(16) RowRange {
     int32_t s;
     int32_t e;
-    unsigned long long sig;
+    double w;
+};
+
+// Maximum matching: the best offer a row received at this level (order key
+// of the edge weight, then the lowest column), or a tree's end (order key of
+// its last edge, then the lowest row); one 128-bit compare-and-swap updates
+// both fields together.
+struct alignas(16) Off {
+    long long key;
+    int32_t who;
+    int32_t pad;
 };
 
 // Step-D selection at a key column k (Algorithm 6): best gain and its root j.
@@ -135,10 +148,8 @@ struct Work {
     int32_t *mc;        // row matched to column j
     int32_t *mr;        // column matched to row i
     double *wm;         // w(mc[j], j)
-    RowRec *rr;         // the row-record buffer (16 B per row), split into:
     unsigned long long *rsig;  // per row i: signature of the rows of column mr[i]
-    int2 *rrange;              // per row i: that column's range {colptr[m_i], colptr[m_i+1]}
-    double *wmr;        // per row i: wm[mr[i]] = w(i, mr[i])
+    RowRange *rrange;          // per row i: that column's range and w(i, mr[i])
     unsigned long long *colsig;  // per column: signature of its rows
     unsigned long long *htab;    // per-column hash tables (2 slots per nonzero), or null
     uint32_t *bloom;    // blocked Bloom filters of the long columns (a word per 4 nonzeros), or null
@@ -180,10 +191,8 @@ struct Work {
     int32_t *mrpar;
     uint32_t *mfront;
     uint32_t *mnext;
-    long long *mrkey;
-    int32_t *mrcol;
-    long long *mtkey;
-    int32_t *mtrow;
+    Off *mroff;         // per row: the level's best offer (key, column)
+    Off *mtend;         // per tree (root column): its end (key of the last edge, row)
     int32_t *mmate;
     int32_t *mcolof;    // column of every entry
     int32_t *mtiles;    // tiles holding a frontier column, this level

@@ -58,6 +58,23 @@ __device__ __forceinline__ void raise_err(Ctl *ctl, unsigned bits)
     atomicOr(&ctl->err, bits);
 }
 
+// Index checks of builds with AWPM_DEBUG_BOUNDS: an index derived from data
+// (a row, a mate, a position) outside [0, lim) sets kErrBounds (reported as
+// AWPM_ERR_INTERNAL) and the access is skipped; nothing traps.  Other builds
+// compile the checks away.
+#ifdef AWPM_DEBUG_BOUNDS
+__device__ __noinline__ bool in_bounds(Ctl *ctl, long long i, long long lim)
+{
+    if (i >= 0 && i < lim)
+        return true;
+    atomicOr(&ctl->err, kErrBounds);
+    return false;
+}
+#define AWPM_IN(ctl, i, lim) in_bounds((ctl), (long long)(i), (long long)(lim))
+#else
+#define AWPM_IN(ctl, i, lim) true
+#endif
+
 __device__ __forceinline__ bool gate(const Ctl *ctl)
 {
     return *(volatile const unsigned *)&ctl->err == 0u &&
@@ -274,13 +291,28 @@ __device__ __forceinline__ unsigned long long policy_evict_last()
     return pol;
 }
 
-// Row record of `row` (the column matched to it: range and signature), kept as
-// two arrays so that the signature test gathers 8 bytes per candidate.
+// Row record of `row`: the signature, range and matched weight of the column
+// matched to it (two arrays, so that the signature test gathers 8 bytes per
+// candidate).
 __device__ __forceinline__ void put_rowrec(const Work &w, int32_t row, int32_t s, int32_t e,
-                                           unsigned long long sig)
+                                           unsigned long long sig, double wmatch)
 {
     w.rsig[row] = sig;
-    w.rrange[row] = make_int2(s, e);
+    RowRange g;
+    g.s = s;
+    g.e = e;
+    g.w = wmatch;
+    w.rrange[row] = g;
+}
+
+__device__ __forceinline__ RowRange ld_range(const RowRange *p)
+{
+    const int4 v = __ldg(reinterpret_cast<const int4 *>(p));
+    RowRange g;
+    g.s = v.x;
+    g.e = v.y;
+    g.w = __hiloint2double(v.w, v.z);
+    return g;
 }
 
 __device__ __forceinline__ unsigned long long ld_u64_last(const unsigned long long *ptr,
@@ -524,12 +556,18 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
         raise_err(w.ctl, bits);
 }
 
-// mc = mate_in, mr = its inverse, and the row record and matched weight of
-// every row; checks that mate_in is a permutation over stored entries (the
-// entry pass left wm[j] = NaN where (mate_in[j], j) is not stored).  Each
-// thread takes eight columns per round and issues their loads together: the
-// scattered writes by row and the inverse's compare-and-swap are latency
-// bound, so the rounds overlap eight of them.
+// Initialisation of the matching in two passes, so that no record is
+// written to a scattered address:
+//   k_init_mates (per column j): mc[j] = mate_in[j], and mr[mate_in[j]] = j
+//     (a 4-byte scattered store per column; mr stays in L2 while it fills);
+//     checks that every mate_in[j] is a row number and a stored entry of
+//     column j (the entry pass left wm[j] = NaN where (mate_in[j], j) is not
+//     stored);
+//   k_init_rows (per row r): the row record of r from column mr[r] (gathers
+//     of that column's range, signature and matched weight; the records are
+//     written row by row, whole sectors at a time), and the check that every
+//     row got a column: with n columns and n rows that holds exactly when
+//     mate_in is a permutation.
 __global__ void k_init_mates(const Work *__restrict__ W)
 {
     const Work &w = *W;
@@ -538,44 +576,72 @@ __global__ void k_init_mates(const Work *__restrict__ W)
     constexpr int kU = 8;
     const int64_t stride = gstride();
     const int32_t n = w.n;
+    unsigned bits = 0;
     for (int64_t j0 = gtid(); j0 < n; j0 += kU * stride) {
-        int32_t r[kU], s[kU], e[kU], old[kU];
+        int32_t r[kU];
         double x[kU];
-        unsigned long long sig[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int64_t j = j0 + u * stride;
             const bool ok = j < n;
-            r[u] = ok ? w.mate_in[j] : 0;
+            r[u] = ok ? w.mate_in[j] : -1;
             x[u] = ok ? w.wm[j] : 0.0;
-            s[u] = ok ? w.colptr[j] : 0;
-            e[u] = ok ? w.colptr[j + 1] : 0;
-            sig[u] = ok ? w.colsig[j] : 0ull;
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int64_t j = j0 + u * stride;
-            old[u] = -1;
             if (j >= n)
                 continue;
             w.mc[j] = r[u];
-            if (r[u] < 0 || r[u] >= n) {
-                raise_err(w.ctl, kErrNotPerfect);
+            if (r[u] < 0 || r[u] >= n || gbits(x[u]) == (long long)kNaNBits) {
+                bits |= kErrNotPerfect;
                 continue;
             }
-            old[u] = atomicCAS(&w.mr[r[u]], -1, (int32_t)j);
-            if (gbits(x[u]) == (long long)kNaNBits) {
-                raise_err(w.ctl, kErrNotPerfect);
-                continue;
-            }
-            put_rowrec(w, r[u], s[u], e[u], sig[u]);
-            w.wmr[r[u]] = x[u];
+            w.mr[r[u]] = (int32_t)j;
+        }
+    }
+    bits = __reduce_or_sync(FULL_MASK, bits);
+    if ((threadIdx.x & 31) == 0 && bits)
+        raise_err(w.ctl, bits);
+}
+
+__global__ void k_init_rows(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    if (w.ctl->err)
+        return;
+    constexpr int kU = 4;
+    const int64_t stride = gstride();
+    const int32_t n = w.n;
+    bool bad = false;
+    for (int64_t r0 = gtid(); r0 < n; r0 += kU * stride) {
+        int32_t j[kU], cs[kU], ce[kU];
+        unsigned long long sig[kU];
+        double x[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t r = r0 + u * stride;
+            j[u] = r < n ? w.mr[r] : 0;
         }
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
-            if (old[u] != -1)
-                raise_err(w.ctl, kErrNotPerfect);
+        for (int u = 0; u < kU; ++u) {
+            const int64_t r = r0 + u * stride;
+            const bool ok = r < n && j[u] >= 0;
+            bad |= r < n && j[u] < 0;
+            cs[u] = ok ? __ldg(w.colptr + j[u]) : 0;
+            ce[u] = ok ? __ldg(w.colptr + j[u] + 1) : 0;
+            sig[u] = ok ? __ldg(w.colsig + j[u]) : 0ull;
+            x[u] = ok ? __ldg(w.wm + j[u]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t r = r0 + u * stride;
+            if (r < n)
+                put_rowrec(w, (int32_t)r, cs[u], ce[u], sig[u], x[u]);
+        }
     }
+    if (__any_sync(FULL_MASK, bad) && (threadIdx.x & 31) == 0)
+        raise_err(w.ctl, kErrNotPerfect);
 }
 
 // Per-column hash tables (only for AWPM_LOOKUP_HASH).
@@ -1095,8 +1161,6 @@ struct LookupQueue {
     int32_t p[kQueue];    // position of (i, j)
     int32_t i[kQueue];    // row i
     int32_t mj[kQueue];   // m_j, the row looked up in column m_i
-    int32_t lo[kQueue];   // column m_i's rows: rowidx[lo, lo + len)
-    int32_t len[kQueue];
 };
 
 // Resolve the queued requests head .. head + k - 1 (k <= 32, lane x takes
@@ -1112,27 +1176,27 @@ struct LookupQueue {
 template <int kLookup>
 __device__ __forceinline__ void resolve_lookups(
     const LookupQueue &qu, int head, int k, int lane, const int32_t *__restrict__ rowidx,
-    const double *__restrict__ wv, const double *__restrict__ wm, const double *__restrict__ wmr,
+    const double *__restrict__ wv, const double *__restrict__ wm,
     const unsigned long long *__restrict__ htab, const uint32_t *__restrict__ bloom,
     const int32_t *__restrict__ trowptr, const int32_t *__restrict__ tpos,
-    const int2 *__restrict__ rrange, int32_t nnz, Rec *__restrict__ best, uint32_t *winbits,
+    const RowRange *__restrict__ rrange, int32_t nnz, int32_t nrows, Rec *__restrict__ best,
+    uint32_t *winbits,
     Ctl *ctl, uint32_t &n_found, uint32_t &n_pos)
 {
     const int x = (head + lane) & (kQueue - 1);
     const bool act = lane < k;
     const int32_t mj = act ? qu.mj[x] : 0;
-    // column m_i's rows rowidx[lo, lo + len): queued with row marking (the
-    // filter needed them), else read here from the row record of i
+    // column m_i's rows rowidx[lo, lo + len) and w(i, m_i), from the row
+    // record of i
     int32_t lo = 0, len = 0;
-    if (act) {
-        if (kLookup == AWPM_LOOKUP_ROWMARK) {
-            lo = qu.lo[x];
-            len = qu.len[x];
-        } else {
-            const int2 rg = __ldg(rrange + qu.i[x]);
-            lo = rg.x;
-            len = rg.y - rg.x;
-        }
+    double wmi = 0.0;
+    if (act && AWPM_IN(ctl, qu.i[x], nrows)) {
+        const RowRange rg = ld_range(rrange + qu.i[x]);
+        lo = rg.s;
+        len = rg.e - rg.s;
+        wmi = rg.w;
+        if (!(AWPM_IN(ctl, lo, (long long)nnz + 1) && AWPM_IN(ctl, len, (long long)nnz - lo + 1)))
+            lo = len = 0;
     }
     int32_t q = -1;
     if (kLookup == AWPM_LOOKUP_HASH) {
@@ -1230,6 +1294,9 @@ __device__ __forceinline__ void resolve_lookups(
             }
         }
     }
+    if (q >= 0 && !(AWPM_IN(ctl, q, nnz) && AWPM_IN(ctl, qu.p[x], nnz) &&
+                    AWPM_IN(ctl, qu.j[x], nrows)))
+        q = -1;
     if (q >= 0) {
         ++n_found;
         const int32_t j = qu.j[x];
@@ -1237,7 +1304,6 @@ __device__ __forceinline__ void resolve_lookups(
         const int32_t i = qu.i[x];
         const double wij = __ldg(wv + p);
         const double wq = __ldg(wv + q);
-        const double wmi = __ldg(wmr + i);
         const double gg = ((wij + wq) - wmi) - __ldg(wm + j);
         if (gain_positive(gg)) {
             ++n_pos;
@@ -1282,8 +1348,7 @@ __global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
     const int32_t *__restrict__ mc = W->mc;
     const double *__restrict__ wm = W->wm;
     const unsigned long long *__restrict__ rsig = W->rsig;
-    const int2 *__restrict__ rrange = W->rrange;
-    const double *__restrict__ wmr = W->wmr;
+    const RowRange *__restrict__ rrange = W->rrange;
     const unsigned long long *__restrict__ htab = W->htab;
     const uint32_t *__restrict__ bloom = W->bloom;
     const unsigned long long *__restrict__ rowsig = W->rowsig;
@@ -1307,8 +1372,8 @@ __global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
 
     auto flush = [&](int k) {
         __syncwarp();
-        resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, wmr, htab, bloom, trowptr,
-                                 tpos, rrange, nnz, best, winbits, ctl, n_found, n_pos);
+        resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, htab, bloom, trowptr,
+                                 tpos, rrange, nnz, W->n, best, winbits, ctl, n_found, n_pos);
         __syncwarp();
         qhead = (qhead + k) & (kQueue - 1);
         qn -= k;
@@ -1397,10 +1462,14 @@ __global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
             for (int u = 0; u < kU; ++u) {
                 iv[u] = valid[u] ? iv[u] : 0;
                 jv[u] = valid[u] ? lane_column(c0[u], mask[u], lane) : -1 - lane;
+                if (valid[u] && !(AWPM_IN(ctl, jv[u], W->n) && AWPM_IN(ctl, iv[u], W->n))) {
+                    valid[u] = false;
+                    jv[u] = -1 - lane;
+                }
                 mjv[u] = valid[u] ? ld_i32_last(mc + jv[u], pol) : 0x7fffffff;
             }
             unsigned long long sig[kU], mark[kU];
-            int2 rg[kU];
+            int32_t cs[kU];  // row marking: first position of column m_i
             bool cand[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
@@ -1409,12 +1478,12 @@ __global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
                 cand[u] = valid[u] && iv[u] > mjv[u];
                 sig[u] = 0ull;
                 mark[u] = 0ull;
-                rg[u] = make_int2(0, 0);
+                cs[u] = 0;
                 if (cand[u]) {
                     ++n_cand;
                     sig[u] = ld_u64_last(rsig + iv[u], pol);
                     if (kLookup == AWPM_LOOKUP_ROWMARK) {
-                        rg[u] = __ldg(rrange + iv[u]);
+                        cs[u] = __ldg(&rrange[iv[u]].s);
                         mark[u] = __ldg(rowsig + mjv[u]);  // the mark of row m_j
                     }
                 }
@@ -1424,7 +1493,7 @@ __global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
                 // row m_j in column m_i's signature; with row marking also
                 // column m_i (first position rg.x) marked by row m_j
                 const bool pass = cand[u] && sig_has(sig[u], mjv[u]) &&
-                                  (kLookup != AWPM_LOOKUP_ROWMARK || sig_has(mark[u], rg[u].x));
+                                  (kLookup != AWPM_LOOKUP_ROWMARK || sig_has(mark[u], cs[u]));
                 const unsigned need = __ballot_sync(FULL_MASK, pass);
                 if (pass) {
                     const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
@@ -1432,10 +1501,6 @@ __global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
                     qu.p[x] = pv[u];
                     qu.i[x] = iv[u];
                     qu.mj[x] = mjv[u];
-                    if (kLookup == AWPM_LOOKUP_ROWMARK) {
-                        qu.lo[x] = rg[u].x;
-                        qu.len[x] = rg[u].y - rg[u].x;
-                    }
                 }
                 qn += __popc(need);
                 if (qn >= 32)
@@ -1502,8 +1567,7 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
     const int32_t *__restrict__ mc = W->mc;
     const double *__restrict__ wm = W->wm;
     const unsigned long long *__restrict__ rsig = W->rsig;
-    const int2 *__restrict__ rrange = W->rrange;
-    const double *__restrict__ wmr = W->wmr;
+    const RowRange *__restrict__ rrange = W->rrange;
     const unsigned long long *__restrict__ htab = W->htab;
     const uint32_t *__restrict__ bloom = W->bloom;
     const unsigned long long *__restrict__ rowsig = W->rowsig;
@@ -1524,8 +1588,8 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
 
     auto flush = [&](int k) {
         __syncwarp();
-        resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, wmr, htab, bloom, trowptr,
-                                 tpos, rrange, nnz, best, winbits, ctl, n_found, n_pos);
+        resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, htab, bloom, trowptr,
+                                 tpos, rrange, nnz, W->n, best, winbits, ctl, n_found, n_pos);
         __syncwarp();
         qhead = (qhead + k) & (kQueue - 1);
         qn -= k;
@@ -1540,7 +1604,7 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
     // stage R: the row records in flight (and, with row marking, the mark of m_j)
     int32_t rj[kU], ri[kU], rm[kU];
     unsigned long long rsg[kU], rmark[kU];
-    int2 rrg[kU];
+    int32_t rcs[kU];  // row marking: first position of column m_i
     bool rcand[kU];
 
     auto load_p = [&](int32_t tr) {
@@ -1565,7 +1629,9 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
             const bool valid = tu < ntiles && tu * kTile + lane < nnz;
             mi_[u] = valid ? pi[u] : 0;
             mj_[u] = valid ? lane_column(pc0[u], pmask[u], lane) : -1;
-            mm_[u] = valid ? ld_i32_last(mc + mj_[u], pol) : 0x7fffffff;
+            const bool ok = valid && AWPM_IN(ctl, mj_[u], W->n) && AWPM_IN(ctl, mi_[u], W->n);
+            mj_[u] = ok ? mj_[u] : -1;
+            mm_[u] = ok ? ld_i32_last(mc + mj_[u], pol) : 0x7fffffff;
         }
     };
 
@@ -1577,7 +1643,7 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
         rcand[u] = false;
         rj[u] = ri[u] = rm[u] = 0;
         rsg[u] = 0ull;
-        rrg[u] = make_int2(0, 0);
+        rcs[u] = 0;
         rmark[u] = 0ull;
     }
     for (int32_t tr = t0;; tr += stride) {
@@ -1586,7 +1652,7 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const bool pass = rcand[u] && sig_has(rsg[u], rm[u]) &&
-                              (kLookup != AWPM_LOOKUP_ROWMARK || sig_has(rmark[u], rrg[u].x));
+                              (kLookup != AWPM_LOOKUP_ROWMARK || sig_has(rmark[u], rcs[u]));
             const unsigned need = __ballot_sync(FULL_MASK, pass);
             if (pass) {
                 const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
@@ -1594,10 +1660,6 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
                 qu.p[x] = (tprev + u * nwarps) * kTile + lane;
                 qu.i[x] = ri[u];
                 qu.mj[x] = rm[u];
-                if (kLookup == AWPM_LOOKUP_ROWMARK) {
-                    qu.lo[x] = rrg[u].x;
-                    qu.len[x] = rrg[u].y - rrg[u].x;
-                }
             }
             qn += __popc(need);
             if (qn >= 32)
@@ -1612,11 +1674,13 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
             ri[u] = mi_[u];
             rm[u] = mm_[u];
             rcand[u] = mj_[u] >= 0 && mi_[u] > mm_[u];
+            if (rcand[u] && !AWPM_IN(ctl, mm_[u], W->n))
+                rcand[u] = false;
             if (rcand[u]) {
                 ++n_cand;
                 rsg[u] = ld_u64_last(rsig + mi_[u], pol);
                 if (kLookup == AWPM_LOOKUP_ROWMARK) {
-                    rrg[u] = __ldg(rrange + mi_[u]);
+                    rcs[u] = __ldg(&rrange[mi_[u]].s);
                     rmark[u] = __ldg(rowsig + mm_[u]);
                 }
             }
@@ -1661,9 +1725,17 @@ __global__ void k_select(const Work *__restrict__ W)
             if (!((bits >> lane) & 1u))
                 continue;
             const int32_t j = (int32_t)((x0 + src) * 32 + lane);
+            if (!AWPM_IN(w.ctl, j, w.n))
+                continue;
             const Rec r = w.best[j];
+            if (!AWPM_IN(w.ctl, r.p, w.nnz))
+                continue;
             const int32_t i = __ldg(w.rowidx + r.p);
+            if (!AWPM_IN(w.ctl, i, w.n))
+                continue;
             const int32_t k = w.mr[i];
+            if (!AWPM_IN(w.ctl, k, w.n))
+                continue;
             if ((w.winbits[k >> 5] >> (k & 31)) & 1u) {
                 w.wkey[j] = -1;
                 continue;
@@ -1705,14 +1777,21 @@ __global__ void k_flip(const Work *__restrict__ W)
                 int32_t mat = -1;  // matrix of a flipped cycle (batched solve)
                 if ((bits >> lane) & 1u) {
                     const int32_t j = (int32_t)((x0 + src) * 32 + lane);
-                    const Rec r = w.best[j];
-                    w.best[j] = Rec{0.0, 0, 0};
-                    const int32_t k = w.wkey[j];
+                    const Rec r = AWPM_IN(w.ctl, j, w.n) ? w.best[j] : Rec{0.0, 0, 0};
+                    if (AWPM_IN(w.ctl, j, w.n))
+                        w.best[j] = Rec{0.0, 0, 0};
+                    int32_t k = AWPM_IN(w.ctl, j, w.n) ? w.wkey[j] : -1;
+                    if (k >= 0 && !(AWPM_IN(w.ctl, k, w.n) && AWPM_IN(w.ctl, r.p, w.nnz) &&
+                                    AWPM_IN(w.ctl, r.q, w.nnz)))
+                        k = -1;
                     const Sel sl = k >= 0 ? w.dsel[k] : Sel{0.0, 0, 0};
                     if (k >= 0 && gbits(sl.g) > 0ll && sl.j == j) {
                         w.dsel[k] = Sel{0.0, 0, 0};
-                        const int32_t i = w.rowidx[r.p];
-                        const int32_t mj = w.mc[j];
+                    }
+                    const int32_t i = k >= 0 && gbits(sl.g) > 0ll && sl.j == j ? w.rowidx[r.p] : -1;
+                    const int32_t mj = i >= 0 ? w.mc[j] : -1;
+                    // every lane reaches the warp-wide match below: no early exit
+                    if (i >= 0 && AWPM_IN(w.ctl, i, w.n) && AWPM_IN(w.ctl, mj, w.n)) {
                         const double wij = w.w[r.p];
                         const double wq = w.w[r.q];
                         w.mc[j] = i;
@@ -1721,10 +1800,8 @@ __global__ void k_flip(const Work *__restrict__ W)
                         w.mr[mj] = k;
                         w.wm[j] = wij;
                         w.wm[k] = wq;
-                        put_rowrec(w, i, w.colptr[j], w.colptr[j + 1], w.colsig[j]);
-                        w.wmr[i] = wij;
-                        put_rowrec(w, mj, w.colptr[k], w.colptr[k + 1], w.colsig[k]);
-                        w.wmr[mj] = wq;
+                        put_rowrec(w, i, w.colptr[j], w.colptr[j + 1], w.colsig[j], wij);
+                        put_rowrec(w, mj, w.colptr[k], w.colptr[k + 1], w.colsig[k], wq);
                         ++flips;
                         if (w.bw.count > 0)
                             mat = w.bw.colmat[k];
@@ -2340,8 +2417,7 @@ __global__ void k_wt_out(const Work *__restrict__ W)
 // Phases of breadth-first augmenting-path searches from every free column.
 // Per level, every frontier column offers its rows not reached yet (through
 // unmatched edges); a row goes to the offer with the heaviest edge, then the
-// lowest column (order keys, 64-bit atomics: maximum key, then minimum
-// column).  A free row so reached ends a path of its tree (the tree keeps
+// lowest column (order key and column in one 128-bit record).  A free row so reached ends a path of its tree (the tree keeps
 // the heaviest last edge, then the lowest row, and stops growing); a
 // matched row brings its matched column into the next frontier.  The trees
 // are vertex-disjoint, so all paths found in a phase are augmented at once.
@@ -2473,10 +2549,8 @@ __global__ void k_mc_phase(const Work *__restrict__ W)
     if (!w.ctl->err) {
         for (int64_t x = gtid(); x < w.n; x += gstride()) {
             w.mrpar[x] = -1;
-            w.mrkey[x] = kKeyNone;
-            w.mrcol[x] = 0x7fffffff;
-            w.mtkey[x] = kKeyNone;
-            w.mtrow[x] = 0x7fffffff;
+            w.mroff[x] = Off{kKeyNone, 0x7fffffff, 0};
+            w.mtend[x] = Off{kKeyNone, 0x7fffffff, 0};
             if (w.mc[x] < 0)
                 w.mroot[x] = (int32_t)x;
         }
@@ -2531,8 +2605,33 @@ __global__ void k_mc_phase(const Work *__restrict__ W)
         const int32_t r = w.rowidx[p];
 #define MC_TILE_LOOP_END }
 
-// Level, step 1: the heaviest offer per unreached row.
-__global__ void k_mc_offer_max(const Work *__restrict__ W)
+// (key, who) beats the record cur: heavier key, then lower index.
+__device__ __forceinline__ bool off_better(long long key, int32_t who, const Off &cur)
+{
+    return key > cur.key || (key == cur.key && who < cur.who);
+}
+
+// Fold (key, who) into the record at addr (128-bit compare-and-swap; a
+// failed exchange means another thread stored a better record, so the loop
+// is short; its bound only turns a broken invariant into an error bit).
+__device__ void off_combine(Off *addr, long long key, int32_t who, Ctl *ctl)
+{
+    Off cur = *addr;
+    Off mine{key, who, 0};
+    for (int k = 0; k < kCasRetryCap; ++k) {
+        if (!off_better(key, who, cur))
+            return;
+        const Off old = atomicCAS(addr, cur, mine);
+        if (old.key == cur.key && old.who == cur.who && old.pad == cur.pad)
+            return;
+        cur = old;
+    }
+    raise_err(ctl, kErrTimeout);
+}
+
+// Level, step 1: per unreached row the best offer of the level: the
+// heaviest edge from a frontier column, then the lowest column.
+__global__ void k_mc_offer(const Work *__restrict__ W)
 {
     const Work &w = *W;
     if (w.ctl->err)
@@ -2543,14 +2642,14 @@ __global__ void k_mc_offer_max(const Work *__restrict__ W)
     MC_TILE_LOOP_BEGIN(w.ctl->level_tiles)
     if (r == w.mc[c] || w.mrpar[r] != -1)
         continue;
-    const long long key = order_key(w.w[p]);
-    if (key > *(volatile const long long *)(w.mrkey + r))
-        atomicMax(w.mrkey + r, key);
+    off_combine(w.mroff + r, order_key(w.w[p]), c, w.ctl);
     MC_TILE_LOOP_END
 }
 
-// Level, step 2: the lowest column among the heaviest offers.
-__global__ void k_mc_offer_min(const Work *__restrict__ W)
+// Level, step 2: rows join the winning column's tree.  A free row is a
+// candidate end of the tree: the tree keeps the heaviest last edge, then the
+// lowest row.  A matched row brings its column into the next frontier.
+__global__ void k_mc_join(const Work *__restrict__ W)
 {
     const Work &w = *W;
     if (w.ctl->err)
@@ -2559,53 +2658,17 @@ __global__ void k_mc_offer_min(const Work *__restrict__ W)
     if (gtid() == 0)
         w.ctl->level_tiles = 0;
     MC_TILE_LOOP_BEGIN(w.ctl->level_listed)
-    if (r == w.mc[c] || w.mrpar[r] != -1)
-        continue;
-    if (order_key(w.w[p]) == w.mrkey[r] && c < *(volatile const int32_t *)(w.mrcol + r))
-        atomicMin(w.mrcol + r, c);
-    MC_TILE_LOOP_END
-}
-
-// Level, step 3: rows join the winning column's tree; a free row is a
-// candidate end of the tree (heaviest last edge), a matched row brings its
-// column into the next frontier.
-__global__ void k_mc_join(const Work *__restrict__ W)
-{
-    const Work &w = *W;
-    if (w.ctl->err)
-        return;
-    MC_TILE_LOOP_BEGIN(w.ctl->level_listed)
-    if (r == w.mc[c] || w.mrcol[r] != c || w.mrpar[r] != -1)
+    if (r == w.mc[c] || w.mroff[r].who != c || w.mrpar[r] != -1)
         continue;
     w.mrpar[r] = c;
-    const long long key = order_key(w.w[p]);
-    w.mrkey[r] = kKeyNone;
-    w.mrcol[r] = 0x7fffffff;
     const int32_t t_root = w.mroot[c];
     const int32_t c2 = w.mr[r];
     if (c2 < 0) {
-        if (key > *(volatile const long long *)(w.mtkey + t_root))
-            atomicMax(w.mtkey + t_root, key);
+        off_combine(w.mtend + t_root, order_key(w.w[p]), r, w.ctl);
     } else {
         w.mroot[c2] = t_root;
         atomicOr(w.mnext + (c2 >> 5), 1u << (c2 & 31));
     }
-    MC_TILE_LOOP_END
-}
-
-// Level, step 4: among a tree's free rows with the heaviest last edge, the
-// lowest row is its end.
-__global__ void k_mc_end(const Work *__restrict__ W)
-{
-    const Work &w = *W;
-    if (w.ctl->err)
-        return;
-    MC_TILE_LOOP_BEGIN(w.ctl->level_listed)
-    if (w.mrpar[r] != c || w.mr[r] >= 0)
-        continue;
-    const int32_t t_root = w.mroot[c];
-    if (order_key(w.w[p]) == w.mtkey[t_root] && r < *(volatile const int32_t *)(w.mtrow + t_root))
-        atomicMin(w.mtrow + t_root, r);
     MC_TILE_LOOP_END
 }
 
@@ -2645,7 +2708,7 @@ __global__ void k_mc_advance(const Work *__restrict__ W)
                     const int b = __ffs(bits) - 1;
                     bits &= bits - 1;
                     const int32_t c = (int32_t)(x * 32 + b);
-                    if (w.mtkey[w.mroot[c]] == kKeyNone)
+                    if (w.mtend[w.mroot[c]].key == kKeyNone)
                         keep |= 1u << b;
                 }
                 w.mfront[x] = keep;
@@ -2693,9 +2756,9 @@ __global__ void k_mc_augment(const Work *__restrict__ W)
     unsigned long long aug = 0;
     if (!w.ctl->err) {
         for (int64_t t = gtid(); t < w.n; t += gstride()) {
-            if (w.mc[t] >= 0 || w.mtrow[t] == 0x7fffffff)
+            if (w.mc[t] >= 0 || w.mtend[t].who == 0x7fffffff)
                 continue;
-            int32_t r = w.mtrow[t];
+            int32_t r = w.mtend[t].who;
             for (int32_t guard = 0; guard <= w.n; ++guard) {
                 const int32_t c = w.mrpar[r];
                 if (c < 0) {  // a broken tree: report instead of walking on
@@ -2782,6 +2845,7 @@ void launch_init(const Work *d, const Shape &sh, Sink &k)
     if (sh.batch)
         k.launch((const void *)k_batch_cols, init_grid(sh), kThreads, a);
     k.launch((const void *)k_init_mates, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_init_rows, init_grid(sh), kThreads, a);
     if (sh.batch) {
         k.launch((const void *)k_batch_check, init_tile_grid(sh), kThreads, a);
         k.launch((const void *)k_batch_list, init_grid(sh), kThreads, a);
@@ -2993,10 +3057,8 @@ void launch_mcm_level(const Work *d, const Shape &sh, Sink &k)
     void *a[] = {(void *)&d};
     // one wave of blocks: a level's work follows its frontier, and a small
     // frontier should not pay for launching idle blocks
-    k.launch((const void *)k_mc_offer_max, tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_mc_offer_min, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_offer, tile_grid(sh), kThreads, a);
     k.launch((const void *)k_mc_join, tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_mc_end, tile_grid(sh), kThreads, a);
     k.launch((const void *)k_mc_advance, util_grid(sh), kThreads, a);
 }
 

@@ -37,8 +37,8 @@ constexpr size_t kOffMc = kOffCtl + up(sizeof(Ctl));
 constexpr size_t kOffMr = kOffMc + up(sizeof(int32_t) * kMaxN);
 constexpr size_t kOffWm = kOffMr + up(sizeof(int32_t) * kMaxN);
 constexpr size_t kOffRr = kOffWm + up(sizeof(double) * kMaxN);
-constexpr size_t kOffWmr = kOffRr + up(sizeof(RowRec) * kMaxN);
-constexpr size_t kOffSig = kOffWmr + up(sizeof(double) * kMaxN);
+constexpr size_t kOffRsig = kOffRr + up(sizeof(RowRange) * kMaxN);
+constexpr size_t kOffSig = kOffRsig + up(sizeof(unsigned long long) * kMaxN);
 constexpr size_t kOffBest = kOffSig + up(sizeof(unsigned long long) * kMaxN);
 constexpr size_t kOffWin = kOffBest + up(sizeof(Rec) * kMaxN);
 constexpr size_t kOffWkey = kOffWin + up(sizeof(uint32_t) * (kMaxN / 32 + 1));
@@ -143,10 +143,8 @@ extern "C" int awpm_search_noalloc(int32_t n, const int32_t *colptr, const int32
     wk.mc = (int32_t *)(base + kOffMc);
     wk.mr = (int32_t *)(base + kOffMr);
     wk.wm = (double *)(base + kOffWm);
-    wk.rr = (RowRec *)(base + kOffRr);
-    wk.rsig = (unsigned long long *)(base + kOffRr);
-    wk.rrange = (int2 *)(wk.rsig + n);
-    wk.wmr = (double *)(base + kOffWmr);
+    wk.rrange = (RowRange *)(base + kOffRr);
+    wk.rsig = (unsigned long long *)(base + kOffRsig);
     wk.colsig = (unsigned long long *)(base + kOffSig);
     wk.best = (Rec *)(base + kOffBest);
     // the search never selects (Step D): its selection records share the

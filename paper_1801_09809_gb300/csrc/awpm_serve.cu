@@ -105,6 +105,7 @@ void finish_item(awpm_server_impl *s, Item *it, int rc)
 // (0 = no limit).
 void start(awpm_server_impl *s, std::unique_lock<std::mutex> &lk, int k, Item *it, size_t cap)
 {
+    NvtxRange nvtx_range("admit");
     it->state = 1;
     s->running[k] = it;
     awpm_ctx *c = s->slots[k];
@@ -402,6 +403,7 @@ void awpm_server_memory(awpm_ctx *ctx, size_t *held, size_t *peak)
 
 int awpm_submit(awpm_ctx *ctx, const awpm_problem *p, uint64_t *ticket)
 {
+    NvtxRange nvtx_range("awpm_submit");
     if (!ctx || !p || !ticket || p->n < 0)
         return AWPM_ERR_INVALID_ARG;
     int rc;
