@@ -420,8 +420,7 @@ int build_mcm_graph(awpm_ctx *c, const Shape &sh, cudaGraphExec_t *out)
         goto done;
     }
     sl.graph = cp2.conditional.phGraph_out[0];
-    launch_mcm_level(d, sh, sl);
-    launch_mcm_cond_level(d, sh, h2, sl);
+    launch_mcm_level_graph(d, sh, h2, sl);
     sb.last = n_inner;
     launch_mcm_augment(d, sh, sb);
     launch_mcm_cond_phase(d, sh, h1, sb);

@@ -95,6 +95,8 @@ struct Ctl {
     int32_t phase_levels;        // maximum matching: levels of the running phase
     int32_t level_tiles;         // maximum matching: tiles listed for the next level
     int32_t level_listed;        // maximum matching: tiles listed for this level
+    uint32_t level_done;         // maximum matching: blocks done with the level's last step
+    uint32_t pad_ld;
     unsigned long long levels;   // maximum matching: search levels run
     unsigned long long pass_flips;   // cycles flipped in the running pass
     unsigned long long cycles;       // cycles flipped in total
@@ -268,6 +270,10 @@ void launch_weights(const Work *d, const Shape &sh, Sink &k);
 void launch_mcm_load(const Work *d, const Shape &sh, Sink &k);
 void launch_mcm_phase(const Work *d, const Shape &sh, Sink &k);
 void launch_mcm_level(const Work *d, const Shape &sh, Sink &k);
+// Graph form of a level: its steps, the last one also setting the level
+// loop's condition (no separate condition kernel).
+void launch_mcm_level_graph(const Work *d, const Shape &sh, cudaGraphConditionalHandle h,
+                            Sink &k);
 void launch_mcm_augment(const Work *d, const Shape &sh, Sink &k);
 void launch_mcm_store(const Work *d, const Shape &sh, Sink &k);
 // Graph forms: the condition of the level loop (undecided frontier left),

@@ -469,21 +469,25 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
     const Work &w = *W;
     if (w.ctl->err & kErrInvalid)
         return;
-    constexpr int kU = 2;
+#ifndef AWPM_ENTRIES_U
+#define AWPM_ENTRIES_U 2
+#endif
+    constexpr int kU = AWPM_ENTRIES_U;
     const int lane = threadIdx.x & 31;
-    const int64_t nwarps = gstride() >> 5;
-    const int32_t n = w.n, nnz = w.nnz;
+    // 32-bit tile arithmetic: ntiles < 2^26, positions < 2^31
+    const int32_t nwarps = (int32_t)(gstride() >> 5);
+    const int32_t n = w.n, nnz = w.nnz, ntiles = w.ntiles;
     const int32_t *__restrict__ rowidx = w.rowidx;
     unsigned bits = 0;
-    for (int64_t t0 = gtid() >> 5; t0 < w.ntiles; t0 += kU * nwarps) {
+    for (int32_t t0 = (int32_t)(gtid() >> 5); t0 < ntiles; t0 += kU * nwarps) {
         int32_t c0[kU], r[kU], prev[kU], mate[kU], j[kU], cs[kU], ce[kU];
         uint32_t mask[kU];
         double x[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int64_t t = t0 + u * nwarps;
-            const int32_t p = (int32_t)(t * kTile) + lane;
-            const bool tv = t < w.ntiles;
+            const int32_t t = t0 + u * nwarps;
+            const bool tv = t < ntiles;
+            const int32_t p = tv ? t * kTile + lane : 0;
             const bool valid = tv && p < nnz;
             c0[u] = tv ? __ldg(w.tile_col + t) : 0;
             mask[u] = tv ? __ldg(w.starts + t) : 1u;
@@ -493,9 +497,8 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int64_t t = t0 + u * nwarps;
-            const int32_t p = (int32_t)(t * kTile) + lane;
-            const bool valid = t < w.ntiles && p < nnz;
+            const int32_t t = t0 + u * nwarps;
+            const bool valid = t < ntiles && t * kTile + lane < nnz;
             j[u] = valid ? lane_column(c0[u], mask[u], lane) : -1 - lane;
             mate[u] = valid ? __ldg(w.mate_in + j[u]) : -1;
             const bool bl = valid && w.bloom;
@@ -504,10 +507,11 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int64_t t = t0 + u * nwarps;
-            const int32_t base = (int32_t)(t * kTile);
+            const int32_t t = t0 + u * nwarps;
+            const bool tv = t < ntiles;
+            const int32_t base = tv ? t * kTile : 0;
             const int32_t p = base + lane;
-            const bool valid = t < w.ntiles && p < nnz;
+            const bool valid = tv && p < nnz;
             const int32_t up = __shfl_up_sync(FULL_MASK, r[u], 1);
             const int32_t before = lane == 0 ? prev[u] : up;
             const bool in_range = r[u] >= 0 && r[u] < n;
@@ -2441,6 +2445,7 @@ __global__ void k_mc_reset(const Work *__restrict__ W)
         c->cycles = 0ull;
         c->level_tiles = 0;
         c->level_listed = 0;
+        c->level_done = 0u;
     }
     for (int64_t x = gtid(); x < w.n; x += gstride())
         w.mr[x] = -1;
@@ -2688,15 +2693,14 @@ __global__ void k_mc_colof(const Work *__restrict__ W)
             w.mcolof[p] = (int32_t)j;
 }
 
-// Level, step 5: the next frontier without the trees that have an end; its
+// Level, step 3: the next frontier without the trees that have an end; its
 // size into Ctl::live.
-__global__ void k_mc_advance(const Work *__restrict__ W)
+__device__ __forceinline__ void mc_advance(const Work &w)
 {
-    const Work &w = *W;
     int live = 0;
     if (!w.ctl->err) {
         // the next frontier and its tile list (the list's count was zeroed
-        // by k_mc_offer_min of this level)
+        // by k_mc_join of this level)
         const int lane = threadIdx.x & 31;
         const int64_t words = (int64_t)w.n / 32 + 1;
         for (int64_t x0 = gtid() - lane; x0 < words; x0 += gstride()) {
@@ -2721,19 +2725,49 @@ __global__ void k_mc_advance(const Work *__restrict__ W)
     warp_add_i32(live, &w.ctl->live);
 }
 
-// Graph form of the level loop's condition: a frontier is left.
-__global__ void k_mc_cond_level(const Work *__restrict__ W, cudaGraphConditionalHandle h)
+__global__ void k_mc_advance(const Work *__restrict__ W)
 {
-    Ctl *c = W->ctl;
-    const int32_t live = c->live;
-    c->live = 0;
+    mc_advance(*W);
+}
+
+// The level loop's condition from the live count: count the level, cap the
+// levels of a phase (every level adds a row to the search forest, so n + 1
+// levels mean a broken invariant), continue while a frontier is left.
+__device__ __forceinline__ void mc_level_condition(const Work &w, cudaGraphConditionalHandle h)
+{
+    Ctl *c = w.ctl;
+    const int32_t live = atomicExch(&c->live, 0);
     if (live > 0) {
         c->levels += 1;
-        // every level adds at least one row to the search forest
-        if (++c->phase_levels > W->n + 1)
+        if (++c->phase_levels > w.n + 1)
             raise_err(c, kErrTimeout);
     }
-    cudaGraphSetConditional(h, (live > 0 && c->err == 0u) ? 1u : 0u);
+    cudaGraphSetConditional(h, (live > 0 && *(volatile unsigned *)&c->err == 0u) ? 1u : 0u);
+}
+
+// Graph form of step 3: the block that finishes last also sets the level
+// loop's condition (its count of finished blocks orders it after every
+// other block's frontier count).
+__global__ void k_mc_advance_graph(const Work *__restrict__ W, cudaGraphConditionalHandle h)
+{
+    const Work &w = *W;
+    mc_advance(w);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(&w.ctl->level_done, 1u);
+        if (prev == gridDim.x - 1) {
+            __threadfence();
+            w.ctl->level_done = 0u;
+            mc_level_condition(w, h);
+        }
+    }
+}
+
+// Graph form of the level loop's condition before a phase's first level.
+__global__ void k_mc_cond_level(const Work *__restrict__ W, cudaGraphConditionalHandle h)
+{
+    mc_level_condition(*W, h);
 }
 
 // Graph form of the end of a phase: count it and the paths it augmented;
@@ -3066,6 +3100,16 @@ void launch_mcm_augment(const Work *d, const Shape &sh, Sink &k)
 {
     void *a[] = {(void *)&d};
     k.launch((const void *)k_mc_augment, util_grid(sh), kThreads, a);
+}
+
+void launch_mcm_level_graph(const Work *d, const Shape &sh, cudaGraphConditionalHandle h,
+                            Sink &k)
+{
+    void *a[] = {(void *)&d};
+    void *ah[] = {(void *)&d, (void *)&h};
+    k.launch((const void *)k_mc_offer, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_join, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_mc_advance_graph, util_grid(sh), kThreads, ah);
 }
 
 void launch_mcm_cond_level(const Work *d, const Shape &sh, cudaGraphConditionalHandle h, Sink &k)
