@@ -298,11 +298,9 @@ __device__ __forceinline__ void put_rowrec(const Work &w, int32_t row, int32_t s
                                            unsigned long long sig, double wmatch)
 {
     w.rsig[row] = sig;
-    RowRange g;
-    g.s = s;
-    g.e = e;
-    g.w = wmatch;
-    w.rrange[row] = g;
+    // one 16-byte store
+    *reinterpret_cast<int4 *>(w.rrange + row) =
+        make_int4(s, e, __double2loint(wmatch), __double2hiint(wmatch));
 }
 
 __device__ __forceinline__ RowRange ld_range(const RowRange *p)
