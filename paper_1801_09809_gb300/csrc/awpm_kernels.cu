@@ -1702,13 +1702,56 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
 // Step D (Algorithm 6): conflicts, per-key selection, flip
 // ---------------------------------------------------------------------------
 
+// The winners (set bits) of the bitmap words [x0, x0 + 32), 32 at a time
+// with every lane busy: the words' bit counts are scanned across the warp,
+// and in each round lane l takes the winner of rank round * 32 + l (found by
+// a binary search over the scan and the word's rank-th set bit).  Calls
+// f(j) on every lane each round, j = -1 for lanes past the last winner.
+// Called by the whole warp; `clear` zeroes the words as they are read.
+template <typename F>
+__device__ __forceinline__ void for_winners(uint32_t *winbits, int64_t x0, int64_t words, int lane,
+                                            bool clear, F f)
+{
+    const uint32_t mine = x0 + lane < words ? winbits[x0 + lane] : 0u;
+    if (clear && mine)
+        winbits[x0 + lane] = 0u;
+    const int cnt = __popc(mine);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(FULL_MASK, incl, 31);
+    for (int base = 0; base < total; base += 32) {
+        const int want = base + lane;
+        // the last word whose first rank is <= want
+        int src = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(FULL_MASK, excl, src + step);
+            if (e <= want)
+                src += step;
+        }
+        const int first = __shfl_sync(FULL_MASK, excl, src);
+        const uint32_t word = __shfl_sync(FULL_MASK, mine, src);
+        int32_t j = -1;
+        if (want < total) {
+            const int bit = (int)__fns(word, 0u, want - first + 1);
+            j = (int32_t)((x0 + src) * 32 + bit);
+        }
+        f(j);
+    }
+}
+
 // For every Step-C winner rooted at j (a set bit of the winner bitmap) with
 // second matched edge at column k = m_i: drop it if column k is itself the
 // root of a Step-C winner, otherwise compete for key k (maximum gain, then
-// lowest root j).  The winner's key (or -1) is kept for the flip.
-// A warp loads 32 bitmap words at a time and takes their nonzero words one
-// by one, lane b handling the winner at bit b, so the winners of a word are
-// handled side by side rather than one after another.
+// lowest root j).  The winner's key (or -1) is kept for the flip.  A warp
+// takes 32 bitmap words at a time and their winners 32 at a time, a lane
+// per winner.
 __global__ void k_select(const Work *__restrict__ W)
 {
     const Work &w = *W;
@@ -1718,29 +1761,21 @@ __global__ void k_select(const Work *__restrict__ W)
     const int64_t words = (int64_t)w.n / 32 + 1;
     const int64_t nwarps = gstride() >> 5;
     for (int64_t x0 = (gtid() >> 5) * 32; x0 < words; x0 += nwarps * 32) {
-        const uint32_t mine = x0 + lane < words ? w.winbits[x0 + lane] : 0u;
-        unsigned nz = __ballot_sync(FULL_MASK, mine != 0u);
-        while (nz) {
-            const int src = __ffs(nz) - 1;
-            nz &= nz - 1;
-            const uint32_t bits = __shfl_sync(FULL_MASK, mine, src);
-            if (!((bits >> lane) & 1u))
-                continue;
-            const int32_t j = (int32_t)((x0 + src) * 32 + lane);
-            if (!AWPM_IN(w.ctl, j, w.n))
-                continue;
+        for_winners(w.winbits, x0, words, lane, false, [&](int32_t j) {
+            if (j < 0 || !AWPM_IN(w.ctl, j, w.n))
+                return;
             const Rec r = w.best[j];
             if (!AWPM_IN(w.ctl, r.p, w.nnz))
-                continue;
+                return;
             const int32_t i = __ldg(w.rowidx + r.p);
             if (!AWPM_IN(w.ctl, i, w.n))
-                continue;
+                return;
             const int32_t k = w.mr[i];
             if (!AWPM_IN(w.ctl, k, w.n))
-                continue;
+                return;
             if ((w.winbits[k >> 5] >> (k & 31)) & 1u) {
                 w.wkey[j] = -1;
-                continue;
+                return;
             }
             w.wkey[j] = k;
             Sel sl;
@@ -1748,7 +1783,7 @@ __global__ void k_select(const Work *__restrict__ W)
             sl.j = j;
             sl.pad = 0;
             sel_combine(w.dsel + k, sl, w.ctl);
-        }
+        });
     }
 }
 
@@ -1756,9 +1791,9 @@ __global__ void k_select(const Work *__restrict__ W)
 // the row records of rows i and m_j follow their new mates.  The selected
 // cycles are vertex-disjoint, so each lane owns its four vertices.  The
 // Step-C records and winner bits visited are cleared, which leaves them
-// empty for the next pass.  Words of the winner bitmap are taken as in
-// k_select; in a batched solve the flips of a word are counted per matrix
-// with one atomic per matrix (the word's columns are consecutive).
+// empty for the next pass.  Winners are taken as in k_select; in a batched
+// solve the flips of a round are counted per matrix with one atomic per
+// matrix.
 __global__ void k_flip(const Work *__restrict__ W)
 {
     const Work &w = *W;
@@ -1768,53 +1803,44 @@ __global__ void k_flip(const Work *__restrict__ W)
         const int64_t words = (int64_t)w.n / 32 + 1;
         const int64_t nwarps = gstride() >> 5;
         for (int64_t x0 = (gtid() >> 5) * 32; x0 < words; x0 += nwarps * 32) {
-            const uint32_t mine = x0 + lane < words ? w.winbits[x0 + lane] : 0u;
-            if (mine)
-                w.winbits[x0 + lane] = 0u;
-            unsigned nz = __ballot_sync(FULL_MASK, mine != 0u);
-            while (nz) {
-                const int src = __ffs(nz) - 1;
-                nz &= nz - 1;
-                const uint32_t bits = __shfl_sync(FULL_MASK, mine, src);
+            for_winners(w.winbits, x0, words, lane, true, [&](int32_t j) {
                 int32_t mat = -1;  // matrix of a flipped cycle (batched solve)
-                if ((bits >> lane) & 1u) {
-                    const int32_t j = (int32_t)((x0 + src) * 32 + lane);
-                    const Rec r = AWPM_IN(w.ctl, j, w.n) ? w.best[j] : Rec{0.0, 0, 0};
-                    if (AWPM_IN(w.ctl, j, w.n))
-                        w.best[j] = Rec{0.0, 0, 0};
-                    int32_t k = AWPM_IN(w.ctl, j, w.n) ? w.wkey[j] : -1;
+                if (j >= 0 && AWPM_IN(w.ctl, j, w.n)) {
+                    const Rec r = w.best[j];
+                    w.best[j] = Rec{0.0, 0, 0};
+                    int32_t k = w.wkey[j];
                     if (k >= 0 && !(AWPM_IN(w.ctl, k, w.n) && AWPM_IN(w.ctl, r.p, w.nnz) &&
                                     AWPM_IN(w.ctl, r.q, w.nnz)))
                         k = -1;
                     const Sel sl = k >= 0 ? w.dsel[k] : Sel{0.0, 0, 0};
                     if (k >= 0 && gbits(sl.g) > 0ll && sl.j == j) {
                         w.dsel[k] = Sel{0.0, 0, 0};
-                    }
-                    const int32_t i = k >= 0 && gbits(sl.g) > 0ll && sl.j == j ? w.rowidx[r.p] : -1;
-                    const int32_t mj = i >= 0 ? w.mc[j] : -1;
-                    // every lane reaches the warp-wide match below: no early exit
-                    if (i >= 0 && AWPM_IN(w.ctl, i, w.n) && AWPM_IN(w.ctl, mj, w.n)) {
-                        const double wij = w.w[r.p];
-                        const double wq = w.w[r.q];
-                        w.mc[j] = i;
-                        w.mr[i] = j;
-                        w.mc[k] = mj;
-                        w.mr[mj] = k;
-                        w.wm[j] = wij;
-                        w.wm[k] = wq;
-                        put_rowrec(w, i, w.colptr[j], w.colptr[j + 1], w.colsig[j], wij);
-                        put_rowrec(w, mj, w.colptr[k], w.colptr[k + 1], w.colsig[k], wq);
-                        ++flips;
-                        if (w.bw.count > 0)
-                            mat = w.bw.colmat[k];
+                        const int32_t i = w.rowidx[r.p];
+                        const int32_t mj = w.mc[j];
+                        if (AWPM_IN(w.ctl, i, w.n) && AWPM_IN(w.ctl, mj, w.n)) {
+                            const double wij = w.w[r.p];
+                            const double wq = w.w[r.q];
+                            w.mc[j] = i;
+                            w.mr[i] = j;
+                            w.mc[k] = mj;
+                            w.mr[mj] = k;
+                            w.wm[j] = wij;
+                            w.wm[k] = wq;
+                            put_rowrec(w, i, w.colptr[j], w.colptr[j + 1], w.colsig[j], wij);
+                            put_rowrec(w, mj, w.colptr[k], w.colptr[k + 1], w.colsig[k], wq);
+                            ++flips;
+                            if (w.bw.count > 0)
+                                mat = w.bw.colmat[k];
+                        }
                     }
                 }
+                // every lane reaches the warp-wide match: no early exit above
                 if (w.bw.count > 0) {
                     const unsigned peers = __match_any_sync(FULL_MASK, mat);
                     if (mat >= 0 && (peers & ((1u << lane) - 1u)) == 0u)
                         atomicAdd(w.bw.mflips + mat, (unsigned long long)__popc(peers));
                 }
-            }
+            });
         }
     }
     block_add_u64(flips, &w.ctl->pass_flips);
