@@ -571,7 +571,7 @@ void ctx_trim(awpm_ctx *c)
                       &c->gcpos,   &c->grkey,    &c->grcol,    &c->gmate,    &c->gtdead,
                       &c->psel,    &c->pslive,   &c->pstaken,  &c->psused,   &c->wt_cmax,
                       &c->wt_rmax, &c->wt_stage, &c->mroot,    &c->mrpar,    &c->mfront,
-                      &c->mnext,   &c->mroff,    &c->mtend,
+                      &c->mnext,   &c->mroff,    &c->mtend,    &c->mtouch,
                       &c->mstage,  &c->mcolof,   &c->mtiles,   &c->rowsig,   &c->trowptr,
                       &c->rs_k0,   &c->rs_k1,    &c->rs_v0,    &c->rs_v1,    &c->rs_hist,
                       &c->rs_sums};
@@ -658,7 +658,7 @@ void teardown_ctx(awpm_ctx *c)
                       &c->gtdead,  &c->psel,     &c->pslive,   &c->pstaken,  &c->psused,
                       &c->wt_cmax, &c->wt_rmax,  &c->wt_stage,
                       &c->mroot,   &c->mrpar,    &c->mfront,   &c->mnext,    &c->mroff,
-                      &c->mtend,   &c->mstage,   &c->mcolof,
+                      &c->mtend,   &c->mtouch,   &c->mstage,   &c->mcolof,
                       &c->mtiles,  &c->rowsig,   &c->trowptr,  &c->rs_k0,    &c->rs_k1,
                       &c->rs_v0,   &c->rs_v1,    &c->rs_hist,  &c->rs_sums};
     for (DevBuf *b : bufs)
@@ -1451,6 +1451,7 @@ int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *row
     AWPM_TRY(ensure(c, c->mrpar, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->mroff, sizeof(Off) * n));
     AWPM_TRY(ensure(c, c->mtend, sizeof(Off) * n));
+    AWPM_TRY(ensure(c, c->mtouch, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->mfront, sizeof(uint32_t) * words));
     AWPM_TRY(ensure(c, c->mcolof, sizeof(int32_t) * ((size_t)nnz + 1)));
     AWPM_TRY(ensure(c, c->mnext, sizeof(uint32_t) * words));
@@ -1488,6 +1489,7 @@ int awpm_mcm(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *row
     wk.mnext = (uint32_t *)c->mnext.p;
     wk.mroff = (Off *)c->mroff.p;
     wk.mtend = (Off *)c->mtend.p;
+    wk.mtouch = (int32_t *)c->mtouch.p;
     wk.mmate = dmate;
     wk.mcolof = (int32_t *)c->mcolof.p;
     wk.mtiles = (int32_t *)c->mtiles.p;

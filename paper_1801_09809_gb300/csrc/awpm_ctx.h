@@ -115,7 +115,7 @@ struct awpm_ctx {
     awpm::DevBuf gmate;                       // greedy start of awpm_improve_ctx
     awpm::DevBuf psel, pslive, pstaken, psused;  // greedy (Pettie-Sanders) selection
     awpm::DevBuf wt_cmax, wt_rmax, wt_stage;     // weights from matrix values
-    awpm::DevBuf mroot, mrpar, mfront, mnext, mroff, mtend, mstage,
+    awpm::DevBuf mroot, mrpar, mfront, mnext, mroff, mtend, mtouch, mstage,
         mcolof, mtiles;  // maximum matching
     awpm::DevBuf rowsig, trowptr, rs_k0, rs_k1, rs_v0, rs_v1, rs_hist, rs_sums;  // row marking
     awpm::DevBuf b_noff, b_colmat, b_tilemat, b_tlist, b_i32, b_u64, b_f64;

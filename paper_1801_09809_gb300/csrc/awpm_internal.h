@@ -96,7 +96,7 @@ struct Ctl {
     int32_t level_tiles;         // maximum matching: tiles listed for the next level
     int32_t level_listed;        // maximum matching: tiles listed for this level
     uint32_t level_done;         // maximum matching: blocks done with the level's last step
-    uint32_t pad_ld;
+    int32_t touched;             // maximum matching: rows listed in mtouch this level
     unsigned long long levels;   // maximum matching: search levels run
     unsigned long long pass_flips;   // cycles flipped in the running pass
     unsigned long long cycles;       // cycles flipped in total
@@ -195,6 +195,7 @@ struct Work {
     uint32_t *mnext;
     Off *mroff;         // per row: the level's best offer (key, column)
     Off *mtend;         // per tree (root column): its end (key of the last edge, row)
+    int32_t *mtouch;    // rows offered something at this level (each once)
     int32_t *mmate;
     int32_t *mcolof;    // column of every entry
     int32_t *mtiles;    // tiles holding a frontier column, this level

@@ -2470,6 +2470,7 @@ __global__ void k_mc_reset(const Work *__restrict__ W)
         c->level_tiles = 0;
         c->level_listed = 0;
         c->level_done = 0u;
+        c->touched = 0;
     }
     for (int64_t x = gtid(); x < w.n; x += gstride())
         w.mr[x] = -1;
@@ -2604,8 +2605,10 @@ __global__ void k_mc_phase(const Work *__restrict__ W)
             mc_list_tiles(w, x, bits, lane);
         }
     }
-    if (gtid() == 0)
+    if (gtid() == 0) {
         w.ctl->phase_levels = 0;
+        w.ctl->touched = 0;
+    }
     warp_add_i32(live, &w.ctl->live);
 }
 
@@ -2643,19 +2646,20 @@ __device__ __forceinline__ bool off_better(long long key, int32_t who, const Off
 // Fold (key, who) into the record at addr (128-bit compare-and-swap; a
 // failed exchange means another thread stored a better record, so the loop
 // is short; its bound only turns a broken invariant into an error bit).
-__device__ void off_combine(Off *addr, long long key, int32_t who, Ctl *ctl)
+__device__ bool off_combine(Off *addr, long long key, int32_t who, Ctl *ctl)
 {
     Off cur = *addr;
     Off mine{key, who, 0};
     for (int k = 0; k < kCasRetryCap; ++k) {
         if (!off_better(key, who, cur))
-            return;
+            return false;
         const Off old = atomicCAS(addr, cur, mine);
         if (old.key == cur.key && old.who == cur.who && old.pad == cur.pad)
-            return;
+            return old.who == 0x7fffffff;  // this exchange replaced the empty record
         cur = old;
     }
     raise_err(ctl, kErrTimeout);
+    return false;
 }
 
 // Level, step 1: per unreached row the best offer of the level: the
@@ -2665,17 +2669,17 @@ __global__ void k_mc_offer(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    // the list's count, kept for the level's later steps
-    if (gtid() == 0)
-        w.ctl->level_listed = w.ctl->level_tiles;
     MC_TILE_LOOP_BEGIN(w.ctl->level_tiles)
     if (r == w.mc[c] || w.mrpar[r] != -1)
         continue;
-    off_combine(w.mroff + r, order_key(w.w[p]), c, w.ctl);
+    // the exchange that fills a row's empty record lists the row, once
+    if (off_combine(w.mroff + r, order_key(w.w[p]), c, w.ctl))
+        w.mtouch[atomicAdd(&w.ctl->touched, 1)] = r;
     MC_TILE_LOOP_END
 }
 
-// Level, step 2: rows join the winning column's tree.  A free row is a
+// Level, step 2: every row offered something at this level (listed by
+// k_mc_offer) joins the tree of its best offer's column.  A free row is a
 // candidate end of the tree: the tree keeps the heaviest last edge, then the
 // lowest row.  A matched row brings its column into the next frontier.
 __global__ void k_mc_join(const Work *__restrict__ W)
@@ -2683,22 +2687,24 @@ __global__ void k_mc_join(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    // the next level's list starts empty (filled by k_mc_advance)
+    // the next level's tile list starts empty (filled by k_mc_advance)
     if (gtid() == 0)
         w.ctl->level_tiles = 0;
-    MC_TILE_LOOP_BEGIN(w.ctl->level_listed)
-    if (r == w.mc[c] || w.mroff[r].who != c || w.mrpar[r] != -1)
-        continue;
-    w.mrpar[r] = c;
-    const int32_t t_root = w.mroot[c];
-    const int32_t c2 = w.mr[r];
-    if (c2 < 0) {
-        off_combine(w.mtend + t_root, order_key(w.w[p]), r, w.ctl);
-    } else {
-        w.mroot[c2] = t_root;
-        atomicOr(w.mnext + (c2 >> 5), 1u << (c2 & 31));
+    const int32_t touched = w.ctl->touched;
+    for (int64_t x = gtid(); x < touched; x += gstride()) {
+        const int32_t r = w.mtouch[x];
+        const Off o = w.mroff[r];
+        const int32_t c = o.who;
+        w.mrpar[r] = c;
+        const int32_t t_root = w.mroot[c];
+        const int32_t c2 = w.mr[r];
+        if (c2 < 0) {
+            off_combine(w.mtend + t_root, o.key, r, w.ctl);
+        } else {
+            w.mroot[c2] = t_root;
+            atomicOr(w.mnext + (c2 >> 5), 1u << (c2 & 31));
+        }
     }
-    MC_TILE_LOOP_END
 }
 
 #undef MC_TILE_LOOP_BEGIN
@@ -2721,6 +2727,9 @@ __global__ void k_mc_colof(const Work *__restrict__ W)
 // size into Ctl::live.
 __device__ __forceinline__ void mc_advance(const Work &w)
 {
+    // the next level's offered rows start empty
+    if (gtid() == 0)
+        w.ctl->touched = 0;
     int live = 0;
     if (!w.ctl->err) {
         // the next frontier and its tile list (the list's count was zeroed
