@@ -234,7 +234,7 @@ struct Shape {
     int select;         // AWPM_SELECT_STEP_D or AWPM_SELECT_GREEDY
 };
 
-constexpr int kWsumBlocks = 256;
+constexpr int kWsumBlocks = 1024;
 constexpr int kWsumThreads = 256;
 
 // Where launches go: a stream (launched at once, asynchronously) or a graph
