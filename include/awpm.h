@@ -398,7 +398,7 @@ int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
 
 /*
  * Size limits of awpm_search_noalloc (its scratch is a fixed array of about
- * 18 MB in device memory, held by every GPU that loads the library).
+ * 19 MB in device memory, held by every GPU that loads the library).
  */
 #define AWPM_NOALLOC_MAX_N 262144
 #define AWPM_NOALLOC_MAX_NNZ 4194304
@@ -412,7 +412,7 @@ int awpm_search(awpm_ctx *ctx, int32_t n, const int32_t *colptr, const int32_t *
  * (Step-C winner gain and row per column, and the request counters in stats)
  * but allocates nothing: no cudaMalloc, no cudaFree, no pinned buffers, no
  * allocating library routine.  Its scratch is one fixed __device__ array of
- * about 18 MB inside the library, which every GPU that loads the library holds
+ * about 19 MB inside the library, which every GPU that loads the library holds
  * until the process exits.
  *   - n <= AWPM_NOALLOC_MAX_N and nnz <= AWPM_NOALLOC_MAX_NNZ, otherwise
  *     AWPM_ERR_TOO_LARGE.

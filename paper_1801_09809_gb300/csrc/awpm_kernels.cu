@@ -27,13 +27,8 @@ namespace awpm {
 // into an error bit instead of a hang).
 constexpr int kCasRetryCap = 1 << 20;
 
-// Closing-edge ranges longer than this go to the warp-cooperative search,
-// and so do all of a warp's ranges when at most kCoopFew lanes need one.
+// Closing-edge ranges longer than this go to the warp-cooperative search.
 constexpr int32_t kCoopMin = 32;
-#ifndef AWPM_COOP_FEW
-#define AWPM_COOP_FEW 3
-#endif
-constexpr int kCoopFew = AWPM_COOP_FEW;
 // Quiet NaN: wm[j] before the entry pass finds the matched entry of column j.
 constexpr unsigned long long kNaNBits = 0x7ff8000000000000ull;
 

@@ -5,7 +5,7 @@
 // handed the whole GPU to its own memory pool, or code running where an
 // allocation (which may synchronise the device) is not allowed.  This entry
 // point therefore allocates nothing.  Its scratch lives in one file-scope
-// __device__ array of fixed size (kScratchBytes, about 18 MB), which every
+// __device__ array of fixed size (kScratchBytes, about 19 MB), which every
 // GPU that loads the library keeps until the process exits.  The caller
 // passes every input and output in device memory.
 #include <cuda_runtime.h>
