@@ -715,19 +715,15 @@ __global__ void k_batch_cols(const Work *__restrict__ W)
         if ((x == 0 && o != 0) || (x == count && o != w.n) || (x < count && n_off[x + 1] < o))
             raise_err(w.ctl, kErrInvalid);
     }
-    for (int64_t x = gtid(); x < w.n; x += gstride()) {
-        // number of matrices ending at or before column x = its matrix
-        int32_t lo = 0, len = count;
-        while (len > 0) {
-            const int32_t half = len >> 1;
-            if (__ldg(n_off + lo + half + 1) <= x) {
-                lo += half + 1;
-                len -= half + 1;
-            } else {
-                len = half;
-            }
-        }
-        w.bw.colmat[x] = lo < count ? lo : count - 1;
+    // a warp per matrix writes the matrix number of its columns (clamped to
+    // [0, n): offsets found invalid above raise the error but write nothing
+    // out of range)
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t b = gtid() >> 5; b < count; b += nwarps) {
+        const int32_t lo = max(n_off[b], 0), hi = min(n_off[b + 1], w.n);
+        for (int32_t x = lo + lane; x < hi; x += 32)
+            w.bw.colmat[x] = (int32_t)b;
     }
 }
 
@@ -742,20 +738,35 @@ __global__ void __launch_bounds__(kThreads) k_batch_check(const Work *__restrict
     const int64_t nwarps = gstride() >> 5;
     const BatchWork &bw = w.bw;
     unsigned bad = 0;
-    for (int64_t t = gtid() >> 5; t < w.ntiles; t += nwarps) {
-        const int32_t p = (int32_t)(t * kTile) + lane;
-        const int32_t c0 = w.tile_col[t];
-        if (p < w.nnz) {
-            const int32_t b = bw.colmat[lane_column(c0, w.starts[t], lane)];
-            const int32_t r = w.rowidx[p];
-            if (r < bw.n_off[b] || r >= bw.n_off[b + 1])
-                bad = 1;
+    // four tiles per warp round, their loads side by side (the checks are
+    // chains of dependent gathers)
+    constexpr int kU = 4;
+    for (int64_t t0 = gtid() >> 5; t0 < w.ntiles; t0 += kU * nwarps) {
+        int32_t c0[kU], b[kU], r[kU];
+        uint32_t mask[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t t = t0 + u * nwarps;
+            const bool tv = t < w.ntiles;
+            c0[u] = tv ? w.tile_col[t] : 0;
+            mask[u] = tv ? w.starts[t] : 1u;
+            const int64_t p = t * kTile + lane;
+            r[u] = tv && p < w.nnz ? w.rowidx[p] : -1;
         }
-        if (lane == 0) {
-            const int32_t b0 = bw.colmat[c0];
-            const int32_t b1 =
-                (t + 1 < w.ntiles) ? bw.colmat[w.tile_col[t + 1]] : bw.colmat[w.n - 1];
-            bw.tilemat[t] = b0 | (b0 == b1 ? kTileSingle : 0);
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            b[u] = r[u] >= 0 ? bw.colmat[lane_column(c0[u], mask[u], lane)] : 0;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t t = t0 + u * nwarps;
+            if (r[u] >= 0 && (r[u] < bw.n_off[b[u]] || r[u] >= bw.n_off[b[u] + 1]))
+                bad = 1;
+            if (lane == 0 && t < w.ntiles) {
+                const int32_t b0 = bw.colmat[c0[u]];
+                const int32_t b1 =
+                    (t + 1 < w.ntiles) ? bw.colmat[w.tile_col[t + 1]] : bw.colmat[w.n - 1];
+                bw.tilemat[t] = b0 | (b0 == b1 ? kTileSingle : 0);
+            }
         }
     }
     if (__any_sync(FULL_MASK, bad) && lane == 0)
@@ -2664,13 +2675,40 @@ __global__ void k_mc_offer(const Work *__restrict__ W)
     const Work &w = *W;
     if (w.ctl->err)
         return;
-    MC_TILE_LOOP_BEGIN(w.ctl->level_tiles)
-    if (r == w.mc[c] || w.mrpar[r] != -1)
-        continue;
-    // the exchange that fills a row's empty record lists the row, once
-    if (off_combine(w.mroff + r, order_key(w.w[p]), c, w.ctl))
-        w.mtouch[atomicAdd(&w.ctl->touched, 1)] = r;
-    MC_TILE_LOOP_END
+    // (the loop of the other level steps, written out: every lane stays to
+    // the warp-wide append of the rows it lists)
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = gstride() >> 5;
+    const bool exact = w.ctl->nonempty != 0;
+    const int64_t listed = w.ctl->level_tiles;
+    for (int64_t x = gtid() >> 5; x < listed; x += nwarps) {
+        const int64_t t = w.mtiles[x];
+        const int32_t p = (int32_t)(t * kTile) + lane;
+        const bool valid = p < w.nnz;
+        const int32_t c = !valid ? 0
+                          : exact ? lane_column(__ldg(w.tile_col + t), __ldg(w.starts + t), lane)
+                                  : __ldg(w.mcolof + p);
+        const bool inf = valid && ((w.mfront[c >> 5] >> (c & 31)) & 1u);
+        if (!__any_sync(FULL_MASK, inf))
+            continue;
+        bool first = false;
+        int32_t r = -1;
+        if (inf) {
+            r = w.rowidx[p];
+            // the exchange that fills a row's empty record lists the row, once
+            if (r != w.mc[c] && w.mrpar[r] == -1)
+                first = off_combine(w.mroff + r, order_key(w.w[p]), c, w.ctl);
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, first);
+        if (m) {
+            int32_t base = 0;
+            if (lane == 0)
+                base = atomicAdd(&w.ctl->touched, __popc(m));
+            base = __shfl_sync(FULL_MASK, base, 0);
+            if (first)
+                w.mtouch[base + __popc(m & ((1u << lane) - 1u))] = r;
+        }
+    }
 }
 
 // Level, step 2: every row offered something at this level (listed by
