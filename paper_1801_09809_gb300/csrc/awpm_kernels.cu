@@ -1181,9 +1181,9 @@ struct LookupQueue {
 // ((w_ij + w_q) - w(i, m_i)) - w(m_j, j), and a positive gain goes into the
 // root's Step-C record (maximum gain, then lowest position; Algorithm 5).
 // Called by the whole warp.
-template <int kLookup>
+template <int kLookup, typename Queue>
 __device__ __forceinline__ void resolve_lookups(
-    const LookupQueue &qu, int head, int k, int lane, const int32_t *__restrict__ rowidx,
+    const Queue &qu, int head, int k, int lane, const int32_t *__restrict__ rowidx,
     const double *__restrict__ wv, const double *__restrict__ wm,
     const unsigned long long *__restrict__ htab, const uint32_t *__restrict__ bloom,
     const int32_t *__restrict__ trowptr, const int32_t *__restrict__ tpos,
@@ -1526,18 +1526,22 @@ __global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
     block_add_u64((unsigned long long)n_pos, &ctl->positive);
 }
 
-// Pipelined form of the single-problem search (same work, same results as
+// Pipelined form of the single-problem search (the same work and results as
 // k_search<kLookup, false, ...>).  A warp's tiles are taken kU at a time
-// (tiles t, t + nwarps, ...), and each round advances three stages at once,
-// each on loads issued one round earlier:
-//   R: the row records of round r-1 arrived: signature test, queue;
-//   M: the matched rows m_j of round r arrived: candidate test (i > m_j),
-//      row-record loads of the candidates issued;
-//   P: first column, start bits and row indices of round r+1 arrived: the
-//      lanes' columns, loads of m_j issued; loads of round r+2 issued.
-// So the two dependent gathers of a nonzero (m_j, then the row record of i)
-// are each hidden behind a round of other work instead of being waited for
-// back to back.  All tile arithmetic is 32-bit (ntiles < 2^26).
+// (tiles t, t + nwarps, ...), and each round advances four stages at once,
+// each on loads issued one round earlier: the signature test of one round,
+// the candidate test (i > m_j) and signature loads of the next, the lanes'
+// columns and the loads of m_j of the one after, the tile loads (first
+// column, start bits, row indices) of the one after that.  So the two
+// dependent gathers of a nonzero (m_j, then the signature of its row's
+// column) are each hidden behind a round of other work.  Three slot sets
+// carry a round's tiles through the stages; the loop body is written out
+// three times with the slots' roles rotated, so no value is copied from one
+// stage's registers to the next.  Tile loads take the tile index clamped to
+// ntiles (always in bounds) and a lane is valid exactly when its position is
+// below nnz; a lane's request goes to its queue slot, or to a discard slot
+// of its own when it does not pass, so the stores need no branch.  All tile
+// arithmetic is 32-bit (ntiles < 2^26).
 #ifndef AWPM_PIPE_U_WIDE
 #define AWPM_PIPE_U_WIDE 2
 #endif
@@ -1556,13 +1560,22 @@ struct PipeCfg {
     static constexpr int kMinBlocks = kWide ? AWPM_PIPE_MINB_WIDE : AWPM_PIPE_MINB_NARROW;
 };
 
-template <int kLookup, bool kWide>
+// The lookup queue with a discard slot per lane after the 64 ring slots.
+constexpr int kQueueDiscard = kQueue + 32;
+struct LookupQueueD {
+    int32_t j[kQueueDiscard];
+    int32_t p[kQueueDiscard];
+    int32_t i[kQueueDiscard];
+    int32_t mj[kQueueDiscard];
+};
+
+template <int kLookup, bool kWide, bool kBatch>
 __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
     k_search_pipe(const Work *__restrict__ W)
 {
     constexpr int kU = PipeCfg<kWide>::kU;
     __shared__ int s_go;
-    __shared__ LookupQueue s_queue[kThreads / 32];
+    __shared__ LookupQueueD s_queue[kThreads / 32];
     if (threadIdx.x == 0)
         s_go = gate(W->ctl) ? 1 : 0;
     __syncthreads();
@@ -1584,7 +1597,13 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
     Rec *__restrict__ best = W->best;
     uint32_t *winbits = W->winbits;
     Ctl *ctl = W->ctl;
-    LookupQueue &qu = s_queue[threadIdx.x >> 5];
+    LookupQueueD &qd = s_queue[threadIdx.x >> 5];
+    // a batched solve walks the list of the running matrices' tiles
+    const int32_t steps = kBatch ? *W->bw.tlist_n : ntiles;
+    const int32_t *__restrict__ tlist = W->bw.tlist;
+    const int32_t *__restrict__ tilemat = W->bw.tilemat;
+    const int32_t *__restrict__ colmat = W->bw.colmat;
+    const int32_t *__restrict__ mdone = W->bw.mdone;
 
     const int lane = threadIdx.x & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
@@ -1596,107 +1615,129 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
 
     auto flush = [&](int k) {
         __syncwarp();
-        resolve_lookups<kLookup>(qu, qhead, k, lane, rowidx, wv, wm, htab, bloom, trowptr,
+        resolve_lookups<kLookup>(qd, qhead, k, lane, rowidx, wv, wm, htab, bloom, trowptr,
                                  tpos, rrange, nnz, W->n, best, winbits, ctl, n_found, n_pos);
         __syncwarp();
         qhead = (qhead + k) & (kQueue - 1);
         qn -= k;
     };
 
-    const int32_t t0 = s_go ? (int32_t)(gtid() >> 5) : ntiles;
-    // stage P: loads of a round's tiles (first column, start bits, row index)
-    int32_t pc0[kU], pi[kU];
-    uint32_t pmask[kU];
-    // stage M: columns, rows and the loads of m_j in flight
-    int32_t mj_[kU], mi_[kU], mm_[kU];
-    // stage R: the row records in flight (and, with row marking, the mark of m_j)
-    int32_t rj[kU], ri[kU], rm[kU];
-    unsigned long long rsg[kU], rmark[kU];
-    int32_t rcs[kU];  // row marking: first position of column m_i
-    bool rcand[kU];
+    // slot set s, tile u: row i, column (the tile's first column before the
+    // column step), start bits then m_j, the signature, the candidate flag
+    int32_t si[3][kU], sj[3][kU], sx[3][kU];
+    int32_t stile[3][kU];  // batched solve: the tile of the walk's entry
+    unsigned long long ssig[3][kU], smark[3][kU];
+    int32_t scs[3][kU];
+    bool scand[3][kU];
 
-    auto load_p = [&](int32_t tr) {
+    // stage 1: tile loads of the round starting at tile tr into slot s
+    auto st_load = [&](int s, int32_t tr) {
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int32_t tu = tr + u * nwarps;
-            pc0[u] = 0;
-            pmask[u] = 1u;
-            pi[u] = 0;
-            if (tu < ntiles) {
-                pc0[u] = __ldg(tile_col + tu);
-                pmask[u] = __ldg(starts + tu);
-                const int32_t pp = tu * kTile + lane;
-                pi[u] = pp < nnz ? __ldcs(rowidx + pp) : 0;
+            const int32_t xu = tr + u * nwarps;
+            const int32_t tu = kBatch ? (xu < steps ? __ldg(tlist + xu) : ntiles) : xu;
+            if (kBatch)
+                stile[s][u] = tu;
+            const int32_t tl = tu < ntiles ? tu : ntiles;  // in bounds
+            sj[s][u] = __ldg(tile_col + tl);
+            sx[s][u] = (int32_t)__ldg(starts + tl);
+            const int32_t p = tu * kTile + lane;
+            si[s][u] = p < nnz ? __ldcs(rowidx + p) : 0;
+        }
+    };
+    // stage 2: columns, and the loads of m_j
+    auto st_cols = [&](int s, int32_t tr) {
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int32_t tu = kBatch ? stile[s][u] : tr + u * nwarps;
+            const int32_t p = tu * kTile + lane;
+            bool valid = p < nnz;
+            const int32_t j = lane_column(sj[s][u], (uint32_t)sx[s][u], lane);
+            if (kBatch && valid) {
+                // lanes of finished matrices take no part
+                const int32_t tm = __ldg(tilemat + tu);
+                valid = (tm & kTileSingle) ? !__ldg(mdone + (tm & ~kTileSingle))
+                                           : !__ldg(mdone + __ldg(colmat + j));
+            }
+            const bool ok = valid && AWPM_IN(ctl, j, W->n) && AWPM_IN(ctl, si[s][u], W->n);
+            sj[s][u] = ok ? j : -1;
+            sx[s][u] = ok ? ld_i32_last(mc + j, pol) : 0x7fffffff;
+        }
+    };
+    // stage 3: candidate test, and the signature loads
+    auto st_cand = [&](int s) {
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            bool c = sj[s][u] >= 0 && si[s][u] > sx[s][u];
+            if (c && !AWPM_IN(ctl, sx[s][u], W->n))
+                c = false;
+            scand[s][u] = c;
+            ssig[s][u] = 0ull;
+            if (c) {
+                ++n_cand;
+                ssig[s][u] = ld_u64_last(rsig + si[s][u], pol);
+                if (kLookup == AWPM_LOOKUP_ROWMARK) {
+                    scs[s][u] = __ldg(&rrange[si[s][u]].s);
+                    smark[s][u] = __ldg(rowsig + sx[s][u]);
+                }
             }
         }
     };
-    auto p_to_m = [&](int32_t tr) {
+    // stage 4: signature test, passing requests queued
+    auto st_test = [&](int s, int32_t tr) {
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int32_t tu = tr + u * nwarps;
-            const bool valid = tu < ntiles && tu * kTile + lane < nnz;
-            mi_[u] = valid ? pi[u] : 0;
-            mj_[u] = valid ? lane_column(pc0[u], pmask[u], lane) : -1;
-            const bool ok = valid && AWPM_IN(ctl, mj_[u], W->n) && AWPM_IN(ctl, mi_[u], W->n);
-            mj_[u] = ok ? mj_[u] : -1;
-            mm_[u] = ok ? ld_i32_last(mc + mj_[u], pol) : 0x7fffffff;
-        }
-    };
-
-    load_p(t0);
-    p_to_m(t0);
-    load_p(t0 + stride);
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-        rcand[u] = false;
-        rj[u] = ri[u] = rm[u] = 0;
-        rsg[u] = 0ull;
-        rcs[u] = 0;
-        rmark[u] = 0ull;
-    }
-    for (int32_t tr = t0;; tr += stride) {
-        // R: signature tests of the previous round, passing requests queued
-        const int32_t tprev = tr - stride;
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const bool pass = rcand[u] && sig_has(rsg[u], rm[u]) &&
-                              (kLookup != AWPM_LOOKUP_ROWMARK || sig_has(rmark[u], rcs[u]));
+            const bool pass = scand[s][u] && sig_has(ssig[s][u], sx[s][u]) &&
+                              (kLookup != AWPM_LOOKUP_ROWMARK ||
+                               sig_has(smark[s][u], scs[s][u]));
             const unsigned need = __ballot_sync(FULL_MASK, pass);
-            if (pass) {
-                const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
-                qu.j[x] = rj[u];
-                qu.p[x] = (tprev + u * nwarps) * kTile + lane;
-                qu.i[x] = ri[u];
-                qu.mj[x] = rm[u];
-            }
+            const int x = pass ? ((qhead + qn + __popc(need & lanes_below)) & (kQueue - 1))
+                               : kQueue + lane;
+            qd.j[x] = sj[s][u];
+            qd.p[x] = (kBatch ? stile[s][u] : tr + u * nwarps) * kTile + lane;
+            qd.i[x] = si[s][u];
+            qd.mj[x] = sx[s][u];
             qn += __popc(need);
             if (qn >= 32)
                 flush(32);
         }
-        if (tr >= ntiles)
-            break;
-        // M: candidates of this round, their row records requested
+    };
+
+    const int32_t t0 = s_go ? (int32_t)(gtid() >> 5) : steps;
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            rj[u] = mj_[u];
-            ri[u] = mi_[u];
-            rm[u] = mm_[u];
-            rcand[u] = mj_[u] >= 0 && mi_[u] > mm_[u];
-            if (rcand[u] && !AWPM_IN(ctl, mm_[u], W->n))
-                rcand[u] = false;
-            if (rcand[u]) {
-                ++n_cand;
-                rsg[u] = ld_u64_last(rsig + mi_[u], pol);
-                if (kLookup == AWPM_LOOKUP_ROWMARK) {
-                    rcs[u] = __ldg(&rrange[mi_[u]].s);
-                    rmark[u] = __ldg(rowsig + mm_[u]);
-                }
-            }
+            scand[s][u] = false;
+            ssig[s][u] = smark[s][u] = 0ull;
+            scs[s][u] = 0;
         }
-        // P -> M for the next round, then the loads of the round after it
-        p_to_m(tr + stride);
-        load_p(tr + 2 * stride);
+    // prologue: round t0 through stage 3, round t0 + stride through stage 2,
+    // round t0 + 2 stride through stage 1
+    st_load(0, t0);
+    st_cols(0, t0);
+    st_load(1, t0 + stride);
+    st_cand(0);
+    st_cols(1, t0 + stride);
+    st_load(2, t0 + 2 * stride);
+    // steady state: each step tests round tr, requests round tr + stride's
+    // signatures, makes round tr + 2 stride's columns, loads round tr + 3 stride
+#define AWPM_ROT_STEP(A, B, C)                                                      \
+    {                                                                               \
+        if (tr >= steps)                                                            \
+            break;                                                                  \
+        st_test(A, tr);                                                             \
+        st_cand(B);                                                                 \
+        st_cols(C, tr + 2 * stride);                                                \
+        st_load(A, tr + 3 * stride);                                                \
+        tr += stride;                                                               \
     }
+    for (int32_t tr = t0;;) {
+        AWPM_ROT_STEP(0, 1, 2)
+        AWPM_ROT_STEP(1, 2, 0)
+        AWPM_ROT_STEP(2, 0, 1)
+    }
+#undef AWPM_ROT_STEP
     if (qn > 0)
         flush(qn);
     block_add_u64((unsigned long long)n_cand, &ctl->candidates);
@@ -3002,12 +3043,19 @@ static int bps_clamp(const void *f)
 template <bool kWide>
 static const void *search_fn(int lookup, bool batch)
 {
-    if (!batch && search_pipe()) {
+    if (search_pipe()) {
+        if (batch) {
+            if (lookup == AWPM_LOOKUP_ROWMARK)
+                return (const void *)k_search_pipe<AWPM_LOOKUP_ROWMARK, kWide, true>;
+            if (lookup == AWPM_LOOKUP_HASH)
+                return (const void *)k_search_pipe<AWPM_LOOKUP_HASH, kWide, true>;
+            return (const void *)k_search_pipe<AWPM_LOOKUP_BSEARCH, kWide, true>;
+        }
         if (lookup == AWPM_LOOKUP_ROWMARK)
-            return (const void *)k_search_pipe<AWPM_LOOKUP_ROWMARK, kWide>;
+            return (const void *)k_search_pipe<AWPM_LOOKUP_ROWMARK, kWide, false>;
         if (lookup == AWPM_LOOKUP_HASH)
-            return (const void *)k_search_pipe<AWPM_LOOKUP_HASH, kWide>;
-        return (const void *)k_search_pipe<AWPM_LOOKUP_BSEARCH, kWide>;
+            return (const void *)k_search_pipe<AWPM_LOOKUP_HASH, kWide, false>;
+        return (const void *)k_search_pipe<AWPM_LOOKUP_BSEARCH, kWide, false>;
     }
     if (lookup == AWPM_LOOKUP_ROWMARK)
         return batch ? (const void *)k_search<AWPM_LOOKUP_ROWMARK, true, kWide>
