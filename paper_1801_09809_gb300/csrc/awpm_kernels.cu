@@ -530,12 +530,15 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
                 const unsigned hi = __reduce_or_sync(FULL_MASK, (unsigned)(v >> 32));
                 v = ((unsigned long long)hi << 32) | lo;
             } else {
+                // start bits after this lane (none for lane 31)
+                const uint32_t after = __funnelshift_rc(mask[u], 0u, lane + 1);
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
                     const unsigned long long ov = __shfl_down_sync(FULL_MASK, v, off);
-                    // lane + off is in the same column: no column starts in between
-                    if (lane + off < 32 &&
-                        ((mask[u] >> (lane + 1)) & ((1u << off) - 1u)) == 0u)
+                    // lane + off is in the same column: no column starts in
+                    // between (past lane 31 the shuffle returns the lane's own
+                    // value, and OR-ing it changes nothing)
+                    if ((after & ((1u << off) - 1u)) == 0u)
                         v |= ov;
                 }
             }
