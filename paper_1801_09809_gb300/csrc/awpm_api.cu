@@ -262,10 +262,14 @@ int build_graph(awpm_ctx *c, const Shape &sh, cudaGraphExec_t *out)
         }
         sb.last = n_inner;
         launch_greedy_select_end_and_flip(d, sh, sb);
+    } else if (!sh.batch) {
+        // the flip's last block ends the pass (no control kernel)
+        launch_select_flip_control_graph(d, sh, h, sb);
     } else {
         launch_select_and_flip(d, sh, sb);
     }
-    launch_control(d, sh, true, h, sb);
+    if (sh.batch || sh.select == AWPM_SELECT_GREEDY)
+        launch_control(d, sh, true, h, sb);
     if (sb.err != cudaSuccess) {
         note_cuda_error(sb.err, "pass body nodes", __LINE__);
         rc = AWPM_ERR_CUDA;

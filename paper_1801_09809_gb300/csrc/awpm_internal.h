@@ -95,6 +95,8 @@ struct Ctl {
     int32_t phase_levels;        // maximum matching: levels of the running phase
     int32_t level_tiles;         // maximum matching: tiles listed for the next level
     int32_t level_listed;        // maximum matching: tiles listed for this level
+    uint32_t flip_done;          // blocks done with the pass's flip (graph form)
+    uint32_t pad_fd;
     uint32_t level_done;         // maximum matching: blocks done with the level's last step
     int32_t touched;             // maximum matching: rows listed in mtouch this level
     unsigned long long levels;   // maximum matching: search levels run
@@ -254,6 +256,10 @@ void launch_init(const Work *d, const Shape &sh, Sink &k);
 void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k);
 void launch_search(const Work *d, const Shape &sh, Sink &k);
 void launch_select_and_flip(const Work *d, const Shape &sh, Sink &k);
+// Graph form for single problems with Step D: the selection and the flip,
+// whose last block also ends the pass (no separate control kernel).
+void launch_select_flip_control_graph(const Work *d, const Shape &sh,
+                                      cudaGraphConditionalHandle h, Sink &k);
 // Greedy selection: the kernels before the rounds (keys, undecided set,
 // condition of the rounds' loop), one round (the loop condition is set at
 // its end), and the kernels after (records for the flip).  With graph ==

@@ -202,11 +202,13 @@ constexpr int32_t kBloomMin = 32;
 __device__ __forceinline__ void bloom_key(int32_t r, int32_t s, int32_t e, uint32_t &word,
                                           uint32_t &bits)
 {
-    const uint32_t h = row_mix(r);
+    // multiplicative hashes (top bits), with constants other than the
+    // column signature's so the two filters reject different rows
+    const uint32_t h = (uint32_t)r * 0x85EBCA6Bu;
     const uint32_t w0 = (uint32_t)s >> 2;
     const uint32_t nw = (((uint32_t)e - 1u) >> 2) - w0 + 1u;
     word = w0 + __umulhi(h, nw);
-    const uint32_t h2 = h * 0x9E3779B1u;
+    const uint32_t h2 = (uint32_t)r * 0xC2B2AE35u;
     bits = (1u << (h2 >> 27)) | (1u << ((h2 >> 22) & 31u)) | (1u << ((h2 >> 17) & 31u));
 }
 
@@ -365,6 +367,7 @@ __global__ void k_reset(const Work *__restrict__ W)
         c->live = 0;
         c->max_passes = w.max_passes;
         c->pass_flips = 0ull;
+        c->flip_done = 0u;
         c->cycles = 0ull;
         c->candidates = 0ull;
         c->found = 0ull;
@@ -428,6 +431,36 @@ __global__ void k_check_colptr(const Work *__restrict__ W)
             raise_err(w.ctl, kErrInvalid);
         else if (j < w.n && w.colptr[j + 1] == c)
             raise_err(w.ctl, kErrNotPerfect);
+    }
+}
+
+// The column-pointer check and the start marks in one pass over colptr (the
+// solve's initialisation): a column's start bit and tile entries are written
+// only when its range lies inside [0, nnz], so a bad colptr (reported as
+// AWPM_ERR_INVALID_ARG, which gates every later kernel) writes nothing out
+// of range.
+__global__ void k_check_mark(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    for (int64_t j = gtid(); j <= w.n; j += gstride()) {
+        const int32_t c = w.colptr[j];
+        const int32_t e = j < w.n ? w.colptr[j + 1] : c;
+        const bool bad = (j == 0 && c != 0) || (j < w.n && e < c) || (j == w.n && c != w.nnz);
+        if (bad) {
+            raise_err(w.ctl, kErrInvalid);
+            continue;
+        }
+        if (j == w.n)
+            continue;
+        if (e == c) {
+            raise_err(w.ctl, kErrNotPerfect);
+            continue;
+        }
+        if (c < 0 || e > w.nnz)
+            continue;  // (reported by the check of the last pointer)
+        atomicOr(&w.starts[c >> 5], 1u << (c & 31));
+        for (int64_t t = ((int64_t)c + kTile - 1) / kTile; t * kTile < e; ++t)
+            w.tile_col[t] = (int32_t)j;
     }
 }
 
@@ -1844,9 +1877,8 @@ __global__ void k_select(const Work *__restrict__ W)
 // empty for the next pass.  Winners are taken as in k_select; in a batched
 // solve the flips of a round are counted per matrix with one atomic per
 // matrix.
-__global__ void k_flip(const Work *__restrict__ W)
+__device__ __forceinline__ unsigned long long flip_body(const Work &w)
 {
-    const Work &w = *W;
     unsigned long long flips = 0;
     if (gate(w.ctl)) {
         const int lane = threadIdx.x & 31;
@@ -1893,7 +1925,13 @@ __global__ void k_flip(const Work *__restrict__ W)
             });
         }
     }
-    block_add_u64(flips, &w.ctl->pass_flips);
+    return flips;
+}
+
+__global__ void k_flip(const Work *__restrict__ W)
+{
+    const Work &w = *W;
+    block_add_u64(flip_body(w), &w.ctl->pass_flips);
 }
 
 // End of a pass (Algorithm 2): count it, stop when nothing was flipped or
@@ -1927,6 +1965,24 @@ __global__ void k_control(const Work *__restrict__ W)
 __global__ void k_control_graph(const Work *__restrict__ W, cudaGraphConditionalHandle h)
 {
     cudaGraphSetConditional(h, control_step(W->ctl) ? 1u : 0u);
+}
+
+// The flip in the graph form of a single problem's pass: the block that
+// finishes last (its count of finished blocks orders it after every other
+// block's flip count) ends the pass and sets the WHILE condition.
+__global__ void k_flip_graph(const Work *__restrict__ W, cudaGraphConditionalHandle h)
+{
+    const Work &w = *W;
+    block_add_u64(flip_body(w), &w.ctl->pass_flips);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&w.ctl->flip_done, 1u);
+        if (prev == gridDim.x - 1) {
+            __threadfence();
+            w.ctl->flip_done = 0u;
+            cudaGraphSetConditional(h, control_step(w.ctl) ? 1u : 0u);
+        }
+    }
 }
 
 // End of a pass for every matrix still running: count the pass, stop the
@@ -2213,6 +2269,7 @@ __global__ void k_gm_reset(const Work *__restrict__ W)
         c->live = 0;
         c->max_passes = w.max_passes;
         c->pass_flips = 0ull;
+        c->flip_done = 0u;
         c->cycles = 0ull;
         c->candidates = 0ull;
         c->found = 0ull;
@@ -2983,8 +3040,7 @@ void launch_init(const Work *d, const Shape &sh, Sink &k)
 {
     void *a[] = {(void *)&d};
     k.launch((const void *)k_reset, util_grid(sh), kThreads, a);
-    k.launch((const void *)k_check_colptr, init_grid(sh), kThreads, a);
-    k.launch((const void *)k_mark_starts, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_check_mark, init_grid(sh), kThreads, a);
     k.launch((const void *)k_entries, init_tile_grid(sh), kThreads, a);
     if (sh.batch)
         k.launch((const void *)k_batch_cols, init_grid(sh), kThreads, a);
@@ -3126,6 +3182,15 @@ void launch_greedy_select_end_and_flip(const Work *d, const Shape &sh, Sink &k)
     void *a[] = {(void *)&d};
     k.launch((const void *)k_ps_end, tile_grid(sh), kThreads, a);
     k.launch((const void *)k_flip, tile_grid(sh), kThreads, a);
+}
+
+void launch_select_flip_control_graph(const Work *d, const Shape &sh,
+                                      cudaGraphConditionalHandle h, Sink &k)
+{
+    void *a[] = {(void *)&d};
+    void *ah[] = {(void *)&d, (void *)&h};
+    k.launch((const void *)k_select, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_flip_graph, tile_grid(sh), kThreads, ah);
 }
 
 void launch_select_and_flip(const Work *d, const Shape &sh, Sink &k)
