@@ -490,14 +490,17 @@ __global__ void k_mark_starts(const Work *__restrict__ W)
 // either, so twice the bytes are in flight.  Column numbers come from the
 // start bitmap, exact once no column is empty (empty columns were reported by
 // the column-pointer check and always stay below n).
-__global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W)
+#ifndef AWPM_ENTRIES_U
+#define AWPM_ENTRIES_U 2
+#endif
+#ifndef AWPM_ENTRIES_MINB
+#define AWPM_ENTRIES_MINB 6
+#endif
+__global__ void __launch_bounds__(kThreads, AWPM_ENTRIES_MINB) k_entries(const Work *__restrict__ W)
 {
     const Work &w = *W;
     if (w.ctl->err & kErrInvalid)
         return;
-#ifndef AWPM_ENTRIES_U
-#define AWPM_ENTRIES_U 2
-#endif
     constexpr int kU = AWPM_ENTRIES_U;
     const int lane = threadIdx.x & 31;
     // 32-bit tile arithmetic: ntiles < 2^26, positions < 2^31
@@ -595,7 +598,8 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
 //     (a 4-byte scattered store per column; mr stays in L2 while it fills);
 //     checks that every mate_in[j] is a row number and a stored entry of
 //     column j (the entry pass left wm[j] = NaN where (mate_in[j], j) is not
-//     stored);
+//     stored); and the matched weights' sum, one partial per block into
+//     wpart (the grid is at most kWsumBlocks), summed by k_wsum_final;
 //   k_init_rows (per row r): the row record of r from column mr[r] (gathers
 //     of that column's range, signature and matched weight; the records are
 //     written row by row, whole sectors at a time), and the check that every
@@ -604,12 +608,16 @@ __global__ void __launch_bounds__(kThreads) k_entries(const Work *__restrict__ W
 __global__ void k_init_mates(const Work *__restrict__ W)
 {
     const Work &w = *W;
-    if (w.ctl->err)
+    if (w.ctl->err) {
+        if (threadIdx.x == 0)
+            w.wpart[blockIdx.x] = 0.0;
         return;
+    }
     constexpr int kU = 8;
     const int64_t stride = gstride();
     const int32_t n = w.n;
     unsigned bits = 0;
+    double sum = 0.0;
     for (int64_t j0 = gtid(); j0 < n; j0 += kU * stride) {
         int32_t r[kU];
         double x[kU];
@@ -631,11 +639,15 @@ __global__ void k_init_mates(const Work *__restrict__ W)
                 continue;
             }
             w.mr[r[u]] = (int32_t)j;
+            sum += x[u];
         }
     }
     bits = __reduce_or_sync(FULL_MASK, bits);
     if ((threadIdx.x & 31) == 0 && bits)
         raise_err(w.ctl, bits);
+    sum = block_sum_f64(sum);
+    if (threadIdx.x == 0)
+        w.wpart[blockIdx.x] = sum;
 }
 
 __global__ void k_init_rows(const Work *__restrict__ W)
@@ -719,10 +731,14 @@ __global__ void k_wsum_partial(const Work *__restrict__ W)
         w.wpart[blockIdx.x] = s;
 }
 
-__global__ void k_wsum_final(const Work *__restrict__ W, int out)
+// The sum of the first `parts` block partials (parts <= blockDim.x); 0 after
+// an error.
+__global__ void k_wsum_final(const Work *__restrict__ W, int out, int parts)
 {
     const Work &w = *W;
-    const double s = block_sum_f64(w.wpart[threadIdx.x]);
+    double s = block_sum_f64((int)threadIdx.x < parts ? w.wpart[threadIdx.x] : 0.0);
+    if (w.ctl->err)
+        s = 0.0;
     if (threadIdx.x == 0) {
         if (out)
             w.ctl->weight_out = s;
@@ -1201,10 +1217,8 @@ __device__ __forceinline__ int32_t coop_last_below(const int32_t *__restrict__ a
 // lanes of a tile that need it.
 constexpr int kQueue = 64;
 struct LookupQueue {
-    int32_t j[kQueue];    // root column
-    int32_t p[kQueue];    // position of (i, j)
-    int32_t i[kQueue];    // row i
-    int32_t mj[kQueue];   // m_j, the row looked up in column m_i
+    int2 im[kQueue];  // row i, and m_j (the row looked up in column m_i)
+    int2 jp[kQueue];  // root column j, and the position of (i, j)
 };
 
 // Resolve the queued requests head .. head + k - 1 (k <= 32, lane x takes
@@ -1229,13 +1243,14 @@ __device__ __forceinline__ void resolve_lookups(
 {
     const int x = (head + lane) & (kQueue - 1);
     const bool act = lane < k;
-    const int32_t mj = act ? qu.mj[x] : 0;
+    const int2 im = act ? qu.im[x] : make_int2(0, 0);
+    const int32_t mj = im.y;
     // column m_i's rows rowidx[lo, lo + len) and w(i, m_i), from the row
     // record of i
     int32_t lo = 0, len = 0;
     double wmi = 0.0;
-    if (act && AWPM_IN(ctl, qu.i[x], nrows)) {
-        const RowRange rg = ld_range(rrange + qu.i[x]);
+    if (act && AWPM_IN(ctl, im.x, nrows)) {
+        const RowRange rg = ld_range(rrange + im.x);
         lo = rg.s;
         len = rg.e - rg.s;
         wmi = rg.w;
@@ -1338,14 +1353,13 @@ __device__ __forceinline__ void resolve_lookups(
             }
         }
     }
-    if (q >= 0 && !(AWPM_IN(ctl, q, nnz) && AWPM_IN(ctl, qu.p[x], nnz) &&
-                    AWPM_IN(ctl, qu.j[x], nrows)))
+    const int2 jp = q >= 0 ? qu.jp[x] : make_int2(0, 0);
+    if (q >= 0 && !(AWPM_IN(ctl, q, nnz) && AWPM_IN(ctl, jp.y, nnz) && AWPM_IN(ctl, jp.x, nrows)))
         q = -1;
     if (q >= 0) {
         ++n_found;
-        const int32_t j = qu.j[x];
-        const int32_t p = qu.p[x];
-        const int32_t i = qu.i[x];
+        const int32_t j = jp.x;
+        const int32_t p = jp.y;
         const double wij = __ldg(wv + p);
         const double wq = __ldg(wv + q);
         const double gg = ((wij + wq) - wmi) - __ldg(wm + j);
@@ -1541,10 +1555,8 @@ __global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
                 const unsigned need = __ballot_sync(FULL_MASK, pass);
                 if (pass) {
                     const int x = (qhead + qn + __popc(need & lanes_below)) & (kQueue - 1);
-                    qu.j[x] = jv[u];
-                    qu.p[x] = pv[u];
-                    qu.i[x] = iv[u];
-                    qu.mj[x] = mjv[u];
+                    qu.im[x] = make_int2(iv[u], mjv[u]);
+                    qu.jp[x] = make_int2(jv[u], pv[u]);
                 }
                 qn += __popc(need);
                 if (qn >= 32)
@@ -1599,10 +1611,8 @@ struct PipeCfg {
 // The lookup queue with a discard slot per lane after the 64 ring slots.
 constexpr int kQueueDiscard = kQueue + 32;
 struct LookupQueueD {
-    int32_t j[kQueueDiscard];
-    int32_t p[kQueueDiscard];
-    int32_t i[kQueueDiscard];
-    int32_t mj[kQueueDiscard];
+    int2 im[kQueueDiscard];
+    int2 jp[kQueueDiscard];
 };
 
 template <int kLookup, bool kWide, bool kBatch>
@@ -1729,10 +1739,8 @@ __global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
             const unsigned need = __ballot_sync(FULL_MASK, pass);
             const int x = pass ? ((qhead + qn + __popc(need & lanes_below)) & (kQueue - 1))
                                : kQueue + lane;
-            qd.j[x] = sj[s][u];
-            qd.p[x] = (kBatch ? stile[s][u] : tr + u * nwarps) * kTile + lane;
-            qd.i[x] = si[s][u];
-            qd.mj[x] = sx[s][u];
+            qd.im[x] = make_int2(si[s][u], sx[s][u]);
+            qd.jp[x] = make_int2(sj[s][u], (kBatch ? stile[s][u] : tr + u * nwarps) * kTile + lane);
             qn += __popc(need);
             if (qn >= 32)
                 flush(32);
@@ -3015,6 +3023,18 @@ static inline unsigned init_tile_grid(const Shape &sh)
     return (unsigned)(sh.num_sms * 32);
 }
 
+// The mate initialisation, which leaves one partial sum per block in wpart:
+// its resident blocks (80 registers: three blocks of 256 per SM), at most
+// kWsumBlocks.
+#ifndef AWPM_SUM_BPS
+#define AWPM_SUM_BPS 3
+#endif
+static inline unsigned sum_grid(const Shape &sh)
+{
+    const int g = sh.num_sms * AWPM_SUM_BPS;
+    return (unsigned)(g < kWsumBlocks ? g : kWsumBlocks);
+}
+
 void Sink::launch(const void *func, unsigned grid, unsigned block, void **args)
 {
     if (err != cudaSuccess)
@@ -3044,7 +3064,7 @@ void launch_init(const Work *d, const Shape &sh, Sink &k)
     k.launch((const void *)k_entries, init_tile_grid(sh), kThreads, a);
     if (sh.batch)
         k.launch((const void *)k_batch_cols, init_grid(sh), kThreads, a);
-    k.launch((const void *)k_init_mates, init_grid(sh), kThreads, a);
+    k.launch((const void *)k_init_mates, sum_grid(sh), kThreads, a);
     k.launch((const void *)k_init_rows, init_grid(sh), kThreads, a);
     if (sh.batch) {
         k.launch((const void *)k_batch_check, init_tile_grid(sh), kThreads, a);
@@ -3070,13 +3090,20 @@ void launch_init(const Work *d, const Shape &sh, Sink &k)
     }
 }
 
+// The matched weights' sum (the input matching's when !out).  The mate
+// initialisation of a single solve already left its partials in wpart;
+// otherwise k_wsum_partial writes them.
 void launch_weight_sum(const Work *d, const Shape &sh, bool out, Sink &k)
 {
     int o = out ? 1 : 0;
+    const bool from_init = !out && !sh.batch;
+    int parts = from_init ? (int)sum_grid(sh) : kWsumBlocks;
     void *a[] = {(void *)&d};
     void *ao[] = {(void *)&d, (void *)&o};
-    k.launch((const void *)k_wsum_partial, kWsumBlocks, kWsumThreads, a);
-    k.launch((const void *)k_wsum_final, 1, kWsumBlocks, ao);
+    void *af[] = {(void *)&d, (void *)&o, (void *)&parts};
+    if (!from_init)
+        k.launch((const void *)k_wsum_partial, kWsumBlocks, kWsumThreads, a);
+    k.launch((const void *)k_wsum_final, 1, kWsumBlocks, af);
     if (sh.batch)
         k.launch((const void *)k_batch_wsum, util_grid(sh), kThreads, ao);
 }
@@ -3184,20 +3211,30 @@ void launch_greedy_select_end_and_flip(const Work *d, const Shape &sh, Sink &k)
     k.launch((const void *)k_flip, tile_grid(sh), kThreads, a);
 }
 
+// Step D's kernels take 32 words of the winner bitmap per warp; a single
+// problem of the large class (two search waves: n up to about 5 M in one
+// round) gets four blocks per SM, a smaller one one block per SM.  Late
+// passes have few winners, so the kernels cost about their launch and a
+// read of the bitmap; blocks past the bitmap's end would only add to that.
+static inline unsigned winner_grid(const Shape &sh)
+{
+    return sh.batch ? tile_grid(sh) : (unsigned)(sh.num_sms * (sh.search_waves > 1 ? 4 : 1));
+}
+
 void launch_select_flip_control_graph(const Work *d, const Shape &sh,
                                       cudaGraphConditionalHandle h, Sink &k)
 {
     void *a[] = {(void *)&d};
     void *ah[] = {(void *)&d, (void *)&h};
-    k.launch((const void *)k_select, tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_flip_graph, tile_grid(sh), kThreads, ah);
+    k.launch((const void *)k_select, winner_grid(sh), kThreads, a);
+    k.launch((const void *)k_flip_graph, winner_grid(sh), kThreads, ah);
 }
 
 void launch_select_and_flip(const Work *d, const Shape &sh, Sink &k)
 {
     void *a[] = {(void *)&d};
-    k.launch((const void *)k_select, tile_grid(sh), kThreads, a);
-    k.launch((const void *)k_flip, tile_grid(sh), kThreads, a);
+    k.launch((const void *)k_select, winner_grid(sh), kThreads, a);
+    k.launch((const void *)k_flip, winner_grid(sh), kThreads, a);
 }
 
 void launch_control(const Work *d, const Shape &sh, bool graph, cudaGraphConditionalHandle h,
