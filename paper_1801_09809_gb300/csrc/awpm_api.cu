@@ -583,6 +583,7 @@ void ctx_trim(awpm_ctx *c)
         cudaStreamSynchronize(c->stream);
     for (DevBuf *b : bufs)
         release(c, *b);
+    c->rec_clean = 0;
     cudaGetLastError();
 }
 
@@ -763,8 +764,11 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     AWPM_TRY(ensure(c, c->rr, sizeof(RowRange) * n));
     AWPM_TRY(ensure(c, c->rsig, sizeof(unsigned long long) * n));
     AWPM_TRY(ensure(c, c->colsig, sizeof(unsigned long long) * n));
+    const void *best_was = c->best.p, *dsel_was = c->dsel.p;
     AWPM_TRY(ensure(c, c->best, sizeof(Rec) * n));
     AWPM_TRY(ensure(c, c->dsel, sizeof(Sel) * n));
+    if (c->best.p != best_was || c->dsel.p != dsel_was)
+        c->rec_clean = 0;
     AWPM_TRY(ensure(c, c->winbits, sizeof(uint32_t) * ((size_t)n / 32 + 1)));
     AWPM_TRY(ensure(c, c->wkey, sizeof(int32_t) * n));
     AWPM_TRY(ensure(c, c->tile_col, sizeof(int32_t) * ((size_t)ntiles + 1)));
@@ -849,6 +853,13 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     }
     wk.best = (Rec *)c->best.p;
     wk.dsel = (Sel *)c->dsel.p;
+    {
+        // single solves with Step D's selection leave the records empty
+        const bool keeps_clean = count == 0 && !r.search_only && !ps;
+        wk.rec_clean = keeps_clean && (int64_t)n <= c->rec_clean ? 1 : 0;
+        pd.rec_clean_after = keeps_clean ? std::max<int64_t>(n, c->rec_clean) : 0;
+        c->rec_clean = 0;
+    }
     wk.winbits = (uint32_t *)c->winbits.p;
     wk.wkey = (int32_t *)c->wkey.p;
     wk.tile_col = (int32_t *)c->tile_col.p;
@@ -975,6 +986,7 @@ int ctx_finish(awpm_ctx *c, awpm_stats *st, awpm_stats *per_matrix)
     const int rc = code_of(h.err);
     if (rc != AWPM_OK)
         return rc;
+    c->rec_clean = pd.rec_clean_after;
     double ms_search = 0.0;
     if (pd.timed) {
         for (int t = 0; t < h.iterations && t < pd.passes_enqueued; ++t) {

@@ -72,6 +72,7 @@ struct Pending {
     bool active = false;
     int32_t n = 0, nnz = 0, count = 0, lookup = 0;
     bool search_only = false, timed = false, trivial = false;
+    int64_t rec_clean_after = 0;  // the context's rec_clean once the solve ends without error
     int passes_enqueued = 0;
     std::vector<int32_t> n_off;  // host copy of the batch offsets
     int tune_cfg = -1;           // autotuner trial of this solve, or -1
@@ -106,6 +107,13 @@ struct awpm_ctx {
     size_t held = 0;
     size_t peak = 0;        // most device bytes held at once
     int32_t fail_after = -1;  // test hook: allocations left before one fails (-1: off)
+    // The Step-C and Step-D records (best, dsel) of columns [0, rec_clean) are
+    // known to be empty: a single solve with Step D's selection that ends
+    // without error clears every record it wrote (each pass's flip empties
+    // its winners' records), so the next solve's reset can skip them.  Zero
+    // while a solve is in flight, after an error, and when the buffers are
+    // reallocated or released.
+    int64_t rec_clean = 0;
     int search_bps[2][3][2] = {};  // [batch][lookup slot][wide]
     bool search_wide = true;      // default when the lookup is given explicitly
     // per-solve device workspace

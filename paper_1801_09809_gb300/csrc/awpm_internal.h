@@ -144,7 +144,7 @@ struct Work {
     int32_t ntiles;
     int32_t max_passes;
     int32_t lookup;     // AWPM_LOOKUP_BSEARCH, _HASH or _ROWMARK
-    int32_t pad;
+    int32_t rec_clean;  // the Step-C and Step-D records of columns [0, n) are all empty
     const int32_t *colptr;
     const int32_t *rowidx;
     const double *w;

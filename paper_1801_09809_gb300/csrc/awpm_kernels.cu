@@ -379,10 +379,13 @@ __global__ void k_reset(const Work *__restrict__ W)
             *w.bw.tlist_n = 0;
         }
     }
+    const bool rec = !w.rec_clean;
     for (int64_t j = gtid(); j < w.n; j += gstride()) {
         w.mr[j] = -1;
-        w.best[j] = Rec{0.0, 0, 0};
-        w.dsel[j] = Sel{0.0, 0, 0};
+        if (rec) {
+            w.best[j] = Rec{0.0, 0, 0};
+            w.dsel[j] = Sel{0.0, 0, 0};
+        }
         w.colsig[j] = 0ull;
         w.wm[j] = __longlong_as_double(kNaNBits);  // "no matched entry seen"
     }
