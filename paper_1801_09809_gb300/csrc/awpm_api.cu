@@ -854,8 +854,9 @@ int ctx_enqueue(awpm_ctx *c, const Request &r)
     wk.best = (Rec *)c->best.p;
     wk.dsel = (Sel *)c->dsel.p;
     {
-        // single solves with Step D's selection leave the records empty
-        const bool keeps_clean = count == 0 && !r.search_only && !ps;
+        // solves with Step D's selection (single or batched) leave the
+        // records empty: every pass's flip clears the records of its winners
+        const bool keeps_clean = !r.search_only && !ps;
         wk.rec_clean = keeps_clean && (int64_t)n <= c->rec_clean ? 1 : 0;
         pd.rec_clean_after = keeps_clean ? std::max<int64_t>(n, c->rec_clean) : 0;
         c->rec_clean = 0;

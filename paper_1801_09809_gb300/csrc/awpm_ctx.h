@@ -108,9 +108,9 @@ struct awpm_ctx {
     size_t peak = 0;        // most device bytes held at once
     int32_t fail_after = -1;  // test hook: allocations left before one fails (-1: off)
     // The Step-C and Step-D records (best, dsel) of columns [0, rec_clean) are
-    // known to be empty: a single solve with Step D's selection that ends
-    // without error clears every record it wrote (each pass's flip empties
-    // its winners' records), so the next solve's reset can skip them.  Zero
+    // known to be empty: a solve with Step D's selection that ends without
+    // error clears every record it wrote (each pass's flip empties its
+    // winners' records), so the next solve's reset can skip them.  Zero
     // while a solve is in flight, after an error, and when the buffers are
     // reallocated or released.
     int64_t rec_clean = 0;

@@ -232,7 +232,8 @@ struct Shape {
     int lookup;         // AWPM_LOOKUP_BSEARCH, _HASH or _ROWMARK
     bool batch;
     bool wide;          // search kernel takes four tiles per warp round (else one)
-    int search_waves;   // search grid = search_waves full waves of resident blocks
+    int search_waves;   // size class: 2 when there are at least 64 tiles per resident
+                        // search warp, else 1 (keys the cached graphs; Step D's grid)
     int select;         // AWPM_SELECT_STEP_D or AWPM_SELECT_GREEDY
 };
 

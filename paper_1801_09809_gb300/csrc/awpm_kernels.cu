@@ -3169,10 +3169,12 @@ bool default_search_wide()
     return true;
 }
 
+// The search grid is one wave of resident blocks: each warp walks its tiles
+// to the end (two, three, four and eight waves were measured slower on the
+// bench graph: the later waves' blocks start only as whole blocks finish).
 void launch_search(const Work *d, const Shape &sh, Sink &k)
 {
-    const unsigned grid = (unsigned)(sh.num_sms * (sh.search_bps > 0 ? sh.search_bps : 1) *
-                                     (sh.search_waves > 1 ? sh.search_waves : 1));
+    const unsigned grid = (unsigned)(sh.num_sms * (sh.search_bps > 0 ? sh.search_bps : 1));
     void *a[] = {(void *)&d};
     const void *f = sh.wide ? search_fn<true>(sh.lookup, sh.batch)
                             : search_fn<false>(sh.lookup, sh.batch);

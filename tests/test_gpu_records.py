@@ -59,7 +59,14 @@ def test_sequence_on_one_context(torch):
         out = np.empty(u.n, np.int32)
         awpm.awpm_improve_batch(ctx, len(graphs), n_off, u.colptr, u.rowidx, u.weight, u.mate,
                                 out)
-        check(ctx, s, torch)               # after a batched solve: cleared
+        orc = oracle.get()
+        for k, m in enumerate(gen.split(n_off, out)):
+            assert np.array_equal(m, orc.improve(graphs[k])[0]), k
+        awpm.awpm_improve_batch(ctx, len(graphs), n_off, u.colptr, u.rowidx, u.weight, u.mate,
+                                out)                 # its records left empty by the first
+        for k, m in enumerate(gen.split(n_off, out)):
+            assert np.array_equal(m, orc.improve(graphs[k])[0]), k
+        check(ctx, s, torch)               # after a batched solve: left empty
         check(ctx, s, torch, host=True)
     finally:
         awpm.awpm_destroy(ctx)
