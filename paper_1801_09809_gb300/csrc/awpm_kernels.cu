@@ -1388,15 +1388,31 @@ __device__ __forceinline__ void resolve_lookups(
 // resolve_lookups).  Step-C records (Algorithm 5) are combined by a 128-bit
 // compare-and-swap; `best` must be zero on entry: only positive records are
 // written.  In a batched solve, tiles of finished matrices are skipped.
+// Block size of the search kernels (each warp has its own lookup queue):
+// 512 threads for a single problem, 256 for a batched solve.  With the grid
+// one wave of resident blocks, the single problem's search measured a little
+// faster with larger blocks on the bench graph (0.267 ms per launch at 512
+// threads, 0.270 at 256, 0.271 at 128), the batched solve slower (21.4 ms
+// per batch at 512, 20.0 at 256).  The minimum blocks per SM below are given
+// in warps per SM, divided by the block's warps.
+#ifndef AWPM_SEARCH_THREADS
+#define AWPM_SEARCH_THREADS 512
+#endif
+template <bool kBatch>
+struct SearchBlock {
+    static constexpr int kThreads = kBatch ? 256 : AWPM_SEARCH_THREADS;
+    static constexpr int kWarps = kThreads / 32;
+};
 #ifndef AWPM_SEARCH_MINB_WIDE
-#define AWPM_SEARCH_MINB_WIDE 4
+#define AWPM_SEARCH_MINB_WIDE (32 / SearchBlock<kBatch>::kWarps)
 #endif
 template <int kLookup, bool kBatch, bool kWide>
-__global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
+__global__ void __launch_bounds__(SearchBlock<kBatch>::kThreads,
+                                  kWide ? AWPM_SEARCH_MINB_WIDE : 48 / SearchBlock<kBatch>::kWarps)
     k_search(const Work *__restrict__ W)
 {
     __shared__ int s_go;
-    __shared__ LookupQueue s_queue[kThreads / 32];
+    __shared__ LookupQueue s_queue[SearchBlock<kBatch>::kWarps];
     if (threadIdx.x == 0)
         s_go = gate(W->ctl) ? 1 : 0;
     __syncthreads();
@@ -1599,16 +1615,17 @@ __global__ void __launch_bounds__(kThreads, kWide ? AWPM_SEARCH_MINB_WIDE : 6)
 #ifndef AWPM_PIPE_U_NARROW
 #define AWPM_PIPE_U_NARROW 1
 #endif
-#ifndef AWPM_PIPE_MINB_WIDE
-#define AWPM_PIPE_MINB_WIDE 4
+#ifndef AWPM_PIPE_WARPS_WIDE
+#define AWPM_PIPE_WARPS_WIDE 32
 #endif
-#ifndef AWPM_PIPE_MINB_NARROW
-#define AWPM_PIPE_MINB_NARROW 5
+#ifndef AWPM_PIPE_WARPS_NARROW
+#define AWPM_PIPE_WARPS_NARROW 40
 #endif
 template <bool kWide>
 struct PipeCfg {
     static constexpr int kU = kWide ? AWPM_PIPE_U_WIDE : AWPM_PIPE_U_NARROW;
-    static constexpr int kMinBlocks = kWide ? AWPM_PIPE_MINB_WIDE : AWPM_PIPE_MINB_NARROW;
+    // resident warps per SM aimed at (the launch bound divides by the block's warps)
+    static constexpr int kWarpsPerSM = kWide ? AWPM_PIPE_WARPS_WIDE : AWPM_PIPE_WARPS_NARROW;
 };
 
 // The lookup queue with a discard slot per lane after the 64 ring slots.
@@ -1619,12 +1636,13 @@ struct LookupQueueD {
 };
 
 template <int kLookup, bool kWide, bool kBatch>
-__global__ void __launch_bounds__(kThreads, PipeCfg<kWide>::kMinBlocks)
+__global__ void __launch_bounds__(SearchBlock<kBatch>::kThreads,
+                                  PipeCfg<kWide>::kWarpsPerSM / SearchBlock<kBatch>::kWarps)
     k_search_pipe(const Work *__restrict__ W)
 {
     constexpr int kU = PipeCfg<kWide>::kU;
     __shared__ int s_go;
-    __shared__ LookupQueueD s_queue[kThreads / 32];
+    __shared__ LookupQueueD s_queue[SearchBlock<kBatch>::kWarps];
     if (threadIdx.x == 0)
         s_go = gate(W->ctl) ? 1 : 0;
     __syncthreads();
@@ -3158,7 +3176,14 @@ static const void *search_fn(int lookup, bool batch)
 
 int search_blocks_per_sm(int lookup, bool batch, bool wide)
 {
-    return bps_clamp(wide ? search_fn<true>(lookup, batch) : search_fn<false>(lookup, batch));
+    const void *f = wide ? search_fn<true>(lookup, batch) : search_fn<false>(lookup, batch);
+    const int threads = batch ? SearchBlock<true>::kThreads : SearchBlock<false>::kThreads;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b < 1 ? 1 : b;
 }
 
 bool default_search_wide()
@@ -3178,12 +3203,13 @@ void launch_search(const Work *d, const Shape &sh, Sink &k)
     void *a[] = {(void *)&d};
     const void *f = sh.wide ? search_fn<true>(sh.lookup, sh.batch)
                             : search_fn<false>(sh.lookup, sh.batch);
-    k.launch(f, grid, kThreads, a);
+    k.launch(f, grid, sh.batch ? SearchBlock<true>::kThreads : SearchBlock<false>::kThreads, a);
 }
 
 int search_waves(int num_sms, int search_bps, int32_t ntiles)
 {
-    const int64_t warps = (int64_t)num_sms * (search_bps > 0 ? search_bps : 1) * (kThreads / 32);
+    const int64_t warps =
+        (int64_t)num_sms * (search_bps > 0 ? search_bps : 1) * SearchBlock<false>::kWarps;
     return (int64_t)ntiles >= 64 * warps ? 2 : 1;
 }
 
