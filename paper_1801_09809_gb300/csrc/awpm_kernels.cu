@@ -2589,7 +2589,8 @@ __global__ void k_wt_out(const Work *__restrict__ W)
 // The levels and phases are driven from the host through Ctl::live and
 // Ctl::pass_flips.
 
-// Clear the per-solve state; mr = -1.
+// Clear the per-solve state; mr = -1; every row unreached, its offer record
+// empty.
 __global__ void k_mc_reset(const Work *__restrict__ W)
 {
     const Work &w = *W;
@@ -2608,8 +2609,11 @@ __global__ void k_mc_reset(const Work *__restrict__ W)
         c->level_done = 0u;
         c->touched = 0;
     }
-    for (int64_t x = gtid(); x < w.n; x += gstride())
+    for (int64_t x = gtid(); x < w.n; x += gstride()) {
         w.mr[x] = -1;
+        w.mrpar[x] = -1;
+        w.mroff[x] = Off{kKeyNone, 0x7fffffff, 0};
+    }
     const int64_t words = ((int64_t)w.nnz + 31) / 32 + 1;
     for (int64_t x = gtid(); x < words; x += gstride())
         w.starts[x] = 0u;
@@ -2706,19 +2710,26 @@ __device__ __forceinline__ void mc_list_tiles(const Work &w, int64_t x, uint32_t
     }
 }
 
-// A phase: every free column roots a tree and forms the frontier; rows
-// unreached; offers and tree ends cleared.
+// A phase: every free column roots a tree (its end record cleared) and forms
+// the frontier; rows unreached, offers cleared.  Only the rows the previous
+// phase reached need clearing: a row's offer record fills only at the level
+// that reaches it (its parent is set at that level's join), and the reset
+// cleared every row before the first phase.  End records are read only for
+// the roots of the running phase.
 __global__ void k_mc_phase(const Work *__restrict__ W)
 {
     const Work &w = *W;
     int live = 0;
     if (!w.ctl->err) {
         for (int64_t x = gtid(); x < w.n; x += gstride()) {
-            w.mrpar[x] = -1;
-            w.mroff[x] = Off{kKeyNone, 0x7fffffff, 0};
-            w.mtend[x] = Off{kKeyNone, 0x7fffffff, 0};
-            if (w.mc[x] < 0)
+            if (w.mrpar[x] != -1) {
+                w.mrpar[x] = -1;
+                w.mroff[x] = Off{kKeyNone, 0x7fffffff, 0};
+            }
+            if (w.mc[x] < 0) {
                 w.mroot[x] = (int32_t)x;
+                w.mtend[x] = Off{kKeyNone, 0x7fffffff, 0};
+            }
         }
         // the frontier and its tile list (the list's count is zero here:
         // the reset, or the last level of the previous phase, which kept no
@@ -2781,10 +2792,16 @@ __device__ __forceinline__ bool off_better(long long key, int32_t who, const Off
 
 // Fold (key, who) into the record at addr (128-bit compare-and-swap; a
 // failed exchange means another thread stored a better record, so the loop
-// is short; its bound only turns a broken invariant into an error bit).
+// is short; its bound only turns a broken invariant into an error bit).  The
+// first read goes to L2, where the other threads' exchanges land, so fewer
+// exchanges start from a stale copy.
 __device__ bool off_combine(Off *addr, long long key, int32_t who, Ctl *ctl)
 {
-    Off cur = *addr;
+    const int4 v = __ldcg(reinterpret_cast<const int4 *>(addr));
+    Off cur;
+    cur.key = (long long)(((unsigned long long)(unsigned)v.y << 32) | (unsigned)v.x);
+    cur.who = v.z;
+    cur.pad = v.w;
     Off mine{key, who, 0};
     for (int k = 0; k < kCasRetryCap; ++k) {
         if (!off_better(key, who, cur))
@@ -3135,16 +3152,6 @@ bool search_pipe()
     if (v && (v[0] == '0' || v[0] == '1') && v[1] == 0)
         return v[0] == '1';
     return true;
-}
-
-static int bps_clamp(const void *f)
-{
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kThreads, 0) != cudaSuccess) {
-        cudaGetLastError();
-        b = 1;
-    }
-    return b < 1 ? 1 : b;
 }
 
 template <bool kWide>
