@@ -812,10 +812,11 @@ def main():
     h2d = 4 * (n + 1) + 12 * nnz + 4 * n
     d2h = 4 * n + 88
 
-    # reset, colptr check with start marks, entries, mates, row records (+
-    # hash build), 2 weight-sum kernels; per pass: search, select, flip (its
-    # last block ends the pass); final weight sum
-    kernels_per_step = 5 + (1 if lookup_used == 2 else 0) + 2 + 3 * passes + 2
+    # reset, colptr check with start marks, entries, mates (with the input
+    # weight's partial sums), row records (+ hash build), the input weight's
+    # final sum; per pass: search, select, flip (its last block ends the
+    # pass); the output weight's two sum kernels
+    kernels_per_step = 5 + (1 if lookup_used == 2 else 0) + 1 + 3 * passes + 2
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
