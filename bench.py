@@ -94,11 +94,13 @@ def peaks():
 def search_kernel_hash():
     """sha256 (16 hex digits) of the search kernels' source text: the Steps
     A+B+C section (lookup queue, lookups, both search kernels) up to the Step D
-    section."""
+    section, and the lines defining the lookup thresholds it uses."""
     text = open(KERNEL_SRC).read()
     a = text.index("// Steps A + B + C (Algorithms 3, 4, 5)")
     b = text.index("// Step D (Algorithm 6)")
-    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
+    consts = [ln for ln in text.splitlines()
+              if ln.startswith(("constexpr int32_t kCoopMin", "constexpr int32_t kBloomMin"))]
+    return hashlib.sha256((text[a:b] + "\n".join(consts)).encode()).hexdigest()[:16]
 
 
 def profile_record(path=None):

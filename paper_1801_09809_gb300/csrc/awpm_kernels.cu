@@ -27,8 +27,10 @@ namespace awpm {
 // into an error bit instead of a hang).
 constexpr int kCasRetryCap = 1 << 20;
 
-// Closing-edge ranges longer than this go to the warp-cooperative search.
-constexpr int32_t kCoopMin = 32;
+// Closing-edge ranges longer than this go to the warp-cooperative search
+// (shorter ones to a binary search per lane).  64 measured 4.5 us per search
+// launch faster than 32 on the bench graph, 16 18 us slower.
+constexpr int32_t kCoopMin = 64;
 // Quiet NaN: wm[j] before the entry pass finds the matched entry of column j.
 constexpr unsigned long long kNaNBits = 0x7ff8000000000000ull;
 
@@ -197,6 +199,9 @@ __device__ __forceinline__ int32_t slot_start(int32_t r, int32_t base, int32_t s
 // Long columns are where the 64-bit signature fills up, so this filter keeps
 // most of their absent closing entries away from the search.
 
+// (Filters from 8 or 4 rows up took 8-12 us off a search launch on the
+// R-MAT bench graph, but cost the 27-point stencil 8 % and the 4,096-matrix
+// batch 2 % of their solve time, so the threshold stays at 32.)
 constexpr int32_t kBloomMin = 32;
 
 __device__ __forceinline__ void bloom_key(int32_t r, int32_t s, int32_t e, uint32_t &word,
