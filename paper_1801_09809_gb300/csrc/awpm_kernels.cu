@@ -28,8 +28,9 @@ namespace awpm {
 constexpr int kCasRetryCap = 1 << 20;
 
 // Closing-edge ranges longer than this go to the warp-cooperative search
-// (shorter ones to a binary search per lane).  64 measured 4.5 us per search
-// launch faster than 32 on the bench graph, 16 18 us slower.
+// (shorter ones to a binary search per lane).  On an R-MAT graph of scale 22
+// (n = 4.2 M, 69 M nonzeros) 64 measured 4.5 us per search launch faster
+// than 32, and 16 was 18 us slower.
 constexpr int32_t kCoopMin = 64;
 // Quiet NaN: wm[j] before the entry pass finds the matched entry of column j.
 constexpr unsigned long long kNaNBits = 0x7ff8000000000000ull;
@@ -199,9 +200,10 @@ __device__ __forceinline__ int32_t slot_start(int32_t r, int32_t base, int32_t s
 // Long columns are where the 64-bit signature fills up, so this filter keeps
 // most of their absent closing entries away from the search.
 
-// (Filters from 8 or 4 rows up took 8-12 us off a search launch on the
-// R-MAT bench graph, but cost the 27-point stencil 8 % and the 4,096-matrix
-// batch 2 % of their solve time, so the threshold stays at 32.)
+// (Filters from 8 or 4 rows up took 8-12 us off a search launch on an
+// R-MAT graph of scale 22, but cost a 27-point stencil of 96^3 8 % and a
+// batch of 4,096 small matrices 2 % of their solve time, so the threshold
+// stays at 32.)
 constexpr int32_t kBloomMin = 32;
 
 __device__ __forceinline__ void bloom_key(int32_t r, int32_t s, int32_t e, uint32_t &word,
@@ -1396,9 +1398,9 @@ __device__ __forceinline__ void resolve_lookups(
 // Block size of the search kernels (each warp has its own lookup queue):
 // 512 threads for a single problem, 256 for a batched solve.  With the grid
 // one wave of resident blocks, the single problem's search measured a little
-// faster with larger blocks on the bench graph (0.267 ms per launch at 512
-// threads, 0.270 at 256, 0.271 at 128), the batched solve slower (21.4 ms
-// per batch at 512, 20.0 at 256).  The minimum blocks per SM below are given
+// faster with larger blocks on an R-MAT graph of scale 22 (0.267 ms per
+// launch at 512 threads, 0.270 at 256, 0.271 at 128), a batch of 4,096 small
+// matrices slower (21.4 ms per batch at 512, 20.0 at 256).  The minimum blocks per SM below are given
 // in warps per SM, divided by the block's warps.
 #ifndef AWPM_SEARCH_THREADS
 #define AWPM_SEARCH_THREADS 512
@@ -3207,8 +3209,9 @@ bool default_search_wide()
 }
 
 // The search grid is one wave of resident blocks: each warp walks its tiles
-// to the end (two, three, four and eight waves were measured slower on the
-// bench graph: the later waves' blocks start only as whole blocks finish).
+// to the end (two, three, four and eight waves were measured slower on an
+// R-MAT graph of scale 22: the later waves' blocks start only as whole
+// blocks finish).
 void launch_search(const Work *d, const Shape &sh, Sink &k)
 {
     const unsigned grid = (unsigned)(sh.num_sms * (sh.search_bps > 0 ? sh.search_bps : 1));
@@ -3255,8 +3258,9 @@ void launch_greedy_select_end_and_flip(const Work *d, const Shape &sh, Sink &k)
 }
 
 // Step D's kernels take 32 words of the winner bitmap per warp; a single
-// problem of the large class (two search waves: n up to about 5 M in one
-// round) gets four blocks per SM, a smaller one one block per SM.  Late
+// problem of the large size class (at least 64 tiles per resident search
+// warp) gets four blocks per SM (one round of words covers n up to about
+// 5 M), a smaller one one block per SM.  Late
 // passes have few winners, so the kernels cost about their launch and a
 // read of the bitmap; blocks past the bitmap's end would only add to that.
 static inline unsigned winner_grid(const Shape &sh)
