@@ -24,6 +24,28 @@ def test_search_kernel_hash_is_stable(bench):
     assert bench.search_kernel_hash() == h
 
 
+def test_search_kernel_hash_covers_section_and_thresholds(bench, tmp_path, monkeypatch):
+    """The hash changes with the search section's text and with the lookup
+    thresholds defined outside it, and not with other code."""
+    src = open(bench.KERNEL_SRC).read()
+    h0 = bench.search_kernel_hash()
+
+    def hash_of(text):
+        f = tmp_path / "k.cu"
+        f.write_text(text)
+        monkeypatch.setattr(bench, "KERNEL_SRC", str(f))
+        return bench.search_kernel_hash()
+
+    assert hash_of(src) == h0
+    coop = [ln for ln in src.splitlines() if ln.startswith("constexpr int32_t kCoopMin")]
+    assert len(coop) == 1
+    assert hash_of(src.replace(coop[0], coop[0].replace("=", "= 1 +"))) != h0
+    a = src.index("// Steps A + B + C (Algorithms 3, 4, 5)") + 40
+    assert hash_of(src[:a] + "\n// inside\n" + src[a:]) != h0
+    b = src.index("// Step D (Algorithm 6)")
+    assert hash_of(src[:b + 10] + "\n// elsewhere\n" + src[b + 10:]) == h0
+
+
 def write_profile(path, sha, traffic):
     import json
     path.write_text(json.dumps({"kernel_source_sha256_16": sha, "dram_bytes_per_launch": traffic,
