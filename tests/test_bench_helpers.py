@@ -42,8 +42,8 @@ def test_search_kernel_hash_covers_section_and_thresholds(bench, tmp_path, monke
     assert hash_of(src.replace(coop[0], coop[0].replace("=", "= 1 +"))) != h0
     a = src.index("// Steps A + B + C (Algorithms 3, 4, 5)") + 40
     assert hash_of(src[:a] + "\n// inside\n" + src[a:]) != h0
-    b = src.index("// Step D (Algorithm 6)")
-    assert hash_of(src[:b + 10] + "\n// elsewhere\n" + src[b + 10:]) == h0
+    b = src.index("// Step D (Algorithm 6)") + len("// Step D (Algorithm 6)")
+    assert hash_of(src[:b] + "\n// elsewhere\n" + src[b:]) == h0
 
 
 def write_profile(path, sha, traffic):
